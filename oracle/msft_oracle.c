@@ -1,0 +1,568 @@
+/*
+ * msft_oracle.c -- plain, slow FP64 CPU oracle of the Multi-Slice Fourier
+ * Transform (MSFT) as "The Scatman" (arXiv 2202.03411) defines it.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this file's library.  It shares no code,
+ * header, table or constant with the CUDA library; the two only share the
+ * seeded input generators (workloads/), which hold none of the arithmetic.
+ *
+ * Every function follows one passage of the paper and is written for a reader
+ * to check against it by eye: no blocking, no fusion, no reordering beyond
+ * what the equation states.  The only liberty taken is precomputing per-pixel
+ * phase tables e^{-i q_x x}, e^{-i q_y y}, e^{-i q_z z} (a factorisation of
+ * the same exponential, exact up to rounding).
+ *
+ * Conventions (readings of passages where the paper is silent or ambiguous):
+ *  - q = k_out - k_in with k_in = k0 z^; the phase is e^{-i q.r}.  This is
+ *    Eq. 9 rewritten: E_s carries e^{i k0 s dz} and the slice prefactor is
+ *    e^{-i k_z s dz}, so the net z-phase is e^{-i (k_z - k0) z}.
+ *  - Flat detector normal to z at distance D=1; theta_max is reached at the
+ *    edge midpoints; pixel centres X_u = tan(theta_max) (2u+1-N)/N.
+ *  - Voxel centres are (index - (N-1)/2) * voxel; the shape centre is the
+ *    grid centre plus an offset.
+ *  - Slice strength is linear in the occupancy chi (Eq. 2 defines the slice
+ *    strength as the slice integral of rho, and rho ~ n^2-1 inside the shape);
+ *    propagation uses the slice-averaged index n~ - 1 = chi (n-1) (Eq. 8).
+ *  - E_0 = 1 on slice 0 and slice j sees only slices < j (Eq. 8-9): the
+ *    transmission is an EXCLUSIVE product along z.
+ *  - Prefactor of the proportionality in Eq. 9 is 1.
+ *
+ * Array layouts: voxel arrays are [z][x][y] (y fastest); q arrays are
+ * [pixel][3]; detector pixel p = v*det_nx + u.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#include <complex.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_SPHERE 0
+#define ORC_ELLIPSOID 1
+#define ORC_SPHHARM 2
+
+/* Shape parameters as in the paper's Listings 1-2 (Sec. 5). */
+typedef struct {
+    int kind;
+    double r, a, b, c;          /* sphere radius; ellipsoid semi-axes (c on the main axis) */
+    double R0;                  /* harmonics mean radius */
+    int lmax;
+    const double *alm;          /* (lmax+1)^2 coefficients, index l*l+l+m, alm[0] unused */
+    double delta, beta;         /* n = 1 - delta + i beta (Eq. 7) */
+    double latitude, longitude, rotation;   /* degrees (Fig. 6) */
+    double cx, cy, cz;          /* centre offset from the grid centre */
+} orc_shape;
+
+static const double ORC_PI = 3.14159265358979323846;
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* cos and sin of an angle in degrees, exact at multiples of 90 degrees so
+ * that axis-aligned orientations give exact rotation matrices. */
+static void orc_cos_sin_deg(double deg, double *c, double *s)
+{
+    double q = deg / 90.0;
+    if (q == floor(q)) {
+        long k = ((long)q % 4 + 4) % 4;
+        static const double cs[4] = {1.0, 0.0, -1.0, 0.0};
+        static const double sn[4] = {0.0, 1.0, 0.0, -1.0};
+        *c = cs[k];
+        *s = sn[k];
+        return;
+    }
+    double rad = deg * ORC_PI / 180.0;
+    *c = cos(rad);
+    *s = sin(rad);
+}
+
+static void orc_matmul3(const double A[9], const double B[9], double C[9])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < 3; ++k) acc += A[3 * i + k] * B[3 * k + j];
+            C[3 * i + j] = acc;
+        }
+}
+
+/*
+ * Body-to-lab rotation (Fig. 6 caption, Sec. 5.1 "Define a shape"):
+ * the main axis (body z) points along latitude/longitude, where +90 deg
+ * latitude points towards the incoming beam (-z) and longitude is measured
+ * from +x towards +y; afterwards the body is spun about its main axis.
+ * R = Rz(longitude) * Ry(90 deg + latitude) * Rz(rotation).  Row-major.
+ */
+void orc_rotation(double lat, double lon, double rot, double R[9])
+{
+    double c1, s1, c2, s2, c3, s3;
+    orc_cos_sin_deg(lon, &c1, &s1);
+    orc_cos_sin_deg(90.0 + lat, &c2, &s2);
+    orc_cos_sin_deg(rot, &c3, &s3);
+    double Rz1[9] = {c1, -s1, 0, s1, c1, 0, 0, 0, 1};
+    double Ry[9] = {c2, 0, s2, 0, 1, 0, -s2, 0, c2};
+    double Rz3[9] = {c3, -s3, 0, s3, c3, 0, 0, 0, 1};
+    double T[9];
+    orc_matmul3(Rz1, Ry, T);
+    orc_matmul3(T, Rz3, R);
+}
+
+/* Associated Legendre function P_l^m(x), m >= 0, including the
+ * Condon-Shortley phase (-1)^m; Eq. 11 gives the negative-m relation.
+ * Standard upward recurrence in l. */
+double orc_legendre(int l, int m, double x)
+{
+    double pmm = 1.0;
+    double sx = sqrt((1.0 - x) * (1.0 + x));
+    for (int k = 1; k <= m; ++k) pmm *= -(2.0 * k - 1.0) * sx;
+    if (l == m) return pmm;
+    double pm1 = x * (2.0 * m + 1.0) * pmm;
+    if (l == m + 1) return pm1;
+    double pl = 0.0;
+    for (int ll = m + 2; ll <= l; ++ll) {
+        pl = ((2.0 * ll - 1.0) * x * pm1 - (ll + m - 1.0) * pmm) / (ll - m);
+        pmm = pm1;
+        pm1 = pl;
+    }
+    return pl;
+}
+
+/* Real orthonormal spherical harmonic built from Eq. 10's complex Y_l^m:
+ * m > 0: sqrt(2) Re Y_l^m;  m < 0: sqrt(2) Im Y_l^{|m|};  m = 0: Y_l^0.
+ * theta is the polar angle from the body z axis, phi the azimuth from body x. */
+double orc_real_sh(int l, int m, double theta, double phi)
+{
+    int am = m < 0 ? -m : m;
+    double ratio = 1.0;                     /* (l-|m|)! / (l+|m|)! */
+    for (int k = l - am + 1; k <= l + am; ++k) ratio /= (double)k;
+    double norm = sqrt((2.0 * l + 1.0) / (4.0 * ORC_PI) * ratio);
+    double p = orc_legendre(l, am, cos(theta));
+    if (m == 0) return norm * p;
+    if (m > 0) return sqrt(2.0) * norm * p * cos(am * phi);
+    return sqrt(2.0) * norm * p * sin(am * phi);
+}
+
+static double orc_half_width(int nx, int ny, int nz, double voxel)
+{
+    int n = nx < ny ? nx : ny;
+    if (nz < n) n = nz;
+    return 0.5 * (n - 1) * voxel;
+}
+
+/* Harmonics surface radius r(theta,phi) = R0 (1 + sum_{1<=l<=L} a_lm Y_lm)
+ * (Sec. 5.2 "Shape (1/3)", Eq. 10-11), clipped to [0.1 R0, hw - voxel]. */
+static double orc_sh_radius(const orc_shape *sh, double theta, double phi,
+                            double rmax, int *clipped)
+{
+    double sum = 0.0;
+    for (int l = 1; l <= sh->lmax; ++l)
+        for (int m = -l; m <= l; ++m)
+            sum += sh->alm[l * l + l + m] * orc_real_sh(l, m, theta, phi);
+    double r = sh->R0 * (1.0 + sum);
+    *clipped = 0;
+    if (r < 0.1 * sh->R0) { r = 0.1 * sh->R0; *clipped = 1; }
+    if (r > rmax) { r = rmax; *clipped = 1; }
+    return r;
+}
+
+static double orc_sigmoid(double t) { return 1.0 / (1.0 + exp(-t)); }
+
+/* Body-frame coordinates of voxel centre (ix,iy,iz). */
+static void orc_body_coords(const orc_shape *sh, const double R[9], int ix, int iy, int iz,
+                            int nx, int ny, int nz, double voxel, double p[3])
+{
+    double d[3];
+    d[0] = (ix - 0.5 * (nx - 1)) * voxel - sh->cx;
+    d[1] = (iy - 0.5 * (ny - 1)) * voxel - sh->cy;
+    d[2] = (iz - 0.5 * (nz - 1)) * voxel - sh->cz;
+    /* p = R^T d */
+    for (int i = 0; i < 3; ++i) p[i] = R[0 + i] * d[0] + R[3 + i] * d[1] + R[6 + i] * d[2];
+}
+
+/*
+ * Block 5 (Sec. 3.2, "render the slice's scattering potential"): occupancy
+ * chi of every voxel, [z][x][y].  Binary (soft==0): the voxel centre is
+ * inside (ties count as inside) -- sphere |p|^2 <= r^2, ellipsoid
+ * (x/a)^2+(y/b)^2+(z/c)^2 <= 1, harmonics |p| <= r(theta,phi).  Soft:
+ * chi = sigmoid((r_s(p^) - |p|)/w) with r_s the surface radius along the
+ * voxel's direction from the centre.  Returns 1 if a harmonics radius was
+ * clipped.
+ */
+int orc_voxelise(const orc_shape *sh, int nx, int ny, int nz, double voxel,
+                 int soft, double w, double *chi)
+{
+    double R[9];
+    orc_rotation(sh->latitude, sh->longitude, sh->rotation, R);
+    double rmax = orc_half_width(nx, ny, nz, voxel) - voxel;
+    int any_clip = 0;
+#pragma omp parallel for collapse(2) reduction(| : any_clip)
+    for (int iz = 0; iz < nz; ++iz)
+        for (int ix = 0; ix < nx; ++ix)
+            for (int iy = 0; iy < ny; ++iy) {
+                double p[3];
+                orc_body_coords(sh, R, ix, iy, iz, nx, ny, nz, voxel, p);
+                double rr = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+                double v;
+                if (!soft) {
+                    if (sh->kind == ORC_SPHERE) {
+                        v = (p[0] * p[0] + p[1] * p[1] + p[2] * p[2] <= sh->r * sh->r) ? 1.0 : 0.0;
+                    } else if (sh->kind == ORC_ELLIPSOID) {
+                        double qf = (p[0] / sh->a) * (p[0] / sh->a) + (p[1] / sh->b) * (p[1] / sh->b)
+                                    + (p[2] / sh->c) * (p[2] / sh->c);
+                        v = (qf <= 1.0) ? 1.0 : 0.0;
+                    } else {
+                        double th = rr > 0.0 ? acos(p[2] / rr) : 0.0;
+                        double ph = atan2(p[1], p[0]);
+                        int cl;
+                        double rs = orc_sh_radius(sh, th, ph, rmax, &cl);
+                        any_clip |= cl;
+                        v = (rr <= rs) ? 1.0 : 0.0;
+                    }
+                } else {
+                    double rs;
+                    if (sh->kind == ORC_SPHERE) {
+                        rs = sh->r;
+                    } else if (sh->kind == ORC_ELLIPSOID) {
+                        double u0 = 0.0, u1 = 0.0, u2 = 1.0;
+                        if (rr > 0.0) { u0 = p[0] / rr; u1 = p[1] / rr; u2 = p[2] / rr; }
+                        rs = 1.0 / sqrt((u0 / sh->a) * (u0 / sh->a) + (u1 / sh->b) * (u1 / sh->b)
+                                        + (u2 / sh->c) * (u2 / sh->c));
+                    } else {
+                        double th = rr > 0.0 ? acos(p[2] / rr) : 0.0;
+                        double ph = atan2(p[1], p[0]);
+                        int cl;
+                        rs = orc_sh_radius(sh, th, ph, rmax, &cl);
+                        any_clip |= cl;
+                    }
+                    v = orc_sigmoid((rs - rr) / w);
+                }
+                chi[((size_t)iz * nx + ix) * ny + iy] = v;
+            }
+    return any_clip;
+}
+
+/*
+ * Eq. 5-9 and Blocks 4 + 9: effective slice strength
+ *   rho_j(x,y) = (n^2 - 1) chi_j(x,y) E_j(x,y) / (E_0 e^{i k0 j dz})
+ * with the projection-approximation recursion of Eq. 8,
+ *   E_j = E_{j-1} e^{i k0 dz n~_{j-1}},  E_0 = 1 (Block 4: plane wave),
+ *   n~_{j-1} - 1 = chi_{j-1} (n - 1),  n = 1 - delta + i beta (Eq. 7).
+ * Dividing out the free-space phase e^{i k0 j dz} leaves the running product
+ *   T_j = prod_{j'<j} e^{i k0 dz chi_{j'} (n-1)}.
+ * Output [z][x][y], real and imaginary parts in separate arrays.
+ */
+void orc_slices(const double *chi, int nx, int ny, int nz, double dz, double wavelength,
+                double delta, double beta, double *rho_re, double *rho_im)
+{
+    double k0 = 2.0 * ORC_PI / wavelength;
+    double complex n = 1.0 - delta + I * beta;
+    double complex strength = n * n - 1.0;
+#pragma omp parallel for collapse(2)
+    for (int ix = 0; ix < nx; ++ix)
+        for (int iy = 0; iy < ny; ++iy) {
+            double complex T = 1.0;                 /* E_0 / E_0 */
+            for (int iz = 0; iz < nz; ++iz) {
+                size_t idx = ((size_t)iz * nx + ix) * ny + iy;
+                double complex rho = strength * chi[idx] * T;
+                rho_re[idx] = creal(rho);
+                rho_im[idx] = cimag(rho);
+                /* Block 9: propagate through slice iz for the next slice */
+                T = T * cexp(I * k0 * dz * chi[idx] * (n - 1.0));
+            }
+        }
+}
+
+/*
+ * Eq. 3 and Block 1 + 3: transfer momentum of every pixel of a flat detector
+ * normal to the beam.  Pixel (u,v) sits at (X_u, Y_v, 1) with
+ * X_u = tan(theta_max) (2u+1-Nx)/Nx; its scattering angle is
+ * theta = atan(sqrt(X^2+Y^2)) and azimuth phi = atan2(Y,X); k_out is
+ * k0 (sin th cos ph, sin th sin ph, cos th) on the Ewald sphere and
+ * q = k_out - k_in, so q_z = -k0 (1 - cos theta) (Eq. 3 up to the sign
+ * convention stated in the header).
+ */
+void orc_detector_q(int det_nx, int det_ny, double theta_max_deg, double wavelength, double *q)
+{
+    double k0 = 2.0 * ORC_PI / wavelength;
+    double h = tan(theta_max_deg * ORC_PI / 180.0);
+    for (int v = 0; v < det_ny; ++v)
+        for (int u = 0; u < det_nx; ++u) {
+            double X = h * (2.0 * u + 1.0 - det_nx) / det_nx;
+            double Y = h * (2.0 * v + 1.0 - det_ny) / det_ny;
+            double th = atan(sqrt(X * X + Y * Y));
+            double ph = atan2(Y, X);
+            size_t p = (size_t)v * det_nx + u;
+            q[3 * p + 0] = k0 * sin(th) * cos(ph);
+            q[3 * p + 1] = k0 * sin(th) * sin(ph);
+            q[3 * p + 2] = k0 * (cos(th) - 1.0);
+        }
+}
+
+/*
+ * Eq. 9 (Blocks 6-8, 10): the scattered field at each q,
+ *   A(q) = sum_j e^{-i q_z z_j} F[rho_j](q_x, q_y),
+ *   F[rho_j](q_x, q_y) = sum_{x,y} rho_j(x,y) e^{-i (q_x x + q_y y)},
+ * slice by slice as the main loop does (Block 6: per-slice Fourier sum;
+ * Block 7: slice phase; Block 8: accumulate).  The Fourier "transform" is
+ * the direct non-uniform sum at the detector's q.
+ */
+void orc_msft(const double *rho_re, const double *rho_im, int nx, int ny, int nz, double voxel,
+              const double *q, long n_q, double *A_re, double *A_im)
+{
+#pragma omp parallel
+    {
+        double complex *ex = malloc(sizeof(double complex) * nx);
+        double complex *ey = malloc(sizeof(double complex) * ny);
+#pragma omp for schedule(dynamic, 4)
+        for (long p = 0; p < n_q; ++p) {
+            double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+            for (int ix = 0; ix < nx; ++ix) {
+                double x = (ix - 0.5 * (nx - 1)) * voxel;
+                ex[ix] = cexp(-I * qx * x);
+            }
+            for (int iy = 0; iy < ny; ++iy) {
+                double y = (iy - 0.5 * (ny - 1)) * voxel;
+                ey[iy] = cexp(-I * qy * y);
+            }
+            double complex A = 0.0;
+            for (int iz = 0; iz < nz; ++iz) {
+                double z = (iz - 0.5 * (nz - 1)) * voxel;
+                double complex F = 0.0;            /* Block 6 */
+                for (int ix = 0; ix < nx; ++ix)
+                    for (int iy = 0; iy < ny; ++iy) {
+                        size_t idx = ((size_t)iz * nx + ix) * ny + iy;
+                        F += (rho_re[idx] + I * rho_im[idx]) * ex[ix] * ey[iy];
+                    }
+                A += cexp(-I * qz * z) * F;        /* Blocks 7-8 */
+            }
+            A_re[p] = creal(A);
+            A_im[p] = cimag(A);
+        }
+        free(ex);
+        free(ey);
+    }
+}
+
+/* Block 11: I = |A|^2. */
+void orc_intensity(const double *A_re, const double *A_im, long n_q, double *I_out)
+{
+    for (long p = 0; p < n_q; ++p) I_out[p] = A_re[p] * A_re[p] + A_im[p] * A_im[p];
+}
+
+/*
+ * Adjoint of the linear map rho -> A of Eq. 9:
+ *   S(r_v) = sum_q g_q e^{+i q . r_v},  [z][x][y],
+ * so that sum_q conj(A(rho)_q) g_q = sum_v conj(rho_v) S_v.  Each thread owns
+ * whole slices and walks every q with the same per-q phase tables as the
+ * forward sum.
+ */
+void orc_msft_adjoint(const double *g_re, const double *g_im, const double *q, long n_q,
+                      int nx, int ny, int nz, double voxel, double *S_re, double *S_im)
+{
+#pragma omp parallel
+    {
+        double complex *ex = malloc(sizeof(double complex) * nx);
+        double complex *ey = malloc(sizeof(double complex) * ny);
+        double complex *acc = malloc(sizeof(double complex) * (size_t)nx * ny);
+#pragma omp for schedule(dynamic, 1)
+        for (int iz = 0; iz < nz; ++iz) {
+            double z = (iz - 0.5 * (nz - 1)) * voxel;
+            for (size_t k = 0; k < (size_t)nx * ny; ++k) acc[k] = 0.0;
+            for (long p = 0; p < n_q; ++p) {
+                double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+                for (int ix = 0; ix < nx; ++ix) ex[ix] = cexp(I * qx * ((ix - 0.5 * (nx - 1)) * voxel));
+                for (int iy = 0; iy < ny; ++iy) ey[iy] = cexp(I * qy * ((iy - 0.5 * (ny - 1)) * voxel));
+                double complex gz = (g_re[p] + I * g_im[p]) * cexp(I * qz * z);
+                for (int ix = 0; ix < nx; ++ix) {
+                    double complex gx = gz * ex[ix];
+                    for (int iy = 0; iy < ny; ++iy) acc[(size_t)ix * ny + iy] += gx * ey[iy];
+                }
+            }
+            for (int ix = 0; ix < nx; ++ix)
+                for (int iy = 0; iy < ny; ++iy) {
+                    size_t idx = ((size_t)iz * nx + ix) * ny + iy;
+                    S_re[idx] = creal(acc[(size_t)ix * ny + iy]);
+                    S_im[idx] = cimag(acc[(size_t)ix * ny + iy]);
+                }
+        }
+        free(ex);
+        free(ey);
+        free(acc);
+    }
+}
+
+/* Derivative of the surface radius r_s(p^) with respect to each geometric
+ * parameter, plus r_s itself.  Geometric parameters:
+ *   sphere: [r]; ellipsoid: [a, b, c]; harmonics: [a_lm (l>=1), R0]. */
+static double orc_radius_and_grad(const orc_shape *sh, const double p[3], double rr, double rmax,
+                                  double *dr)
+{
+    if (sh->kind == ORC_SPHERE) {
+        dr[0] = 1.0;
+        return sh->r;
+    }
+    double u0 = 0.0, u1 = 0.0, u2 = 1.0;
+    if (rr > 0.0) { u0 = p[0] / rr; u1 = p[1] / rr; u2 = p[2] / rr; }
+    if (sh->kind == ORC_ELLIPSOID) {
+        double s = (u0 / sh->a) * (u0 / sh->a) + (u1 / sh->b) * (u1 / sh->b) + (u2 / sh->c) * (u2 / sh->c);
+        double rs = 1.0 / sqrt(s);
+        /* r_s = s^{-1/2}; ds/da = -2 u0^2 / a^3 */
+        double f = -0.5 * rs * rs * rs;
+        dr[0] = f * (-2.0 * u0 * u0 / (sh->a * sh->a * sh->a));
+        dr[1] = f * (-2.0 * u1 * u1 / (sh->b * sh->b * sh->b));
+        dr[2] = f * (-2.0 * u2 * u2 / (sh->c * sh->c * sh->c));
+        return rs;
+    }
+    double th = rr > 0.0 ? acos(p[2] / rr) : 0.0;
+    double ph = atan2(p[1], p[0]);
+    int nlm = (sh->lmax + 1) * (sh->lmax + 1) - 1;
+    double sum = 0.0;
+    for (int l = 1; l <= sh->lmax; ++l)
+        for (int m = -l; m <= l; ++m) {
+            double y = orc_real_sh(l, m, th, ph);
+            dr[l * l + l + m - 1] = sh->R0 * y;
+            sum += sh->alm[l * l + l + m] * y;
+        }
+    dr[nlm] = 1.0 + sum;
+    double rs = sh->R0 * (1.0 + sum);
+    if (rs < 0.1 * sh->R0) {
+        for (int k = 0; k < nlm; ++k) dr[k] = 0.0;
+        dr[nlm] = 0.1;
+        rs = 0.1 * sh->R0;
+    } else if (rs > rmax) {
+        for (int k = 0; k <= nlm; ++k) dr[k] = 0.0;
+        rs = rmax;
+    }
+    return rs;
+}
+
+static int orc_n_geom(const orc_shape *sh)
+{
+    if (sh->kind == ORC_SPHERE) return 1;
+    if (sh->kind == ORC_ELLIPSOID) return 3;
+    return (sh->lmax + 1) * (sh->lmax + 1);   /* (L+1)^2 - 1 coefficients + R0 */
+}
+
+int orc_n_params(const orc_shape *sh) { return orc_n_geom(sh) + 2; }
+
+/*
+ * Gradient of a real loss L(I) with respect to the shape parameters, given
+ * dL/dI on every pixel, for soft occupancy (binary occupancy has no shape
+ * gradient).  With A_q = c F_q, c = n^2 - 1, F_q = sum_v s_v e^{-i q.r_v},
+ * s_v = chi_v T_v and T_v = exp(i k0 dz (n-1) C_v), C_v = sum_{v' before v
+ * along z} chi_{v'}:
+ *   dL/dtheta = sum_q w_q 2 Re(conj(A_q) dA_q/dtheta),  w = dL/dI,
+ *   dA_q/dtheta = c' F_q + c sum_v (ds_v/dtheta) e^{-i q.r_v}.
+ * Writing R_v = c sum_q w_q conj(A_q) e^{-i q.r_v}:
+ *   dL/dtheta = 2 Re[(c'/c) sum_q w_q |A_q|^2] + 2 Re sum_v R_v ds_v/dtheta,
+ *   ds_v = dchi_v T_v + s_v i k0 dz [(n-1) dC_v + C_v d(n-1)].
+ * The chain rule through C_v turns the per-voxel factor into a reverse
+ * (suffix) sum along z.  Parameter order: geometric parameters (sphere r;
+ * ellipsoid a,b,c; harmonics a_lm for l>=1 then R0), then delta, beta.
+ * A_re/A_im must be the forward field for the same shape and q.
+ */
+int orc_gradient(const orc_shape *sh, int nx, int ny, int nz, double voxel, double wavelength,
+                 double w, const double *q, long n_q, const double *dLdI,
+                 const double *A_re, const double *A_im, double *grad)
+{
+    size_t nv = (size_t)nx * ny * nz;
+    int ng = orc_n_geom(sh);
+    double k0 = 2.0 * ORC_PI / wavelength;
+    double dz = voxel;
+    double complex n = 1.0 - sh->delta + I * sh->beta;
+    double complex c = n * n - 1.0;
+    double complex dc_ddelta = -2.0 * n, dc_dbeta = 2.0 * I * n;
+    double complex dn_ddelta = -1.0, dn_dbeta = I;
+
+    double *chi = malloc(sizeof(double) * nv);
+    double *g_re = malloc(sizeof(double) * n_q), *g_im = malloc(sizeof(double) * n_q);
+    double *S_re = malloc(sizeof(double) * nv), *S_im = malloc(sizeof(double) * nv);
+    orc_voxelise(sh, nx, ny, nz, voxel, 1, w, chi);
+
+    /* R_v = c conj(sum_q w_q A_q e^{+i q.r_v}) */
+    for (long p = 0; p < n_q; ++p) {
+        g_re[p] = dLdI[p] * A_re[p];
+        g_im[p] = dLdI[p] * A_im[p];
+    }
+    orc_msft_adjoint(g_re, g_im, q, n_q, nx, ny, nz, voxel, S_re, S_im);
+
+    /* term from c(delta, beta) */
+    double sumWI = 0.0;
+    for (long p = 0; p < n_q; ++p) sumWI += dLdI[p] * (A_re[p] * A_re[p] + A_im[p] * A_im[p]);
+    for (int k = 0; k < ng + 2; ++k) grad[k] = 0.0;
+    grad[ng + 0] += 2.0 * creal(dc_ddelta / c * sumWI);
+    grad[ng + 1] += 2.0 * creal(dc_dbeta / c * sumWI);
+
+    double R[9];
+    orc_rotation(sh->latitude, sh->longitude, sh->rotation, R);
+    double rmax = orc_half_width(nx, ny, nz, voxel) - voxel;
+    double *dr = malloc(sizeof(double) * (ng > 0 ? ng : 1));
+    double complex g_dn_delta = 0.0, g_dn_beta = 0.0;
+    double complex *Rs = malloc(sizeof(double complex) * nz);
+    double *C = malloc(sizeof(double) * nz);
+    double complex *T = malloc(sizeof(double complex) * nz);
+    for (int ix = 0; ix < nx; ++ix)
+        for (int iy = 0; iy < ny; ++iy) {
+            /* forward along z: C_v (exclusive) and T_v */
+            double acc = 0.0;
+            for (int iz = 0; iz < nz; ++iz) {
+                size_t idx = ((size_t)iz * nx + ix) * ny + iy;
+                C[iz] = acc;
+                T[iz] = cexp(I * k0 * dz * (n - 1.0) * acc);
+                acc += chi[idx];
+                Rs[iz] = c * conj(S_re[idx] + I * S_im[idx]);
+            }
+            /* suffix[iz] = sum_{iz' > iz} R_v' s_v' */
+            double complex suffix = 0.0;
+            for (int iz = nz - 1; iz >= 0; --iz) {
+                size_t idx = ((size_t)iz * nx + ix) * ny + iy;
+                double complex s = chi[idx] * T[iz];
+                /* d(n-1) terms: sum_v R_v s_v i k0 dz C_v d(n-1) */
+                g_dn_delta += Rs[iz] * s * I * k0 * dz * C[iz] * dn_ddelta;
+                g_dn_beta += Rs[iz] * s * I * k0 * dz * C[iz] * dn_dbeta;
+                /* dchi_v enters s_v directly and every later C_v' */
+                double complex chibar = Rs[iz] * T[iz] + I * k0 * dz * (n - 1.0) * suffix;
+                suffix += Rs[iz] * s;
+                if (ng > 0) {
+                    double p[3];
+                    orc_body_coords(sh, R, ix, iy, iz, nx, ny, nz, voxel, p);
+                    double rr = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+                    double rs = orc_radius_and_grad(sh, p, rr, rmax, dr);
+                    double sg = orc_sigmoid((rs - rr) / w);
+                    double dsig = sg * (1.0 - sg) / w;
+                    for (int k = 0; k < ng; ++k)
+                        grad[k] += 2.0 * creal(chibar) * dsig * dr[k];
+                }
+            }
+        }
+    free(Rs);
+    free(C);
+    free(T);
+    grad[ng + 0] += 2.0 * creal(g_dn_delta);
+    grad[ng + 1] += 2.0 * creal(g_dn_beta);
+    free(dr);
+    free(chi);
+    free(g_re);
+    free(g_im);
+    free(S_re);
+    free(S_im);
+    return 0;
+}
