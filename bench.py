@@ -1,0 +1,320 @@
+#!/usr/bin/env python
+"""MSFT benchmark: diffraction patterns per second on one or more GB300s.
+
+Workload (default): real spherical-harmonics shapes, l <= 8, R0 = 48 voxels,
+a_lm ~ N(0, 0.05/l), random orientation, on a 128^3 grid, wavelength 10 voxels,
+flat 512x512 detector to 60 deg, delta = 0.01, beta = 0.001; tensor-core
+contraction with BF16 operands, split hi/lo phases and FP32 accumulation.
+A step is one batch of `--batch` such patterns (each: voxelise + transmission
+scan + contraction + intensity).  Inputs are synthetic and seeded.
+
+Contract: W untimed warm-up steps, then K timed steps between a barrier and a
+device synchronisation; rank 0 prints one JSON line.  Under torchrun each rank
+simulates its own batch (independent patterns, no collective on the data path)
+and the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MSFT patterns/sec (128^3 harmonics shape, 512^2 detector to 60 deg)"
+UNIT = "patterns/s"
+WORKLOAD = "sh_l8_R48_grid128_det512_60deg"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tc_bf16_split")
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--cpu-sample-pixels", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(shapes, g, I_gpu, n_sample, seed=0):
+    """The oracle, as it stands, on a bounded sample of the same workload: one
+    pattern's full voxelisation and transmission plus the field at n_sample
+    pixels, scaled to patterns/s.  Also returns the GPU result's relative L2
+    error against the oracle on that sample."""
+    import numpy as np
+
+    import oracle
+    shape = shapes[0]
+    rng = np.random.default_rng(seed)
+    sample = np.sort(rng.choice(g.n_pix, size=min(n_sample, g.n_pix), replace=False))
+    q = oracle.detector_q(g)[sample]
+    t0 = time.perf_counter()
+    chi, _ = oracle.voxelise(shape, g)
+    rho = oracle.slices(chi, g, shape.delta, shape.beta)
+    t1 = time.perf_counter()
+    A = oracle.msft(rho, q, g.voxel)
+    t2 = time.perf_counter()
+    per_pattern = (t1 - t0) + (t2 - t1) * g.n_pix / len(sample)
+    Iref = np.abs(A) ** 2
+    err = oracle.relative_l2(I_gpu[sample], Iref) if I_gpu is not None else None
+    return {"value": 1.0 / per_pattern, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"1 pattern: full 128^3 voxelisation + transmission, field at {len(sample)} of "
+                      f"{g.n_pix} pixels, time scaled to the whole detector ({t2 - t0:.1f} s of CPU work)"}, err
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from workloads import sh_128
+    g, shapes = sh_128(n_shapes=1)
+    shape = shapes[0]
+    rng = np.random.default_rng(0)
+    n_s = max(1, args.cpu_sample_pixels // 4)
+    q_all = oracle.detector_q(g)
+    times = []
+    for k in range(args.warmup + args.steps):
+        sample = rng.choice(g.n_pix, size=n_s, replace=False)
+        t0 = time.perf_counter()
+        chi, _ = oracle.voxelise(shape, g)
+        rho = oracle.slices(chi, g, shape.delta, shape.beta)
+        t1 = time.perf_counter()
+        oracle.msft(rho, q_all[sample], g.voxel)
+        t2 = time.perf_counter()
+        if k >= args.warmup:
+            times.append((t1 - t0) + (t2 - t1) * g.n_pix / n_s)
+    per = statistics.mean(times)
+    value = 1.0 / per
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": 1, "precision": "fp64 oracle (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"per step: 1 pattern's voxelisation + transmission and the field at {n_s} "
+                                   f"random pixels, scaled to {g.n_pix} pixels"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local_rank = dist_env()
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_2202_03411_gb300 as sm
+    from workloads import sh_128
+
+    g, shapes = sh_128(n_shapes=args.batch, seed0=rank * args.batch)
+    B = len(shapes)
+    stream = torch.cuda.current_stream()
+    h = sm.scatman_create(g, args.precision)
+    I_all = torch.empty((B, g.n_pix), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(B)]
+
+    def step():
+        for b, s in enumerate(shapes):
+            ev[b][0].record(stream)
+            sm.scatman_voxelise(h, s)
+            ev[b][1].record(stream)
+            sm.scatman_forward(h, I_all[b])
+            ev[b][2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    sm.scatman_sync(h)
+
+    props = torch.cuda.get_device_properties(local_rank)
+    gpu_id = str(getattr(props, "uuid", local_rank))
+    if gpu_id and not gpu_id.startswith("GPU-") and len(gpu_id) > 8:
+        gpu_id = "GPU-" + gpu_id
+    sampler = ClockSampler(gpu_id)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    step_ms, pat_ms, fwd_ms, vox_ms = [], [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1)                       # evict L2 between timed steps (not timed)
+        step()
+        torch.cuda.synchronize()
+        pats = [ev[b][0].elapsed_time(ev[b][2]) for b in range(B)]
+        fwd_ms += [ev[b][1].elapsed_time(ev[b][2]) for b in range(B)]
+        vox_ms += [ev[b][0].elapsed_time(ev[b][1]) for b in range(B)]
+        pat_ms += pats
+        step_ms.append(ev[0][0].elapsed_time(ev[B - 1][2]))
+    sm.scatman_sync(h)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # roofline of the contraction kernel (the dominant launch)
+    peaks, peak_kind = measured_peaks()
+    n_vox = g.nx * g.ny * g.nz
+    products = 2 if "split" in args.precision else 1
+    flops = products * 8.0 * g.n_pix * n_vox          # real flops of the issued tensor-core products
+    fwd_avg_s = statistics.mean(fwd_ms) / 1e3
+    achieved = flops / fwd_avg_s / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "msft_tc_kernel",
+                "peak_source": f"{peak_kind} bf16_tflops_sustained (cuBLAS bf16; f16 has the same nominal rate)",
+                "flops_per_launch": flops,
+                "useful_single_product_tflops": achieved / products}
+
+    # end to end through the C ABI with host memory: voxelise + forward + D2H per pattern
+    I_host = torch.empty((B, g.n_pix), dtype=torch.float32, pin_memory=True)
+    for s_i, s in enumerate(shapes[:2]):
+        sm.scatman_acquire(h, s, I_host[s_i].numpy())
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(args.steps):
+        for b, s in enumerate(shapes):
+            sm.scatman_acquire(h, s, I_host[b].numpy())
+    e_el = time.perf_counter() - e0
+    if dist is not None:
+        t = torch.tensor([e_el], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_el = float(t.item())
+    h2d = B * (8 * (shapes[0].lmax + 1) ** 2 + 160)      # shape struct + coefficients handed over
+    d2h = B * g.n_pix * 4
+    e2e = {"value": world * B * args.steps / e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, err = cpu_baseline(shapes, g, I_all[0].double().cpu().numpy(), args.cpu_sample_pixels)
+
+    pat_sorted = sorted(pat_ms)
+    p50 = pat_sorted[len(pat_sorted) // 2]
+    p99 = pat_sorted[min(len(pat_sorted) - 1, int(math.ceil(0.99 * len(pat_sorted))) - 1)]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if "bf16" in args.precision else "f16",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_per_gpu": B, "grid": [g.nx, g.ny, g.nz],
+                   "detector": [g.det_nx, g.det_ny], "theta_max_deg": g.theta_max_deg,
+                   "wavelength_voxels": g.wavelength, "precision": args.precision, "parallelism": "replicas",
+                   "l2": "flushed between timed steps (256 MB write, outside the timed events)"},
+        "latency_ms": {"p50": p50, "p99": p99, "unit": "ms per pattern (voxelise + contraction)"},
+        "stage_ms": {"voxelise_scan": statistics.mean(vox_ms), "contraction": statistics.mean(fwd_ms)},
+        "error_vs_fp64_oracle": {"rel_l2_I": err, "on": "cpu_baseline sample of pattern 0"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 2 * B * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    }
+    h.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

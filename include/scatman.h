@@ -1,0 +1,224 @@
+/*
+ * scatman.h -- C ABI of the GB300 Multi-Slice Fourier Transform library.
+ *
+ * The library computes the Scatman's wide-angle diffraction pattern
+ * (arXiv 2202.03411, Eq. 9):
+ *
+ *   A(q) = (n^2 - 1) sum_j e^{-i q_z z_j} sum_{x,y} chi_j(x,y) T_j(x,y) e^{-i (q_x x + q_y y)},
+ *   T_j  = exp(i k0 dz (n - 1) C_j),   C_j = sum_{j' < j} chi_{j'}   (Eq. 8, exclusive),
+ *   I(q) = |A(q)|^2                                                    (Sec. 3.3, Block 11),
+ *
+ * with n = 1 - delta + i beta (Eq. 7), k0 = 2 pi / wavelength, chi the
+ * voxel occupancy of the shape (Block 5) and q the transfer momentum of each
+ * detector pixel on the Ewald sphere (Eq. 3).
+ *
+ * Conventions shared by every call:
+ *  - Voxel arrays are [z][x][y] with y fastest.  Voxel centres sit at
+ *    (index - (N-1)/2) * voxel; the beam travels along +z and enters at z
+ *    index 0.  q = k_out - k_in (so q_z <= 0) and the phase is e^{-i q.r}.
+ *  - Detector pixel p = v*det_nx + u; u runs along x, v along y.  The flat
+ *    detector is normal to z and reaches theta_max at the edge midpoints.
+ *  - All device work is queued on the handle's CUDA stream and is
+ *    asynchronous unless a call says it synchronises.
+ *  - Errors come back as a negative scatman_status; nothing aborts or throws
+ *    across the ABI.  scatman_last_error() describes the last failure.
+ *  - A handle is not thread safe; distinct handles are independent.
+ *  - Pointers are borrowed for the duration of the call only, unless stated.
+ */
+#ifndef SCATMAN_H
+#define SCATMAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SCATMAN_API __attribute__((visibility("default")))
+#else
+#define SCATMAN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SCATMAN_OK = 0,
+    SCATMAN_ERR_ARG = -1,         /* invalid argument or unsupported size */
+    SCATMAN_ERR_OOM = -2,         /* a device or host allocation failed */
+    SCATMAN_ERR_CUDA = -3,        /* a CUDA runtime/driver call failed */
+    SCATMAN_ERR_TIMEOUT = -4,     /* a kernel gave up a bounded wait; results invalid */
+    SCATMAN_ERR_ADMISSION = -5,   /* serving: request exceeds the memory budget */
+    SCATMAN_ERR_STATE = -6,       /* call out of order (e.g. forward before voxelise) */
+    SCATMAN_ERR_UNSUPPORTED = -7  /* no device of compute capability 10.3 */
+} scatman_status;
+
+/* Arithmetic of the Fourier contraction (Eq. 9's per-slice sum). */
+typedef enum {
+    SCATMAN_FP64 = 0,          /* CUDA-core FP64 direct sum; FP64 scan; I and A in double */
+    SCATMAN_FP32 = 1,          /* CUDA-core FP32 direct sum; I float, A float2 */
+    SCATMAN_TC_F16_SPLIT = 2,  /* tcgen05, f16 operands, phases split hi+lo, FP32 accumulate */
+    SCATMAN_TC_BF16_SPLIT = 3, /* tcgen05, bf16 operands, phases split hi+lo, FP32 accumulate */
+    SCATMAN_TC_F16 = 4,        /* tcgen05, f16 operands, single phase product */
+    SCATMAN_TC_BF16 = 5        /* tcgen05, bf16 operands, single phase product */
+} scatman_precision;
+
+enum { SCATMAN_SPHERE = 0, SCATMAN_ELLIPSOID = 1, SCATMAN_SPHHARM = 2 };
+
+/* Maximum harmonic degree accepted for SCATMAN_SPHHARM. */
+#define SCATMAN_MAX_LMAX 12
+
+/*
+ * Experiment and grid (Sec. 3.1, Blocks 1-3; Listing 1 set_experiment).
+ *  nx, ny, nz      voxel grid (each >= 1, nz <= 256; tensor-core modes need
+ *                  nx <= 128 and, with split phases, ny <= 128)
+ *  voxel           voxel edge and slice thickness dz, same length unit as wavelength
+ *  wavelength      lambda; k0 = 2 pi / lambda
+ *  theta_max_deg   scattering angle at the detector's edge midpoints, (0, 90)
+ *  det_nx, det_ny  detector pixels (>= 1)
+ *  q_list, n_q     optional host array of n_q (q_x, q_y, q_z) triples that
+ *                  replaces the flat detector (copied during scatman_create);
+ *                  NULL/0 selects the detector
+ *  precision       scatman_precision
+ *  soft            0: binary occupancy (voxel centre inside, ties inside);
+ *                  1: logistic occupancy sigmoid((r_s - |p|)/soft_width)
+ *  soft_width      logistic width in length units (> 0 when soft)
+ *  scan_fp64       1 forces the transmission scan into FP64 (always on in
+ *                  SCATMAN_FP64; switched on automatically when
+ *                  k0 * voxel * nz * max(delta, beta) > 5)
+ */
+typedef struct {
+    int nx, ny, nz;
+    double voxel;
+    double wavelength;
+    double theta_max_deg;
+    int det_nx, det_ny;
+    const double *q_list;
+    long long n_q;
+    int precision;
+    int soft;
+    double soft_width;
+    int scan_fp64;
+} scatman_config;
+
+/*
+ * Shape (Sec. 5.1-5.2, Listings 1-2; orientation as in Fig. 6).
+ *  kind            SCATMAN_SPHERE (r), SCATMAN_ELLIPSOID (a, b, c; c lies on
+ *                  the main axis), SCATMAN_SPHHARM (R0, lmax, alm)
+ *  alm             (lmax+1)^2 real coefficients indexed l*l+l+m; alm[0] is
+ *                  ignored; radius r(theta,phi) = R0 (1 + sum_{l>=1} a_lm Y_lm)
+ *                  with real orthonormal harmonics (Eq. 10-11), clipped to
+ *                  [0.1 R0, grid half-width - voxel]
+ *  delta, beta     n = 1 - delta + i beta (Eq. 7)
+ *  latitude, longitude, rotation   degrees: the main axis points to
+ *                  (lat, lon) with +90 deg towards the source (-z); the body
+ *                  then spins by `rotation` about that axis
+ *  cx, cy, cz      centre offset from the grid centre, length units
+ */
+typedef struct {
+    int kind;
+    double r, a, b, c;
+    double R0;
+    int lmax;
+    const double *alm;
+    double delta, beta;
+    double latitude, longitude, rotation;
+    double cx, cy, cz;
+} scatman_shape;
+
+typedef struct scatman_handle scatman_handle;
+
+/*
+ * Creates a handle on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL: the library creates and owns a stream).  Allocates the
+ * occupancy, slice, field and reduction buffers for the given sizes and
+ * computes every pixel's q (Eq. 3).  The handle owns its device buffers;
+ * free them with scatman_destroy.
+ * Errors: ERR_ARG (bad sizes or angles), ERR_UNSUPPORTED (device is not
+ * sm_103), ERR_OOM, ERR_CUDA.  On error *out is NULL.
+ */
+SCATMAN_API int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle **out);
+
+/*
+ * Block 5 + Block 9 (Sec. 3.2), Eq. 8: renders the shape's occupancy chi on
+ * the grid and runs the exclusive transmission scan along z, storing
+ * s_j = chi_j T_j in the layout the selected contraction reads.  The shape
+ * (including a copy of alm) is kept for scatman_backward.  Asynchronous.
+ * Errors: ERR_ARG (unknown kind, non-positive size, lmax > SCATMAN_MAX_LMAX,
+ * NULL alm), ERR_CUDA.
+ */
+SCATMAN_API int scatman_voxelise(scatman_handle *h, const scatman_shape *shape);
+
+/*
+ * Eq. 9 and Block 11: A(q) for every pixel and I = |A|^2.
+ *  I_dev  caller-owned device array of n_pix elements: double in
+ *         SCATMAN_FP64, float otherwise
+ *  A_dev  optional caller-owned device array of n_pix complex values
+ *         (interleaved re, im; double in SCATMAN_FP64, float otherwise);
+ *         NULL skips it.  The handle keeps its own copy of A for backward.
+ * Asynchronous.  Errors: ERR_STATE (no voxelise yet), ERR_ARG, ERR_CUDA.
+ */
+SCATMAN_API int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev);
+
+/*
+ * End-to-end acquisition with host memory (the paper's detector.acquire,
+ * Listing 1): voxelise, forward, then copy I to the caller's host array
+ * (n_pix elements, same element type as scatman_forward).  Synchronises
+ * the stream.  Errors as voxelise/forward, plus ERR_TIMEOUT.
+ */
+SCATMAN_API int scatman_acquire(scatman_handle *h, const scatman_shape *shape, void *I_host);
+
+/*
+ * Gradient of a real loss L(I) with respect to the shape parameters, given
+ * dL/dI on every pixel (device array, n_pix elements, same element type as
+ * I), for the shape of the last scatman_voxelise and the field of the last
+ * scatman_forward (soft occupancy is required for the geometric terms).
+ * Writes scatman_param_count() doubles to the host array dLdparams in the
+ * order: sphere [r, delta, beta]; ellipsoid [a, b, c, delta, beta];
+ * harmonics [a_lm for l >= 1 in index order, R0, delta, beta].
+ * Recomputes occupancy and transmission instead of storing them.
+ * Synchronises the stream.  Errors: ERR_STATE (no forward yet), ERR_CUDA,
+ * ERR_TIMEOUT.
+ */
+SCATMAN_API int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams);
+
+/* Number of gradient entries for the current shape (0 before voxelise). */
+SCATMAN_API int scatman_param_count(const scatman_handle *h);
+
+/* Number of detector pixels (or q points) of the handle. */
+SCATMAN_API long long scatman_n_pix(const scatman_handle *h);
+
+/* Bytes per element of I (8 in SCATMAN_FP64, 4 otherwise). */
+SCATMAN_API int scatman_elem_size(const scatman_handle *h);
+
+/* Device bytes held by the handle (buffers only). */
+SCATMAN_API long long scatman_device_bytes(const scatman_handle *h);
+
+/*
+ * Waits for the handle's stream and checks the kernels' error word.
+ * Returns ERR_TIMEOUT if a kernel gave up a bounded wait, ERR_CUDA on a
+ * CUDA error, OK otherwise.
+ */
+SCATMAN_API int scatman_sync(scatman_handle *h);
+
+/* Inspection (tests): copy chi ([z][x][y], double, n_vox), the stored slices
+ * s = chi*T ([z][x][y], interleaved complex double, without the n^2-1
+ * factor) or the pixels' q ([pixel][3] double) to host memory.  Synchronise. */
+SCATMAN_API int scatman_get_occupancy(scatman_handle *h, double *chi_host);
+SCATMAN_API int scatman_get_slices(scatman_handle *h, double *s_host);
+SCATMAN_API int scatman_get_q(scatman_handle *h, double *q_host);
+
+/* Text of the last error on this handle ("" if none), owned by the handle.
+ * With h == NULL: the reason the calling thread's last scatman_create failed. */
+SCATMAN_API const char *scatman_last_error(const scatman_handle *h);
+
+/* Releases every buffer and the owned stream.  Accepts NULL. */
+SCATMAN_API void scatman_destroy(scatman_handle *h);
+
+/* Library version string. */
+SCATMAN_API const char *scatman_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCATMAN_H */

@@ -1,0 +1,19 @@
+"""GB300 (sm_103a) implementation of the Scatman's Multi-Slice Fourier Transform.
+
+The computation lives in ``libscatman.so`` (CUDA kernels behind the C ABI of
+include/scatman.h); this package is its thin Python binding.  Importing it does
+not load the library; the first call does, and fails loudly if the library has
+not been built (``paper_2202_03411_gb300.build.build()``).
+"""
+from . import _lib
+from .api import (Handle, ScatmanError, scatman_acquire, scatman_backward, scatman_create, scatman_destroy,
+                  scatman_device_bytes, scatman_elem_size, scatman_forward, scatman_get_occupancy,
+                  scatman_get_q, scatman_get_slices, scatman_last_error, scatman_n_pix, scatman_param_count,
+                  scatman_sync, scatman_version, scatman_voxelise)
+
+__all__ = [
+    "Handle", "ScatmanError", "scatman_acquire", "scatman_backward", "scatman_create", "scatman_destroy",
+    "scatman_device_bytes", "scatman_elem_size", "scatman_forward", "scatman_get_occupancy", "scatman_get_q",
+    "scatman_get_slices", "scatman_last_error", "scatman_n_pix", "scatman_param_count", "scatman_sync",
+    "scatman_version", "scatman_voxelise",
+]

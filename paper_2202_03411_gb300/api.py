@@ -1,0 +1,189 @@
+"""Thin Python binding of the C ABI, one function per C entry point.
+
+Device memory and streams come from PyTorch (tensors' data pointers and
+``torch.cuda.current_stream()``); every step of the computation runs in the
+library's CUDA kernels.  Errors raise ``ScatmanError`` carrying the status
+code and the library's message.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+from ._lib import scatman_config, scatman_shape
+
+
+class ScatmanError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _check(code: int, handle: Optional["Handle"] = None, what: str = ""):
+    if code != 0:
+        msg = ""
+        if handle is not None and handle.ptr:
+            msg = _lib.load().scatman_last_error(handle.ptr).decode()
+        raise ScatmanError(code, f"{what}: {msg}" if what else msg)
+
+
+class Handle:
+    """Owns a scatman_handle*; keeps the q list and alm buffers alive."""
+
+    def __init__(self, ptr: int, precision: int):
+        self.ptr = ctypes.c_void_p(ptr)
+        self.precision = precision
+        self._keep = []
+
+    @property
+    def fp64(self) -> bool:
+        return self.precision == _lib.SCATMAN_FP64
+
+    def close(self):
+        if self.ptr:
+            _lib.load().scatman_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def make_config(geometry, precision, soft: bool = False, soft_width: float = 0.5, scan_fp64: bool = False,
+                q_list: Optional[np.ndarray] = None):
+    g = geometry
+    cfg = scatman_config()
+    cfg.nx, cfg.ny, cfg.nz = g.nx, g.ny, g.nz
+    cfg.voxel, cfg.wavelength, cfg.theta_max_deg = g.voxel, g.wavelength, g.theta_max_deg
+    cfg.det_nx, cfg.det_ny = g.det_nx, g.det_ny
+    keep = None
+    if q_list is not None:
+        keep = np.ascontiguousarray(q_list, dtype=np.float64)
+        cfg.q_list = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        cfg.n_q = keep.shape[0]
+    cfg.precision = _lib.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    cfg.soft = int(bool(soft))
+    cfg.soft_width = float(soft_width)
+    cfg.scan_fp64 = int(bool(scan_fp64))
+    return cfg, keep
+
+
+def make_shape(shape):
+    st = scatman_shape()
+    st.kind = shape.kind
+    st.r, st.a, st.b, st.c, st.R0 = shape.r, shape.a, shape.b, shape.c, shape.R0
+    st.lmax = shape.lmax
+    alm = shape.alm_array()
+    st.alm = alm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st.delta, st.beta = shape.delta, shape.beta
+    st.latitude, st.longitude, st.rotation = shape.latitude, shape.longitude, shape.rotation
+    st.cx, st.cy, st.cz = shape.cx, shape.cy, shape.cz
+    return st, alm
+
+
+def scatman_create(geometry, precision, soft: bool = False, soft_width: float = 0.5, scan_fp64: bool = False,
+                   q_list: Optional[np.ndarray] = None, stream: Optional[int] = None) -> Handle:
+    """scatman_create: the stream defaults to torch's current CUDA stream."""
+    lib = _lib.load()
+    cfg, keep = make_config(geometry, precision, soft, soft_width, scan_fp64, q_list)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+        if stream == 0:
+            stream = 1          # cudaStreamLegacy: torch's default stream, not a library-owned one
+    out = ctypes.c_void_p()
+    code = lib.scatman_create(ctypes.byref(cfg), ctypes.c_void_p(stream), ctypes.byref(out))
+    if code != 0:
+        raise ScatmanError(code, "scatman_create: " + lib.scatman_last_error(None).decode())
+    h = Handle(out.value, cfg.precision)
+    h._keep.append(keep)
+    return h
+
+
+def scatman_voxelise(h: Handle, shape) -> None:
+    st, alm = make_shape(shape)
+    _check(_lib.load().scatman_voxelise(h.ptr, ctypes.byref(st)), h, "voxelise")
+
+
+def scatman_forward(h: Handle, I, A=None) -> None:
+    """I, A: CUDA tensors (float64/complex128 in FP64 mode, float32/complex64 otherwise)."""
+    _check(_lib.load().scatman_forward(h.ptr, ctypes.c_void_p(I.data_ptr()),
+                                       ctypes.c_void_p(A.data_ptr() if A is not None else None)), h, "forward")
+
+
+def scatman_acquire(h: Handle, shape, I_host) -> None:
+    """I_host: numpy array or pinned CPU tensor of n_pix elements."""
+    st, alm = make_shape(shape)
+    ptr = I_host.ctypes.data if isinstance(I_host, np.ndarray) else I_host.data_ptr()
+    _check(_lib.load().scatman_acquire(h.ptr, ctypes.byref(st), ctypes.c_void_p(ptr)), h, "acquire")
+
+
+def scatman_backward(h: Handle, dLdI) -> np.ndarray:
+    lib = _lib.load()
+    n = lib.scatman_param_count(h.ptr)
+    out = np.zeros(n, dtype=np.float64)
+    _check(lib.scatman_backward(h.ptr, ctypes.c_void_p(dLdI.data_ptr()),
+                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), h, "backward")
+    return out
+
+
+def scatman_param_count(h: Handle) -> int:
+    return _lib.load().scatman_param_count(h.ptr)
+
+
+def scatman_n_pix(h: Handle) -> int:
+    return _lib.load().scatman_n_pix(h.ptr)
+
+
+def scatman_elem_size(h: Handle) -> int:
+    return _lib.load().scatman_elem_size(h.ptr)
+
+
+def scatman_device_bytes(h: Handle) -> int:
+    return _lib.load().scatman_device_bytes(h.ptr)
+
+
+def scatman_sync(h: Handle) -> None:
+    _check(_lib.load().scatman_sync(h.ptr), h, "sync")
+
+
+def scatman_get_occupancy(h: Handle, shape_zxy) -> np.ndarray:
+    out = np.zeros(shape_zxy, dtype=np.float64)
+    _check(_lib.load().scatman_get_occupancy(h.ptr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), h)
+    return out
+
+
+def scatman_get_slices(h: Handle, shape_zxy) -> np.ndarray:
+    buf = np.zeros(tuple(shape_zxy) + (2,), dtype=np.float64)
+    _check(_lib.load().scatman_get_slices(h.ptr, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), h)
+    return buf[..., 0] + 1j * buf[..., 1]
+
+
+def scatman_get_q(h: Handle) -> np.ndarray:
+    n = scatman_n_pix(h)
+    out = np.zeros((n, 3), dtype=np.float64)
+    _check(_lib.load().scatman_get_q(h.ptr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), h)
+    return out
+
+
+def scatman_destroy(h: Handle) -> None:
+    h.close()
+
+
+def scatman_version() -> str:
+    return _lib.load().scatman_version().decode()
+
+
+def scatman_last_error(h: Handle) -> str:
+    return _lib.load().scatman_last_error(h.ptr).decode()

@@ -1,0 +1,476 @@
+// api.cu -- the C ABI declared in include/scatman.h: handle lifecycle,
+// argument checks, buffer ownership and dispatch to the kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace scm {
+
+int set_error(scatman_handle *h, int code, const std::string &msg) {
+    if (h) h->last_error = msg;
+    return code;
+}
+
+int check_cuda(scatman_handle *h, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SCATMAN_OK;
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return set_error(h, SCATMAN_ERR_OOM, m);
+    return set_error(h, SCATMAN_ERR_CUDA, m);
+}
+
+static bool is_tc(int precision) { return precision >= SCATMAN_TC_F16_SPLIT && precision <= SCATMAN_TC_BF16; }
+
+// cos/sin of an angle in degrees, exact at multiples of 90 degrees.
+static void cos_sin_deg(double deg, double *c, double *s) {
+    double q = deg / 90.0;
+    if (q == std::floor(q)) {
+        long k = (((long)q) % 4 + 4) % 4;
+        const double cs[4] = {1, 0, -1, 0}, sn[4] = {0, 1, 0, -1};
+        *c = cs[k];
+        *s = sn[k];
+        return;
+    }
+    double r = deg * kPi / 180.0;
+    *c = std::cos(r);
+    *s = std::sin(r);
+}
+
+// Body->lab rotation for the orientation of Fig. 6: spin about the body z
+// axis by `rotation`, tilt body z by 90+latitude about y, turn by longitude
+// about the lab z axis.  Written as the product of the three matrices.
+static void orientation_matrix(double lat, double lon, double rot, double R[9]) {
+    double c1, s1, c2, s2, c3, s3;
+    cos_sin_deg(lon, &c1, &s1);
+    cos_sin_deg(90.0 + lat, &c2, &s2);
+    cos_sin_deg(rot, &c3, &s3);
+    // Rz(lon) * Ry(90+lat)
+    double M[9] = {c1 * c2, -s1, c1 * s2, s1 * c2, c1, s1 * s2, -s2, 0.0, c2};
+    // (.) * Rz(rot)
+    for (int i = 0; i < 3; ++i) {
+        double a = M[3 * i + 0], b = M[3 * i + 1], c = M[3 * i + 2];
+        R[3 * i + 0] = a * c3 + b * s3;
+        R[3 * i + 1] = -a * s3 + b * c3;
+        R[3 * i + 2] = c;
+    }
+}
+
+static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+}  // namespace scm
+
+using namespace scm;
+
+extern "C" {
+
+const char *scatman_version(void) { return "scatman-gb300 0.1 (sm_103a)"; }
+
+static thread_local std::string g_create_error;
+
+const char *scatman_last_error(const scatman_handle *h) { return h ? h->last_error.c_str() : g_create_error.c_str(); }
+
+long long scatman_n_pix(const scatman_handle *h) { return h ? h->n_pix : 0; }
+
+int scatman_elem_size(const scatman_handle *h) { return h && h->precision == SCATMAN_FP64 ? 8 : 4; }
+
+long long scatman_device_bytes(const scatman_handle *h) { return h ? h->device_bytes : 0; }
+
+int scatman_param_count(const scatman_handle *h) {
+    if (!h || !h->have_shape) return 0;
+    return grad_param_count(h->sp) + 2;
+}
+
+static int alloc_dev(scatman_handle *h, void **p, size_t bytes, const char *what) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return check_cuda(h, e, what);
+    }
+    h->device_bytes += (long long)bytes;
+    return SCATMAN_OK;
+}
+
+void scatman_destroy(scatman_handle *h) {
+    if (!h) return;
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_q);
+    cudaFree(h->d_chi);
+    cudaFree(h->d_s);
+    cudaFree(h->d_A);
+    cudaFree(h->d_I);
+    cudaFree(h->d_err);
+    cudaFree(h->d_part);
+    cudaFree(h->d_S);
+    cudaFree(h->d_partial);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (dev_prev >= 0) cudaSetDevice(dev_prev);
+    delete h;
+}
+
+int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle **out) {
+    if (!out) return SCATMAN_ERR_ARG;
+    *out = nullptr;
+    if (!cfg) return SCATMAN_ERR_ARG;
+    scatman_handle *h = new (std::nothrow) scatman_handle();
+    if (!h) return SCATMAN_ERR_OOM;
+    h->cfg = *cfg;
+    h->cfg.q_list = nullptr;
+    g_create_error.clear();
+    auto fail = [&](int code) {
+        g_create_error = h->last_error;   // readable through scatman_last_error(NULL)
+        scatman_destroy(h);
+        return code;
+    };
+    const scatman_config &c = *cfg;
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.nz > 256 || c.nx > 4096 || c.ny > 4096)
+        return fail(set_error(h, SCATMAN_ERR_ARG, "grid sizes must be >= 1 and nz <= 256"));
+    if (!(c.voxel > 0) || !(c.wavelength > 0))
+        return fail(set_error(h, SCATMAN_ERR_ARG, "voxel and wavelength must be positive"));
+    if (c.precision < SCATMAN_FP64 || c.precision > SCATMAN_TC_BF16)
+        return fail(set_error(h, SCATMAN_ERR_ARG, "unknown precision"));
+    if (c.soft && !(c.soft_width > 0))
+        return fail(set_error(h, SCATMAN_ERR_ARG, "soft occupancy needs soft_width > 0"));
+    if (cfg->q_list) {
+        if (cfg->n_q < 1) return fail(set_error(h, SCATMAN_ERR_ARG, "n_q must be >= 1 with q_list"));
+        h->n_pix = cfg->n_q;
+    } else {
+        if (c.det_nx < 1 || c.det_ny < 1) return fail(set_error(h, SCATMAN_ERR_ARG, "detector size must be >= 1"));
+        if (!(c.theta_max_deg > 0 && c.theta_max_deg < 90))
+            return fail(set_error(h, SCATMAN_ERR_ARG, "theta_max_deg must lie in (0, 90)"));
+        h->n_pix = (long long)c.det_nx * c.det_ny;
+    }
+    h->precision = c.precision;
+    h->tensor_core = is_tc(c.precision);
+    h->split = (c.precision == SCATMAN_TC_F16_SPLIT || c.precision == SCATMAN_TC_BF16_SPLIT);
+    h->bf16 = (c.precision == SCATMAN_TC_BF16_SPLIT || c.precision == SCATMAN_TC_BF16);
+    h->k0 = 2.0 * kPi / c.wavelength;
+
+    // device
+    if (cudaGetDevice(&h->device) != cudaSuccess)
+        return fail(set_error(h, SCATMAN_ERR_UNSUPPORTED, "no CUDA device"));
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, h->device) != cudaSuccess)
+        return fail(set_error(h, SCATMAN_ERR_UNSUPPORTED, "cannot query the CUDA device"));
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(set_error(h, SCATMAN_ERR_UNSUPPORTED,
+                              "this library is built for sm_103a (compute capability 10.3) only"));
+    h->sm_count = prop.multiProcessorCount;
+
+    if (h->tensor_core) {
+        h->Nxp = (int)round_up(c.nx, 16);
+        h->Nyp = (int)round_up(c.ny, 8);
+        h->Kp = 2 * h->Nyp;
+        if (h->Nxp > 128)
+            return fail(set_error(h, SCATMAN_ERR_ARG, "tensor-core modes support nx <= 128"));
+        if (tc_max_stages(h->Kp, h->Nxp, h->split) < 2)
+            return fail(set_error(h, SCATMAN_ERR_ARG, "ny too large for the tensor-core phase tile"));
+        h->b_rows = (size_t)c.nz * 2 * h->Nxp;
+    }
+
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(set_error(h, SCATMAN_ERR_CUDA, "cannot create a stream"));
+        h->own_stream = true;
+    }
+
+    const size_t nvox = (size_t)c.nx * c.ny * c.nz;
+    const size_t npix = (size_t)h->n_pix;
+    const bool f64 = (h->precision == SCATMAN_FP64);
+    int rc;
+    if ((rc = alloc_dev(h, (void **)&h->d_q, npix * 3 * sizeof(double), "q buffer"))) return fail(rc);
+    if ((rc = alloc_dev(h, (void **)&h->d_chi, nvox * sizeof(float), "occupancy buffer"))) return fail(rc);
+    if (h->tensor_core) {
+        h->s_bytes = h->b_rows * (size_t)h->Kp * 2;
+    } else {
+        h->s_bytes = nvox * (f64 ? sizeof(double2) : sizeof(float2));
+    }
+    if ((rc = alloc_dev(h, &h->d_s, h->s_bytes, "slice buffer"))) return fail(rc);
+    const size_t cx = f64 ? sizeof(double2) : sizeof(float2);
+    if ((rc = alloc_dev(h, &h->d_A, npix * cx, "field buffer"))) return fail(rc);
+    if ((rc = alloc_dev(h, &h->d_I, npix * (f64 ? 8 : 4), "intensity buffer"))) return fail(rc);
+    if ((rc = alloc_dev(h, (void **)&h->d_err, sizeof(int), "error word"))) return fail(rc);
+    if (!h->tensor_core) {
+        h->splits = simt_splits(h->n_pix, c.nx, c.nz, h->sm_count);
+        if ((rc = alloc_dev(h, &h->d_partial, (size_t)h->splits * npix * cx, "partial fields"))) return fail(rc);
+    }
+    if ((rc = check_cuda(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "memset"))) return fail(rc);
+    if ((rc = check_cuda(h, cudaMemsetAsync(h->d_s, 0, h->s_bytes, h->stream), "memset"))) return fail(rc);
+
+    if (cfg->q_list) {
+        rc = check_cuda(h, cudaMemcpyAsync(h->d_q, cfg->q_list, npix * 3 * sizeof(double), cudaMemcpyHostToDevice,
+                                           h->stream),
+                        "q upload");
+        if (rc) return fail(rc);
+        if ((rc = check_cuda(h, cudaStreamSynchronize(h->stream), "q upload"))) return fail(rc);
+    } else {
+        rc = check_cuda(h, launch_detector_q(c.det_nx, c.det_ny, c.theta_max_deg, h->k0, h->d_q, h->stream),
+                        "detector q");
+        if (rc) return fail(rc);
+    }
+    if (h->tensor_core) {
+        std::string why;
+        if (!encode_tmap_B(&h->tmap_B, h->d_s, h->Kp, h->b_rows, h->Nxp, h->bf16, &why))
+            return fail(set_error(h, SCATMAN_ERR_CUDA, why));
+        h->have_tmap = true;
+    }
+    *out = h;
+    return SCATMAN_OK;
+}
+
+int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
+    if (!h || !s) return SCATMAN_ERR_ARG;
+    const scatman_config &c = h->cfg;
+    if (s->kind < SCATMAN_SPHERE || s->kind > SCATMAN_SPHHARM)
+        return set_error(h, SCATMAN_ERR_ARG, "unknown shape kind");
+    if (s->kind == SCATMAN_SPHERE && !(s->r > 0)) return set_error(h, SCATMAN_ERR_ARG, "sphere radius must be > 0");
+    if (s->kind == SCATMAN_ELLIPSOID && !(s->a > 0 && s->b > 0 && s->c > 0))
+        return set_error(h, SCATMAN_ERR_ARG, "ellipsoid semi-axes must be > 0");
+    if (s->kind == SCATMAN_SPHHARM) {
+        if (!(s->R0 > 0)) return set_error(h, SCATMAN_ERR_ARG, "R0 must be > 0");
+        if (s->lmax < 0 || s->lmax > SCATMAN_MAX_LMAX) return set_error(h, SCATMAN_ERR_ARG, "lmax out of range");
+        if (s->lmax > 0 && !s->alm) return set_error(h, SCATMAN_ERR_ARG, "alm is NULL");
+    }
+    if (!std::isfinite(s->delta) || !std::isfinite(s->beta))
+        return set_error(h, SCATMAN_ERR_ARG, "delta and beta must be finite");
+
+    h->shape = *s;
+    h->alm.assign((size_t)(s->kind == SCATMAN_SPHHARM ? (s->lmax + 1) * (s->lmax + 1) : 0), 0.0);
+    if (s->kind == SCATMAN_SPHHARM && s->lmax > 0)
+        std::memcpy(h->alm.data(), s->alm, sizeof(double) * h->alm.size());
+    h->shape.alm = h->alm.empty() ? nullptr : h->alm.data();
+
+    ShapeParams &sp = h->sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.kind = s->kind;
+    sp.lmax = s->kind == SCATMAN_SPHHARM ? s->lmax : 0;
+    sp.soft = c.soft ? 1 : 0;
+    sp.inv_w = c.soft ? 1.0 / c.soft_width : 0.0;
+    sp.inv_w_f = (float)sp.inv_w;
+    sp.r = s->r;
+    sp.a = s->a;
+    sp.b = s->b;
+    sp.c = s->c;
+    sp.R0 = s->R0;
+    int nmin = c.nx < c.ny ? c.nx : c.ny;
+    if (c.nz < nmin) nmin = c.nz;
+    sp.rmin = 0.1 * s->R0;
+    sp.rmax = 0.5 * (nmin - 1) * c.voxel - c.voxel;
+    orientation_matrix(s->latitude, s->longitude, s->rotation, sp.R);
+    sp.cx = s->cx;
+    sp.cy = s->cy;
+    sp.cz = s->cz;
+    for (size_t k = 0; k < h->alm.size(); ++k) sp.alm[k] = h->alm[k];
+
+    GridParams gp{c.nx, c.ny, c.nz, c.voxel, h->k0, s->delta, s->beta};
+    SliceOut so;
+    so.layout = h->precision == SCATMAN_FP64 ? kLayoutC64
+                : h->precision == SCATMAN_FP32 ? kLayoutC32
+                : h->bf16 ? kLayoutTcBF16 : kLayoutTcF16;
+    so.Nxp = h->Nxp;
+    so.Nyp = h->Nyp;
+    so.Kp = h->Kp;
+    so.s = h->d_s;
+    so.chi = h->d_chi;
+    double strength = std::fmax(std::fabs(s->delta), std::fabs(s->beta));
+    h->scan_fp64 = c.scan_fp64 || (h->k0 * c.voxel * c.nz * strength > 5.0);
+    int rc = check_cuda(h, launch_voxelise(sp, gp, so, h->scan_fp64, h->precision == SCATMAN_FP64, h->stream),
+                        "voxelise");
+    if (rc) return rc;
+    h->have_shape = true;
+    h->have_forward = false;
+    return SCATMAN_OK;
+}
+
+int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
+    if (!h || !I_dev) return set_error(h, SCATMAN_ERR_ARG, "I_dev is NULL");
+    if (!h->have_shape) return set_error(h, SCATMAN_ERR_STATE, "forward before voxelise");
+    const scatman_config &c = h->cfg;
+    const double d = h->shape.delta, b = h->shape.beta;
+    // n^2 - 1 with n = 1 - delta + i beta
+    const double str_re = -2.0 * d + d * d - b * b;
+    const double str_im = 2.0 * b - 2.0 * d * b;
+    cudaError_t e;
+    if (h->tensor_core) {
+        e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, h->Kp, c.voxel, str_re,
+                           str_im, h->split, h->bf16, (float2 *)h->d_A, (float *)I_dev, h->d_err, h->sm_count,
+                           h->stream);
+    } else {
+        e = launch_msft_simt(h->precision == SCATMAN_FP64, h->d_s, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
+                             str_re, str_im, h->d_A, I_dev, h->d_partial, h->splits, h->stream);
+    }
+    int rc = check_cuda(h, e, "forward");
+    if (rc) return rc;
+    if (A_dev) {
+        size_t cx = h->precision == SCATMAN_FP64 ? sizeof(double2) : sizeof(float2);
+        rc = check_cuda(h, cudaMemcpyAsync(A_dev, h->d_A, (size_t)h->n_pix * cx, cudaMemcpyDeviceToDevice, h->stream),
+                        "field copy");
+        if (rc) return rc;
+    }
+    h->have_forward = true;
+    return SCATMAN_OK;
+}
+
+int scatman_sync(scatman_handle *h) {
+    if (!h) return SCATMAN_ERR_ARG;
+    int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (rc) return rc;
+    int err = 0;
+    rc = check_cuda(h, cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    if (rc) return rc;
+    if (err) {
+        cudaMemset(h->d_err, 0, sizeof(int));
+        return set_error(h, SCATMAN_ERR_TIMEOUT,
+                         "a kernel gave up a bounded wait (error bits " + std::to_string(err) + ")");
+    }
+    return SCATMAN_OK;
+}
+
+int scatman_acquire(scatman_handle *h, const scatman_shape *shape, void *I_host) {
+    if (!h || !shape || !I_host) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
+    int rc = scatman_voxelise(h, shape);
+    if (rc) return rc;
+    rc = scatman_forward(h, h->d_I, nullptr);
+    if (rc) return rc;
+    rc = check_cuda(h, cudaMemcpyAsync(I_host, h->d_I, (size_t)h->n_pix * scatman_elem_size(h),
+                                       cudaMemcpyDeviceToHost, h->stream),
+                    "intensity download");
+    if (rc) return rc;
+    return scatman_sync(h);
+}
+
+int scatman_get_occupancy(scatman_handle *h, double *chi_host) {
+    if (!h || !chi_host) return SCATMAN_ERR_ARG;
+    if (!h->have_shape) return set_error(h, SCATMAN_ERR_STATE, "no voxelised shape");
+    const scatman_config &c = h->cfg;
+    size_t nvox = (size_t)c.nx * c.ny * c.nz;
+    std::vector<float> tmp(nvox);
+    int rc = check_cuda(h, cudaMemcpyAsync(tmp.data(), h->d_chi, nvox * sizeof(float), cudaMemcpyDeviceToHost,
+                                           h->stream),
+                        "occupancy download");
+    if (rc) return rc;
+    if ((rc = scatman_sync(h))) return rc;
+    for (size_t i = 0; i < nvox; ++i) chi_host[i] = tmp[i];
+    return SCATMAN_OK;
+}
+
+static float half_bits_to_float(uint16_t u, bool bf16) {
+    if (bf16) {
+        uint32_t w = (uint32_t)u << 16;
+        float f;
+        std::memcpy(&f, &w, 4);
+        return f;
+    }
+    __half_raw r;
+    r.x = u;
+    return __half2float(__half(r));
+}
+
+int scatman_get_slices(scatman_handle *h, double *s_host) {
+    if (!h || !s_host) return SCATMAN_ERR_ARG;
+    if (!h->have_shape) return set_error(h, SCATMAN_ERR_STATE, "no voxelised shape");
+    const scatman_config &c = h->cfg;
+    size_t nvox = (size_t)c.nx * c.ny * c.nz;
+    std::vector<unsigned char> tmp(h->s_bytes);
+    int rc = check_cuda(h, cudaMemcpyAsync(tmp.data(), h->d_s, h->s_bytes, cudaMemcpyDeviceToHost, h->stream),
+                        "slice download");
+    if (rc) return rc;
+    if ((rc = scatman_sync(h))) return rc;
+    if (h->precision == SCATMAN_FP64) {
+        std::memcpy(s_host, tmp.data(), nvox * sizeof(double2));
+    } else if (h->precision == SCATMAN_FP32) {
+        const float *f = (const float *)tmp.data();
+        for (size_t i = 0; i < 2 * nvox; ++i) s_host[i] = f[i];
+    } else {
+        const uint16_t *B = (const uint16_t *)tmp.data();
+        for (int iz = 0; iz < c.nz; ++iz)
+            for (int ix = 0; ix < c.nx; ++ix)
+                for (int iy = 0; iy < c.ny; ++iy) {
+                    size_t row_r = (size_t)iz * 2 * h->Nxp + ix;
+                    size_t v = ((size_t)iz * c.nx + ix) * c.ny + iy;
+                    s_host[2 * v] = half_bits_to_float(B[row_r * h->Kp + iy], h->bf16);
+                    s_host[2 * v + 1] = half_bits_to_float(B[(row_r + h->Nxp) * h->Kp + iy], h->bf16);
+                }
+    }
+    return SCATMAN_OK;
+}
+
+int scatman_get_q(scatman_handle *h, double *q_host) {
+    if (!h || !q_host) return SCATMAN_ERR_ARG;
+    int rc = check_cuda(h, cudaMemcpyAsync(q_host, h->d_q, (size_t)h->n_pix * 3 * sizeof(double),
+                                           cudaMemcpyDeviceToHost, h->stream),
+                        "q download");
+    if (rc) return rc;
+    return scatman_sync(h);
+}
+
+int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams) {
+    if (!h || !dLdI_dev || !dLdparams) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
+    if (!h->have_forward) return set_error(h, SCATMAN_ERR_STATE, "backward before forward");
+    const scatman_config &c = h->cfg;
+    const bool f64 = h->precision == SCATMAN_FP64;
+    const size_t nvox = (size_t)c.nx * c.ny * c.nz;
+    int rc;
+    if (!h->d_S) {
+        if ((rc = alloc_dev(h, &h->d_S, nvox * (f64 ? sizeof(double2) : sizeof(float2)), "adjoint field")))
+            return rc;
+    }
+    GridParams gp{c.nx, c.ny, c.nz, c.voxel, h->k0, h->shape.delta, h->shape.beta};
+    const int ng = grad_param_count(h->sp);
+    const int nvb = grad_voxel_blocks(gp), npb = grad_pixel_blocks(h->n_pix);
+    const size_t need = (size_t)nvb * (ng + 2) + (size_t)npb;
+    if (h->part_count < need) {
+        cudaFree(h->d_part);
+        h->d_part = nullptr;
+        if ((rc = alloc_dev(h, (void **)&h->d_part, need * sizeof(double), "gradient partials"))) return rc;
+        h->part_count = need;
+    }
+    rc = check_cuda(h, launch_adjoint_field(f64, h->d_A, dLdI_dev, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
+                                            h->d_S, h->stream),
+                    "adjoint field");
+    if (rc) return rc;
+    rc = check_cuda(h, launch_grad_voxels(f64, h->sp, gp, h->d_S, h->d_part, nvb, h->stream), "voxel gradient");
+    if (rc) return rc;
+    rc = check_cuda(h, launch_grad_pixels(f64, h->d_A, dLdI_dev, h->n_pix, h->d_part + (size_t)nvb * (ng + 2), npb,
+                                          h->stream),
+                    "pixel gradient");
+    if (rc) return rc;
+    std::vector<double> part(need);
+    rc = check_cuda(h, cudaMemcpyAsync(part.data(), h->d_part, need * sizeof(double), cudaMemcpyDeviceToHost,
+                                       h->stream),
+                    "gradient download");
+    if (rc) return rc;
+    if ((rc = scatman_sync(h))) return rc;
+    // fixed-order sums of the per-block partials
+    std::vector<double> sums(ng + 2, 0.0);
+    for (int b = 0; b < nvb; ++b)
+        for (int k = 0; k < ng + 2; ++k) sums[k] += part[(size_t)b * (ng + 2) + k];
+    double wI = 0.0;
+    for (int b = 0; b < npb; ++b) wI += part[(size_t)nvb * (ng + 2) + b];
+    // n, c = n^2 - 1 and their derivatives in delta, beta
+    const double d = h->shape.delta, bb = h->shape.beta;
+    const double nr = 1.0 - d, ni = bb;
+    const double cr = nr * nr - ni * ni - 1.0, ci = 2.0 * nr * ni;
+    const double cc = cr * cr + ci * ci;
+    // dc/ddelta = -2n, dc/dbeta = 2 i n;  2 Re[(c'/c) wI]
+    auto re_ratio = [&](double ar, double ai) { return (ar * cr + ai * ci) / cc; };
+    const double g_delta_c = 2.0 * re_ratio(-2.0 * nr, -2.0 * ni) * wI;
+    const double g_beta_c = 2.0 * re_ratio(-2.0 * ni, 2.0 * nr) * wI;
+    // D = sum_v R_v s_v C_v (complex); d(n-1)/ddelta = -1, d(n-1)/dbeta = i; term 2 Re(D i k0 dz d(n-1))
+    const double Dr = sums[ng], Di = sums[ng + 1];
+    const double kdz = h->k0 * c.voxel;
+    const double g_delta_n = 2.0 * (Di * kdz);       // Re(D * i * kdz * -1) = Di kdz
+    const double g_beta_n = 2.0 * (-Dr * kdz);       // Re(D * i * kdz * i) = -Dr kdz
+    for (int k = 0; k < ng; ++k) dLdparams[k] = 2.0 * sums[k];
+    dLdparams[ng] = g_delta_c + g_delta_n;
+    dLdparams[ng + 1] = g_beta_c + g_beta_n;
+    return SCATMAN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,196 @@
+// internal.cuh -- declarations shared by the library's translation units.
+// Not installed; the public surface is include/scatman.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/scatman.h"
+
+namespace scm {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Bits of the device error word written by kernels.
+enum : int {
+    kErrTimeoutProducer = 1,
+    kErrTimeoutMma = 2,
+    kErrTimeoutEpilogue = 4,
+    kErrTimeoutDrain = 8,
+    kErrBadLaunch = 16,
+};
+
+// Shape as the voxeliser kernels read it: body->lab rotation, centre, sizes
+// and harmonic coefficients, everything in length units.
+struct ShapeParams {
+    int kind;
+    int lmax;
+    int soft;
+    float inv_w_f;
+    double inv_w;
+    double r, a, b, c;
+    double R0;
+    double rmin, rmax;              // harmonics radius clip
+    double R[9];                    // row-major body->lab rotation
+    double cx, cy, cz;              // centre offset
+    double alm[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1)];
+};
+
+// Number of geometric gradient parameters: sphere [r]; ellipsoid [a, b, c];
+// harmonics [a_lm for l >= 1, R0].
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int n_geom_params(int kind, int lmax) {
+    if (kind == SCATMAN_SPHERE) return 1;
+    if (kind == SCATMAN_ELLIPSOID) return 3;
+    return (lmax + 1) * (lmax + 1);
+}
+
+struct GridParams {
+    int nx, ny, nz;
+    double voxel;
+    double k0;
+    double delta, beta;
+};
+
+// Where the voxeliser writes s = chi*T.
+enum SliceLayout { kLayoutC64 = 0, kLayoutC32 = 1, kLayoutTcF16 = 2, kLayoutTcBF16 = 3 };
+
+struct SliceOut {
+    int layout;
+    int Nxp, Nyp, Kp;               // tensor-core operand: padded x, y and K = 2*Nyp
+    void *s;                        // C64: double2[nvox]; C32: float2[nvox]; TC: 16-bit [nz*2*Nxp][Kp]
+    float *chi;                     // occupancy [z][x][y]
+};
+
+}  // namespace scm
+
+struct scatman_handle {
+    scatman_config cfg;
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    long long n_pix = 0;
+    double k0 = 0;
+    int precision = 0;
+    bool tensor_core = false;
+    bool split = false;
+    bool bf16 = false;
+    bool scan_fp64 = false;
+    // tensor-core operand geometry
+    int Nxp = 0, Nyp = 0, Kp = 0;
+    size_t b_rows = 0;
+    // device buffers
+    double *d_q = nullptr;          // [n_pix][3]
+    float *d_chi = nullptr;         // [nvox]
+    void *d_s = nullptr;            // slices in the contraction's layout
+    size_t s_bytes = 0;
+    void *d_A = nullptr;            // field cache (double2 or float2)
+    void *d_I = nullptr;            // intensity scratch for acquire
+    int *d_err = nullptr;
+    double *d_part = nullptr;       // backward partial sums
+    size_t part_count = 0;
+    void *d_S = nullptr;            // backward adjoint field (complex, nvox)
+    void *d_partial = nullptr;      // CUDA-core contraction: per-split partial fields
+    int splits = 1;
+    long long device_bytes = 0;
+    CUtensorMap tmap_B;
+    bool have_tmap = false;
+    // state
+    bool have_shape = false;
+    bool have_forward = false;
+    scatman_shape shape;
+    std::vector<double> alm;
+    scm::ShapeParams sp;
+    std::string last_error;
+};
+
+namespace scm {
+
+// ---- host helpers shared by the .cu files --------------------------------
+int set_error(scatman_handle *h, int code, const std::string &msg);
+int check_cuda(scatman_handle *h, cudaError_t e, const char *what);
+
+// Voxeliser + exclusive scan (voxelise.cu).
+cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const SliceOut &out,
+                            bool scan_fp64, bool fp64_mode, cudaStream_t st);
+// Detector q (voxelise.cu).
+cudaError_t launch_detector_q(int det_nx, int det_ny, double theta_max_deg, double k0, double *q,
+                              cudaStream_t st);
+// CUDA-core contraction (msft_simt.cu).
+int simt_splits(long long n_pix, int nx, int nz, int sm_count);
+cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long long n_pix, int nx, int ny,
+                             int nz, double voxel, double str_re, double str_im, void *A, void *I,
+                             void *partial, int splits, cudaStream_t st);
+// Tensor-core contraction (msft_tc.cu).
+int tc_max_stages(int Kp, int Nxp, bool split);
+cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n_pix, int nx, int ny,
+                           int nz, int Nxp, int Nyp, int Kp, double voxel, double str_re, double str_im,
+                           bool split, bool bf16, float2 *A, float *I, int *err, int sm_count,
+                           cudaStream_t st);
+bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, bool bf16, std::string *why);
+// Backward (adjoint.cu).
+cudaError_t launch_adjoint_field(bool fp64, const void *A, const void *dLdI, const double *q, long long n_pix,
+                                 int nx, int ny, int nz, double voxel, void *S, cudaStream_t st);
+int grad_param_count(const ShapeParams &sp);
+cudaError_t launch_grad_voxels(bool fp64, const ShapeParams &sp, const GridParams &gp, const void *S,
+                               double *partials, int n_blocks, cudaStream_t st);
+int grad_voxel_blocks(const GridParams &gp);
+cudaError_t launch_grad_pixels(bool fp64, const void *A, const void *dLdI, long long n_pix,
+                               double *partials, int n_blocks, cudaStream_t st);
+int grad_pixel_blocks(long long n_pix);
+
+}  // namespace scm
+
+// ---- device helpers ---------------------------------------------------------
+#ifdef __CUDACC__
+namespace scm {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// e^{-i q c} for a q held in double and a coordinate c that is a small
+// multiple of the voxel: the argument q*c is formed as a float pair
+// (FMA-exact product of the high part plus the low part's product) and
+// reduced modulo 2 pi in two pieces (Cody-Waite), so the reduced angle is
+// good to ~1e-7 rad even for |q c| of a few hundred radians.
+__device__ __forceinline__ float2 expmi_fs(float qh, float ql, float cf) {
+    const float kTwoPiHi = 6.28318548202514648f;
+    const float kTwoPiLo = -1.7484555314695172e-07f;
+    const float kInvTwoPi = 0.15915494309189535f;
+    float p = qh * cf;
+    float e = fmaf(qh, cf, -p);
+    float lo = fmaf(ql, cf, e);
+    float n = rintf(p * kInvTwoPi);
+    float r = fmaf(-n, kTwoPiHi, p);
+    r = r + fmaf(-n, kTwoPiLo, lo);
+    float s, co;
+    sincosf(r, &s, &co);
+    return make_float2(co, -s);
+}
+
+__device__ __forceinline__ float2 expmi_f(double q, double c) {
+    float qh = (float)q;
+    float ql = (float)(q - (double)qh);
+    return expmi_fs(qh, ql, (float)c);
+}
+
+__device__ __forceinline__ double2 expmi_d(double q, double c) {
+    double s, co;
+    sincos(q * c, &s, &co);
+    return make_double2(co, -s);
+}
+
+}  // namespace scm
+#endif

@@ -1,0 +1,534 @@
+// msft_tc.cu -- tensor-core (tcgen05) form of Eq. 9's per-slice Fourier sum.
+//
+// Per slice j the 2D sum over (x, y) is factored as
+//   G[q, (j,x)] = sum_y e^{-i q_y y} s_j(x, y)          (dense complex contraction)
+//   A[q]        = (n^2-1) sum_j e^{-i q_z z_j} sum_x e^{-i q_x x} G[q, (j,x)]
+// The first line is one real GEMM per slice, D[m, n] = sum_k P[m, k] B[n, k]:
+//   m  = pixel (128 per tile),  k = [cos part: y | sin part: y]  (K = 2*Nyp),
+//   n  = [Re G: x | Im G: x]  (N = 2*Nxp),
+//   P[m, y] = cos(q_y y),  P[m, Nyp+y] = -sin(q_y y)            (e^{-i q_y y}),
+//   B[(x,re), y] = Re s,  B[(x,re), Nyp+y] = -Im s,
+//   B[(x,im), y] = Im s,  B[(x,im), Nyp+y] = Re s.
+// P is built in shared memory once per pixel tile; with split phases it is
+// held as an FP16/BF16 pair P = P_hi + P_lo and both halves are multiplied
+// into the same FP32 accumulator.  B tiles (one slice per N-tile) stream in
+// through TMA with 128-byte swizzle.  Accumulators live in tensor memory,
+// double buffered, and eight epilogue warps apply the x- and z-phases
+// (second line) while the next slice's MMAs run.
+//
+// Warp roles (320 threads): warps 0-7 epilogue (two per TMEM lane quarter,
+// each half of the x chunks), warp 8 TMA producer, warp 9 MMA issuer and
+// tensor-memory owner.  Every wait is bounded: on time-out the kernel sets a
+// bit in the error word, releases its tensor memory and returns.
+#include "internal.cuh"
+
+namespace scm {
+
+constexpr int kTcThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kProducerWarp = 8;
+constexpr int kMmaWarp = 9;
+constexpr int kBM = 128;
+constexpr int kBK = 64;                    // 64 x 16-bit = one 128-byte swizzle row
+constexpr int kKBlockBytes = kBM * 128;    // one 128 x 64 operand block
+constexpr int kMaxStages = 8;
+constexpr int kMaxSmem = 232448;           // 227 KB opt-in per block
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+struct TcParams {
+    const double *q;
+    long long n_pix;
+    int nx, ny, nz;
+    int Nxp, Nyp, Kp, nkb;
+    int stages;
+    int split, bf16;
+    int num_m_tiles;
+    uint32_t idesc;
+    uint32_t tmem_cols;
+    double voxel;
+    float str_re, str_im;
+    float2 *A;
+    float *I;
+    int *err;
+};
+
+// ---- PTX wrappers -------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on a phase parity.  Returns false when the wait gave up (time
+// limit, or another role already gave up).
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                       int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (global_ns() - t0 > kTimeoutNs) {
+            atomicOr(err, code);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(dst), "l"((unsigned long long)map), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7]),
+          "=f"(r[8]), "=f"(r[9]), "=f"(r[10]), "=f"(r[11]), "=f"(r[12]), "=f"(r[13]), "=f"(r[14]), "=f"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+// Waits for outstanding tcgen05.ld; the operands tie every loaded register to
+// the wait so no use of them is scheduled before it.
+__device__ __forceinline__ void tmem_ld_wait(float (&a)[16], float (&b)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(a[4]), "+f"(a[5]), "+f"(a[6]),
+                   "+f"(a[7]), "+f"(a[8]), "+f"(a[9]), "+f"(a[10]), "+f"(a[11]), "+f"(a[12]), "+f"(a[13]),
+                   "+f"(a[14]), "+f"(a[15]), "+f"(b[0]), "+f"(b[1]), "+f"(b[2]), "+f"(b[3]), "+f"(b[4]),
+                   "+f"(b[5]), "+f"(b[6]), "+f"(b[7]), "+f"(b[8]), "+f"(b[9]), "+f"(b[10]), "+f"(b[11]),
+                   "+f"(b[12]), "+f"(b[13]), "+f"(b[14]), "+f"(b[15])
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ void epi_bar_sync() {
+    asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand with 128-byte swizzle:
+// rows of 128 bytes, 8-row atoms 1024 bytes apart (stride byte offset),
+// leading byte offset unused for this layout, descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ uint16_t to16(float v, int bf16) {
+    if (bf16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(v);
+        return *reinterpret_cast<uint16_t *>(&h);
+    }
+    __half h = __float2half_rn(v);
+    return *reinterpret_cast<uint16_t *>(&h);
+}
+__device__ __forceinline__ float from16(uint16_t u, int bf16) {
+    if (bf16) {
+        __nv_bfloat16 h = *reinterpret_cast<__nv_bfloat16 *>(&u);
+        return __bfloat162float(h);
+    }
+    __half h = *reinterpret_cast<__half *>(&u);
+    return __half2float(h);
+}
+
+// Byte offset of 16-byte chunk `c` (8 elements) of row `m` in K-block `kb`
+// of a 128-row operand laid out for the 128-byte swizzle.
+__device__ __forceinline__ uint32_t a_chunk_offset(int m, int k) {
+    const int kb = k >> 6, c = (k & 63) >> 3;
+    return (uint32_t)(kb * kKBlockBytes + m * 128 + ((c ^ (m & 7)) << 4));
+}
+
+// Phase operand P[m, k] of one pixel tile (and its low part when split).
+__device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint8_t *sA_hi, uint8_t *sA_lo,
+                                                 int tid, int nthreads) {
+    const int ny8 = P.Nyp >> 3;
+    for (int it = tid; it < kBM * ny8; it += nthreads) {
+        const int m = it % kBM, y8 = it / kBM;
+        const long long p = (long long)mt * kBM + m;
+        const double qy = p < P.n_pix ? P.q[3 * p + 1] : 0.0;
+        const float qh = (float)qy, ql = (float)(qy - (double)qh);
+        const float yoff = 0.5f * (float)(P.ny - 1), vox = (float)P.voxel;
+        uint32_t re_hi[4], im_hi[4], re_lo[4], im_lo[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float cr[2], ci[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int y = 8 * y8 + e + u;
+                float2 ph = make_float2(0.f, 0.f);
+                if (y < P.ny && p < P.n_pix) ph = expmi_fs(qh, ql, ((float)y - yoff) * vox);
+                cr[u] = ph.x;
+                ci[u] = ph.y;
+            }
+            uint16_t rh0 = to16(cr[0], P.bf16), rh1 = to16(cr[1], P.bf16);
+            uint16_t ih0 = to16(ci[0], P.bf16), ih1 = to16(ci[1], P.bf16);
+            re_hi[e >> 1] = (uint32_t)rh0 | ((uint32_t)rh1 << 16);
+            im_hi[e >> 1] = (uint32_t)ih0 | ((uint32_t)ih1 << 16);
+            uint16_t rl0 = to16(cr[0] - from16(rh0, P.bf16), P.bf16);
+            uint16_t rl1 = to16(cr[1] - from16(rh1, P.bf16), P.bf16);
+            uint16_t il0 = to16(ci[0] - from16(ih0, P.bf16), P.bf16);
+            uint16_t il1 = to16(ci[1] - from16(ih1, P.bf16), P.bf16);
+            re_lo[e >> 1] = (uint32_t)rl0 | ((uint32_t)rl1 << 16);
+            im_lo[e >> 1] = (uint32_t)il0 | ((uint32_t)il1 << 16);
+        }
+        const uint32_t o_re = a_chunk_offset(m, 8 * y8);
+        const uint32_t o_im = a_chunk_offset(m, P.Nyp + 8 * y8);
+        *reinterpret_cast<uint4 *>(sA_hi + o_re) = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+        *reinterpret_cast<uint4 *>(sA_hi + o_im) = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+        if (P.split) {
+            *reinterpret_cast<uint4 *>(sA_lo + o_re) = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+            *reinterpret_cast<uint4 *>(sA_lo + o_im) = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    msft_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t a_bytes = (uint32_t)P.nkb * kKBlockBytes;
+    uint8_t *sA_hi = base;
+    uint8_t *sA_lo = base + a_bytes;
+    uint8_t *sB = base + (P.split ? 2 : 1) * a_bytes;
+    const uint32_t stage_bytes = (uint32_t)P.Nxp * 2 * 128;
+    float2 *red = reinterpret_cast<float2 *>(sB + (size_t)P.stages * stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(red + kBM);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + kMaxStages;
+    uint64_t *tfull = bars + 2 * kMaxStages;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.stages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull[b]), 1);
+            mbar_init(smem_u32(&tempty[b]), kEpiWarps);
+        }
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == kMmaWarp) {
+        tmem_alloc(smem_u32(tmem_slot), P.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    uint32_t prod_it = 0, mma_it = 0, acc_it = 0, epi_it = 0;
+    const int nch = P.Nxp >> 4;                 // 16-column chunks per slice
+    const int nch0 = (nch + 1) >> 1;
+
+    for (int mt = blockIdx.x; mt < P.num_m_tiles; mt += gridDim.x) {
+        if (warp < kEpiWarps) {
+            build_phase_tile(P, mt, sA_hi, sA_lo, threadIdx.x, kEpiWarps * 32);
+            fence_async_smem();
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+
+        if (warp == kProducerWarp) {
+            if (lane == 0) {
+                bool ok = true;
+                for (int t = 0; t < P.nz && ok; ++t) {
+                    for (int kb = 0; kb < P.nkb; ++kb) {
+                        const uint32_t s = prod_it % P.stages, ph = (prod_it / P.stages) & 1;
+                        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutProducer)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(smem_u32(&full[s]), stage_bytes);
+                        tma_load_2d(smem_u32(sB + (size_t)s * stage_bytes), &tmap, smem_u32(&full[s]), kb * kBK,
+                                    t * 2 * P.Nxp);
+                        ++prod_it;
+                    }
+                }
+            }
+            __syncwarp();
+        } else if (warp == kMmaWarp) {
+            if (lane == 0) {
+                bool ok = true;
+                const uint32_t a_hi = smem_u32(sA_hi), a_lo = smem_u32(sA_lo), b0 = smem_u32(sB);
+                for (int t = 0; t < P.nz && ok; ++t) {
+                    const uint32_t b = acc_it & 1, aph = (acc_it >> 1) & 1;
+                    if (!mbar_wait(smem_u32(&tempty[b]), aph ^ 1, abort_flag, P.err, kErrTimeoutMma)) break;
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + b * (uint32_t)(2 * P.Nxp);
+                    for (int kb = 0; kb < P.nkb; ++kb) {
+                        const uint32_t s = mma_it % P.stages, ph = (mma_it / P.stages) & 1;
+                        if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const int ksteps = min(kBK, P.Kp - kb * kBK) >> 4;
+                        const uint32_t bs = b0 + s * stage_bytes;
+                        for (int kk = 0; kk < ksteps; ++kk) {
+                            const uint64_t bdesc = sw128_desc(bs + kk * 32);
+                            const uint32_t aoff = kb * kKBlockBytes + kk * 32;
+                            mma_f16(d, sw128_desc(a_hi + aoff), bdesc, P.idesc, (kb | kk) != 0);
+                            if (P.split) mma_f16(d, sw128_desc(a_lo + aoff), bdesc, P.idesc, 1u);
+                        }
+                        mma_commit(smem_u32(&empty[s]));
+                        ++mma_it;
+                    }
+                    if (!ok) break;
+                    mma_commit(smem_u32(&tfull[b]));
+                    ++acc_it;
+                }
+            }
+            __syncwarp();
+        } else {
+            // ---------------- epilogue warps ----------------
+            const int quarter = warp & 3, half = warp >> 2;
+            const int m = quarter * 32 + lane;
+            const long long p = (long long)mt * kBM + m;
+            const bool valid = p < P.n_pix;
+            const double qx = valid ? P.q[3 * p] : 0.0;
+            const double qz = valid ? P.q[3 * p + 2] : 0.0;
+            const int c_begin = half ? nch0 : 0;
+            const int c_end = half ? nch : nch0;
+            float2 W[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) W[k] = expmi_f(qx, k * P.voxel);
+            float2 E[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int x0 = 16 * (c_begin + i);
+                E[i] = expmi_f(qx, (x0 - 0.5 * (P.nx - 1)) * P.voxel);
+            }
+            const float2 Zstep = expmi_f(qz, P.voxel);
+            float2 Z = expmi_f(qz, (0 - 0.5 * (P.nz - 1)) * P.voxel);
+            float2 acc = make_float2(0.f, 0.f);
+            const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+            for (int t = 0; t < P.nz; ++t) {
+                const uint32_t b = epi_it & 1, ph = (epi_it >> 1) & 1;
+                if (!mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue)) break;
+                tc_fence_after();
+                float2 acct = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (c_begin + i < c_end) {
+                        const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)(c_begin + i);
+                        float gr[16], gi[16];
+                        tmem_ld16(lane_base + col, gr);
+                        tmem_ld16(lane_base + col + (uint32_t)P.Nxp, gi);
+                        tmem_ld_wait(gr, gi);
+                        float hr = 0.f, hi = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            hr = fmaf(W[k].x, gr[k], hr);
+                            hr = fmaf(-W[k].y, gi[k], hr);
+                            hi = fmaf(W[k].x, gi[k], hi);
+                            hi = fmaf(W[k].y, gr[k], hi);
+                        }
+                        acct.x = fmaf(E[i].x, hr, fmaf(-E[i].y, hi, acct.x));
+                        acct.y = fmaf(E[i].x, hi, fmaf(E[i].y, hr, acct.y));
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+                acc.x = fmaf(Z.x, acct.x, fmaf(-Z.y, acct.y, acc.x));
+                acc.y = fmaf(Z.x, acct.y, fmaf(Z.y, acct.x, acc.y));
+                if (((t + 1) & 15) == 0)
+                    Z = expmi_f(qz, ((t + 1) - 0.5 * (P.nz - 1)) * P.voxel);
+                else
+                    Z = cmul(Z, Zstep);
+                ++epi_it;
+            }
+            if (half == 1) red[m] = acc;
+            epi_bar_sync();
+            if (half == 0 && valid) {
+                const float2 o = red[m];
+                float2 a = make_float2(acc.x + o.x, acc.y + o.y);
+                a = cmul(make_float2(P.str_re, P.str_im), a);
+                P.A[p] = a;
+                P.I[p] = a.x * a.x + a.y * a.y;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- teardown: make sure no tensor-core or TMA work is in flight ----
+    __syncthreads();
+    if (*abort_flag) {
+        if (warp == kMmaWarp && lane == 0) {
+            mma_commit(smem_u32(drain));
+            volatile int dummy = 0;
+            mbar_wait(smem_u32(drain), 0, &dummy, P.err, kErrTimeoutDrain);
+        }
+        if (warp == kProducerWarp && lane == 0) {
+            volatile int dummy = 0;
+            const uint32_t first = prod_it > (uint32_t)P.stages ? prod_it - P.stages : 0;
+            for (uint32_t it = first; it < prod_it; ++it) {
+                const uint32_t s = it % P.stages, ph = (it / P.stages) & 1;
+                mbar_wait(smem_u32(&full[s]), ph, &dummy, P.err, kErrTimeoutDrain);
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == kMmaWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, P.tmem_cols);
+    }
+}
+
+// ---- host side ------------------------------------------------------------------
+static size_t tc_fixed_bytes() { return 1024 /*align*/ + kBM * sizeof(float2) + 256 /*barriers*/; }
+
+static int tc_nkb(int Kp) { return (Kp + kBK - 1) / kBK; }
+
+int tc_max_stages(int Kp, int Nxp, bool split) {
+    size_t a = (size_t)(split ? 2 : 1) * tc_nkb(Kp) * kKBlockBytes;
+    size_t stage = (size_t)Nxp * 2 * 128;
+    if (a + tc_fixed_bytes() + 2 * stage > (size_t)kMaxSmem) return 0;
+    size_t s = ((size_t)kMaxSmem - a - tc_fixed_bytes()) / stage;
+    return (int)(s > (size_t)kMaxStages ? kMaxStages : s);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, bool bf16, std::string *why) {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                                         &qr);
+        if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !ptr) {
+            *why = "cuTensorMapEncodeTiled is not available from the driver";
+            return false;
+        }
+        fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)(2 * Nxp)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
+cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n_pix, int nx, int ny, int nz,
+                           int Nxp, int Nyp, int Kp, double voxel, double str_re, double str_im, bool split,
+                           bool bf16, float2 *A, float *I, int *err, int sm_count, cudaStream_t st) {
+    TcParams P;
+    P.q = q;
+    P.n_pix = n_pix;
+    P.nx = nx;
+    P.ny = ny;
+    P.nz = nz;
+    P.Nxp = Nxp;
+    P.Nyp = Nyp;
+    P.Kp = Kp;
+    P.nkb = tc_nkb(Kp);
+    P.stages = tc_max_stages(Kp, Nxp, split);
+    if (P.stages < 2 || Nxp % 16 != 0 || Nxp > 128 || Kp % 16 != 0) return cudaErrorInvalidValue;
+    P.split = split ? 1 : 0;
+    P.bf16 = bf16 ? 1 : 0;
+    P.num_m_tiles = (int)((n_pix + kBM - 1) / kBM);
+    const uint32_t N = (uint32_t)(2 * Nxp), M = kBM;
+    P.idesc = (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+    uint32_t cols = 32;
+    while (cols < (uint32_t)(4 * Nxp)) cols <<= 1;
+    P.tmem_cols = cols;
+    P.voxel = voxel;
+    P.str_re = (float)str_re;
+    P.str_im = (float)str_im;
+    P.A = A;
+    P.I = I;
+    P.err = err;
+    size_t smem = (size_t)(split ? 2 : 1) * P.nkb * kKBlockBytes + (size_t)P.stages * Nxp * 2 * 128 + tc_fixed_bytes();
+    cudaError_t e = cudaFuncSetAttribute(msft_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int grid = P.num_m_tiles < sm_count ? P.num_m_tiles : sm_count;
+    if (grid < 1) grid = 1;
+    msft_tc_kernel<<<grid, kTcThreads, smem, st>>>(tmap, P);
+    return cudaGetLastError();
+}
+
+}  // namespace scm

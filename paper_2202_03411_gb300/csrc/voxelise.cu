@@ -1,0 +1,167 @@
+// voxelise.cu -- detector q (Eq. 3) and the fused voxeliser + transmission
+// scan (Block 5 + Block 9, Eq. 8 of arXiv 2202.03411).
+//
+// One CTA owns one x column-plane strip: a fixed x and 32 consecutive y lines.
+// Each warp takes whole lines along z; lane l renders the occupancy of a
+// contiguous run of z values, and the exclusive prefix C_j = sum_{j'<j} chi
+// is formed with a warp-shuffle scan of the lanes' run totals.  The slice
+// strength s_j = chi_j exp(i k0 dz (n-1) C_j) is staged in shared memory as
+// [z][y] and then written out so that consecutive threads store consecutive
+// y -- the contraction's operand rows are y-contiguous.
+#include "internal.cuh"
+#include "shape_device.cuh"
+
+namespace scm {
+
+// ---------------------------------------------------------------------------
+// a1: transfer momentum of every flat-detector pixel (Eq. 3).  The pixel sits
+// at (X, Y, 1); k_out = k0 (X, Y, 1)/r and q = k_out - k0 z^.  q_z is written
+// as -k0 (X^2+Y^2) / (r (1 + r)) to avoid cancellation near the axis.
+// ---------------------------------------------------------------------------
+__global__ void detector_q_kernel(int det_nx, int det_ny, double h, double k0, double *q) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long n = (long long)det_nx * det_ny;
+    if (p >= n) return;
+    int u = (int)(p % det_nx);
+    int v = (int)(p / det_nx);
+    double X = h * (double)(2 * u + 1 - det_nx) / (double)det_nx;
+    double Y = h * (double)(2 * v + 1 - det_ny) / (double)det_ny;
+    double rho2 = X * X + Y * Y;
+    double r = sqrt(rho2 + 1.0);
+    q[3 * p + 0] = k0 * X / r;
+    q[3 * p + 1] = k0 * Y / r;
+    q[3 * p + 2] = -k0 * rho2 / (r * (1.0 + r));
+}
+
+cudaError_t launch_detector_q(int det_nx, int det_ny, double theta_max_deg, double k0, double *q,
+                              cudaStream_t st) {
+    long long n = (long long)det_nx * det_ny;
+    double h = tan(theta_max_deg * kPi / 180.0);
+    int threads = 256;
+    long long blocks = (n + threads - 1) / threads;
+    detector_q_kernel<<<(unsigned)blocks, threads, 0, st>>>(det_nx, det_ny, h, k0, q);
+    return cudaGetLastError();
+}
+
+constexpr int kLinesPerCta = 32;
+constexpr int kVoxThreads = 256;
+constexpr int kMaxRun = 8;          // z values per lane: nz <= 256
+
+// s_j = chi_j T_j with T_j = exp(i k0 dz (n-1) C_j) = e^{-k0 dz beta C} e^{-i k0 dz delta C}.
+template <bool kFp64, typename ScanT>
+__global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams sp, GridParams gp,
+                                                                    SliceOut out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nz = gp.nz;
+    using Cx = typename std::conditional<kFp64, double2, float2>::type;
+    Cx *s_tile = reinterpret_cast<Cx *>(smem);                                // [nz][32]
+    float *chi_tile = reinterpret_cast<float *>(smem + sizeof(Cx) * nz * kLinesPerCta);
+
+    const int ix = blockIdx.x;
+    const int y0 = blockIdx.y * kLinesPerCta;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int run = (nz + 31) / 32;
+    const ScanT a_att = (ScanT)(gp.k0 * gp.voxel * gp.beta);     // attenuation per unit C
+    const ScanT a_ph = (ScanT)(gp.k0 * gp.voxel * gp.delta);     // phase per unit C
+
+    for (int yl = warp; yl < kLinesPerCta; yl += kVoxThreads / 32) {
+        const int iy = y0 + yl;
+        if (iy >= gp.ny) break;
+        double chi[kMaxRun];
+        ScanT local = (ScanT)0;
+#pragma unroll
+        for (int k = 0; k < kMaxRun; ++k) {
+            int iz = lane * run + k;
+            chi[k] = 0.0;
+            if (k < run && iz < nz) chi[k] = occupancy<kFp64>(sp, gp, ix, iy, iz);
+            local += (ScanT)chi[k];
+        }
+        // warp exclusive scan of the lanes' run totals
+        ScanT incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            ScanT nb = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += nb;
+        }
+        ScanT C = incl - local;
+#pragma unroll
+        for (int k = 0; k < kMaxRun; ++k) {
+            int iz = lane * run + k;
+            if (k < run && iz < nz) {
+                ScanT mag = exp(-a_att * C);
+                ScanT sn, cs;
+                sincos(a_ph * C, &sn, &cs);
+                Cx v;
+                v.x = (decltype(v.x))(chi[k] * (double)(mag * cs));
+                v.y = (decltype(v.y))(-chi[k] * (double)(mag * sn));
+                s_tile[iz * kLinesPerCta + yl] = v;
+                chi_tile[iz * kLinesPerCta + yl] = (float)chi[k];
+                C += (ScanT)chi[k];
+            }
+        }
+    }
+    __syncthreads();
+
+    const int ny_here = min(kLinesPerCta, gp.ny - y0);
+    const long long nxy = (long long)gp.nx * gp.ny;
+    for (int it = threadIdx.x; it < nz * kLinesPerCta; it += kVoxThreads) {
+        const int iz = it / kLinesPerCta, yl = it % kLinesPerCta;
+        if (yl >= ny_here) continue;
+        const int iy = y0 + yl;
+        const Cx v = s_tile[iz * kLinesPerCta + yl];
+        const long long vidx = iz * nxy + (long long)ix * gp.ny + iy;
+        out.chi[vidx] = chi_tile[iz * kLinesPerCta + yl];
+        if (out.layout == kLayoutC64) {
+            reinterpret_cast<double2 *>(out.s)[vidx] = make_double2((double)v.x, (double)v.y);
+        } else if (out.layout == kLayoutC32) {
+            reinterpret_cast<float2 *>(out.s)[vidx] = make_float2((float)v.x, (float)v.y);
+        } else {
+            // tensor-core operand rows: (j, x, re) at j*2Nxp + x, (j, x, im) at j*2Nxp + Nxp + x;
+            // K index y holds the cos part, Nyp + y the sin part (see msft_tc.cu).
+            const size_t row_r = (size_t)iz * 2 * out.Nxp + ix;
+            const size_t row_i = row_r + out.Nxp;
+            const float sr = (float)v.x, si = (float)v.y;
+            if (out.layout == kLayoutTcF16) {
+                __half *B = reinterpret_cast<__half *>(out.s);
+                B[row_r * out.Kp + iy] = __float2half_rn(sr);
+                B[row_r * out.Kp + out.Nyp + iy] = __float2half_rn(-si);
+                B[row_i * out.Kp + iy] = __float2half_rn(si);
+                B[row_i * out.Kp + out.Nyp + iy] = __float2half_rn(sr);
+            } else {
+                __nv_bfloat16 *B = reinterpret_cast<__nv_bfloat16 *>(out.s);
+                B[row_r * out.Kp + iy] = __float2bfloat16_rn(sr);
+                B[row_r * out.Kp + out.Nyp + iy] = __float2bfloat16_rn(-si);
+                B[row_i * out.Kp + iy] = __float2bfloat16_rn(si);
+                B[row_i * out.Kp + out.Nyp + iy] = __float2bfloat16_rn(sr);
+            }
+        }
+    }
+}
+
+cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const SliceOut &out, bool scan_fp64,
+                            bool fp64_mode, cudaStream_t st) {
+    if (gp.nz > 32 * kMaxRun) return cudaErrorInvalidValue;
+    dim3 grid(gp.nx, (gp.ny + kLinesPerCta - 1) / kLinesPerCta);
+    size_t cx = fp64_mode ? sizeof(double2) : sizeof(float2);
+    size_t smem = (cx + sizeof(float)) * (size_t)gp.nz * kLinesPerCta;
+    cudaError_t e;
+    if (fp64_mode) {
+        auto k = voxelise_scan_kernel<true, double>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
+    } else if (scan_fp64) {
+        auto k = voxelise_scan_kernel<false, double>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
+    } else {
+        auto k = voxelise_scan_kernel<false, float>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace scm
