@@ -214,6 +214,34 @@ SCATMAN_API const char *scatman_last_error(const scatman_handle *h);
 /* Releases every buffer and the owned stream.  Accepts NULL. */
 SCATMAN_API void scatman_destroy(scatman_handle *h);
 
+/*
+ * Forward pass that allocates no device memory (the paper has no counterpart;
+ * this is a service to callers that cannot call cudaMalloc -- for example a
+ * host application that has already reserved nearly all device memory for its
+ * own pool, or a latency-critical loop that must not take the device-wide
+ * synchronisation an allocation can cause).
+ *
+ * Runs voxelise + transmission scan + forward (as scatman_voxelise followed by
+ * scatman_forward on a SCATMAN_FP32 handle) for one shape, on cuda_stream
+ * (a cudaStream_t; NULL is the legacy default stream), asynchronously.
+ *  cfg     as for scatman_create; precision must be SCATMAN_FP32
+ *  I_dev   caller-owned device array of n_pix floats (output)
+ *  A_dev   optional caller-owned device array of n_pix complex floats; NULL skips it
+ * Working memory (q, occupancy, slices, partial fields) lives in one fixed
+ * 8 MiB array inside the library, which every GPU that loads the library
+ * keeps until the process exits.  Problems that need more return ERR_ARG
+ * with the required size.  The array is shared by every call and keeps the
+ * previous call's contents; each call overwrites everything it reads, so
+ * nothing has to start at zero, but calls whose GPU work overlaps (for
+ * example on two streams) race on it and give wrong results.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Errors: ERR_ARG, ERR_UNSUPPORTED, ERR_CUDA;
+ * the message is available from scatman_last_error(NULL).
+ */
+SCATMAN_API int scatman_forward_noalloc(const scatman_config *cfg, const scatman_shape *shape, void *cuda_stream,
+                                        float *I_dev, float *A_dev);
+
 /* Library version string. */
 SCATMAN_API const char *scatman_version(void);
 

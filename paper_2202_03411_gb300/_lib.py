@@ -79,6 +79,8 @@ SIGNATURES = {
     "scatman_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "scatman_destroy": (None, [ctypes.c_void_p]),
     "scatman_version": (ctypes.c_char_p, []),
+    "scatman_forward_noalloc": (ctypes.c_int, [ctypes.POINTER(scatman_config), ctypes.POINTER(scatman_shape),
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 _lib = None

@@ -187,3 +187,21 @@ def scatman_version() -> str:
 
 def scatman_last_error(h: Handle) -> str:
     return _lib.load().scatman_last_error(h.ptr).decode()
+
+
+def scatman_forward_noalloc(geometry, shape, I, A=None, soft: bool = False, soft_width: float = 0.5,
+                            scan_fp64: bool = False, q_list: Optional[np.ndarray] = None,
+                            stream: Optional[int] = None) -> None:
+    """scatman_forward_noalloc: the FP32 forward for callers that cannot
+    allocate device memory; I (and A) are float32 (complex64) CUDA tensors."""
+    lib = _lib.load()
+    cfg, keep = make_config(geometry, "fp32", soft, soft_width, scan_fp64, q_list)
+    st, alm = make_shape(shape)
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    code = lib.scatman_forward_noalloc(ctypes.byref(cfg), ctypes.byref(st), ctypes.c_void_p(stream),
+                                       ctypes.c_void_p(I.data_ptr()),
+                                       ctypes.c_void_p(A.data_ptr() if A is not None else None))
+    if code != 0:
+        raise ScatmanError(code, "scatman_forward_noalloc: " + lib.scatman_last_error(None).decode())

@@ -474,3 +474,164 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Forward pass without device allocation.
+//
+// Some callers cannot call cudaMalloc: a host application that has already
+// reserved nearly all device memory for its own pool, or a latency-critical
+// loop that must not take the device-wide synchronisation an allocation can
+// cause.  scatman_forward_noalloc serves them with the CUDA-core FP32 path,
+// keeping its working memory (q, occupancy, slices, partial fields) in one
+// fixed array that the library image carries, so only the caller's output
+// buffers are written.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace scm {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;   // 8 MiB, held by every GPU that loads the library
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; host code only ever sees a host-side stand-in for the symbol).
+static int noalloc_scratch(int dev, void **out, std::string *why) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        *why = "device ordinal out of range for the no-allocation scratch table";
+        return SCATMAN_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            *why = std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e);
+            return SCATMAN_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SCATMAN_OK;
+}
+
+}  // namespace scm
+
+extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_shape *s, void *cuda_stream,
+                                       float *I_dev, float *A_dev) {
+    g_create_error.clear();
+    auto fail = [&](int code, const std::string &msg) {
+        g_create_error = msg;
+        return code;
+    };
+    if (!cfg || !s || !I_dev) return fail(SCATMAN_ERR_ARG, "NULL argument");
+    const scatman_config &c = *cfg;
+    if (c.precision != SCATMAN_FP32) return fail(SCATMAN_ERR_ARG, "the no-allocation forward runs in SCATMAN_FP32 only");
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.nz > 256)
+        return fail(SCATMAN_ERR_ARG, "grid sizes must be >= 1 and nz <= 256");
+    if (!(c.voxel > 0) || !(c.wavelength > 0)) return fail(SCATMAN_ERR_ARG, "voxel and wavelength must be positive");
+    if (c.soft && !(c.soft_width > 0)) return fail(SCATMAN_ERR_ARG, "soft occupancy needs soft_width > 0");
+    long long n_pix;
+    if (c.q_list) {
+        if (c.n_q < 1) return fail(SCATMAN_ERR_ARG, "n_q must be >= 1 with q_list");
+        n_pix = c.n_q;
+    } else {
+        if (c.det_nx < 1 || c.det_ny < 1) return fail(SCATMAN_ERR_ARG, "detector size must be >= 1");
+        if (!(c.theta_max_deg > 0 && c.theta_max_deg < 90))
+            return fail(SCATMAN_ERR_ARG, "theta_max_deg must lie in (0, 90)");
+        n_pix = (long long)c.det_nx * c.det_ny;
+    }
+    if (s->kind < SCATMAN_SPHERE || s->kind > SCATMAN_SPHHARM) return fail(SCATMAN_ERR_ARG, "unknown shape kind");
+    if (s->kind == SCATMAN_SPHERE && !(s->r > 0)) return fail(SCATMAN_ERR_ARG, "sphere radius must be > 0");
+    if (s->kind == SCATMAN_ELLIPSOID && !(s->a > 0 && s->b > 0 && s->c > 0))
+        return fail(SCATMAN_ERR_ARG, "ellipsoid semi-axes must be > 0");
+    if (s->kind == SCATMAN_SPHHARM) {
+        if (!(s->R0 > 0)) return fail(SCATMAN_ERR_ARG, "R0 must be > 0");
+        if (s->lmax < 0 || s->lmax > SCATMAN_MAX_LMAX) return fail(SCATMAN_ERR_ARG, "lmax out of range");
+        if (s->lmax > 0 && !s->alm) return fail(SCATMAN_ERR_ARG, "alm is NULL");
+    }
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(SCATMAN_ERR_UNSUPPORTED, "no CUDA device");
+    int major = 0, minor = 0, sms = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!(major == 10 && minor == 3))
+        return fail(SCATMAN_ERR_UNSUPPORTED, "this library is built for sm_103a (compute capability 10.3) only");
+
+    // carve the scratch: q | occupancy | slices | field (if not supplied) | partial fields
+    const size_t nvox = (size_t)c.nx * c.ny * c.nz;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t q_b = up((size_t)n_pix * 3 * sizeof(double));
+    const size_t chi_b = up(nvox * sizeof(float));
+    const size_t s_b = up(nvox * sizeof(float2));
+    const size_t a_b = A_dev ? 0 : up((size_t)n_pix * sizeof(float2));
+    const size_t fixed = q_b + chi_b + s_b + a_b;
+    int splits = simt_splits(n_pix, c.nx, c.nz, sms);
+    while (splits > 1 && fixed + up((size_t)splits * n_pix * sizeof(float2)) > kNoAllocScratchBytes) --splits;
+    const size_t need = fixed + up((size_t)splits * n_pix * sizeof(float2));
+    if (need > kNoAllocScratchBytes)
+        return fail(SCATMAN_ERR_ARG, "problem needs " + std::to_string(need) + " bytes of scratch; the no-allocation "
+                                     "forward holds " + std::to_string(kNoAllocScratchBytes) + " bytes");
+    void *base = nullptr;
+    std::string why;
+    int rc = noalloc_scratch(dev, &base, &why);
+    if (rc) return fail(rc, why);
+    unsigned char *b = (unsigned char *)base;
+    double *d_q = (double *)b;
+    float *d_chi = (float *)(b + q_b);
+    float2 *d_s = (float2 *)(b + q_b + chi_b);
+    float2 *d_A = A_dev ? (float2 *)A_dev : (float2 *)(b + q_b + chi_b + s_b);
+    float2 *d_part = (float2 *)(b + fixed);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+
+    const double k0 = 2.0 * kPi / c.wavelength;
+    cudaError_t e;
+    if (c.q_list) {
+        e = cudaMemcpyAsync(d_q, c.q_list, (size_t)n_pix * 3 * sizeof(double), cudaMemcpyHostToDevice, st);
+    } else {
+        e = launch_detector_q(c.det_nx, c.det_ny, c.theta_max_deg, k0, d_q, st);
+    }
+    if (e != cudaSuccess) return fail(SCATMAN_ERR_CUDA, std::string("q: ") + cudaGetErrorString(e));
+
+    ShapeParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.kind = s->kind;
+    sp.lmax = s->kind == SCATMAN_SPHHARM ? s->lmax : 0;
+    sp.soft = c.soft ? 1 : 0;
+    sp.inv_w = c.soft ? 1.0 / c.soft_width : 0.0;
+    sp.inv_w_f = (float)sp.inv_w;
+    sp.r = s->r;
+    sp.a = s->a;
+    sp.b = s->b;
+    sp.c = s->c;
+    sp.R0 = s->R0;
+    int nmin = c.nx < c.ny ? c.nx : c.ny;
+    if (c.nz < nmin) nmin = c.nz;
+    sp.rmin = 0.1 * s->R0;
+    sp.rmax = 0.5 * (nmin - 1) * c.voxel - c.voxel;
+    orientation_matrix(s->latitude, s->longitude, s->rotation, sp.R);
+    sp.cx = s->cx;
+    sp.cy = s->cy;
+    sp.cz = s->cz;
+    if (s->kind == SCATMAN_SPHHARM)
+        for (int k = 0; k < (s->lmax + 1) * (s->lmax + 1); ++k) sp.alm[k] = s->alm[k];
+    GridParams gp{c.nx, c.ny, c.nz, c.voxel, k0, s->delta, s->beta};
+    SliceOut so;
+    so.layout = kLayoutC32;
+    so.Nxp = so.Nyp = so.Kp = 0;
+    so.s = d_s;
+    so.chi = d_chi;
+    const double strength = std::fmax(std::fabs(s->delta), std::fabs(s->beta));
+    const bool scan_fp64 = c.scan_fp64 || (k0 * c.voxel * c.nz * strength > 5.0);
+    e = launch_voxelise(sp, gp, so, scan_fp64, false, st);
+    if (e != cudaSuccess) return fail(SCATMAN_ERR_CUDA, std::string("voxelise: ") + cudaGetErrorString(e));
+    const double d = s->delta, bb = s->beta;
+    e = launch_msft_simt(false, d_s, d_q, n_pix, c.nx, c.ny, c.nz, c.voxel, -2.0 * d + d * d - bb * bb,
+                         2.0 * bb - 2.0 * d * bb, d_A, I_dev, d_part, splits, st);
+    if (e != cudaSuccess) return fail(SCATMAN_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
+    return SCATMAN_OK;
+}
