@@ -171,7 +171,9 @@ __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridPara
     if (sp.kind == SCATMAN_SPHERE) {
         rs = (R)sp.r;
     } else if (sp.kind == SCATMAN_ELLIPSOID) {
-        const R ia = (R)(1.0 / sp.a), ib = (R)(1.0 / sp.b), ic = (R)(1.0 / sp.c);
+        const R ia = sizeof(R) == 4 ? (R)sp.inv_af : (R)(1.0 / sp.a);
+        const R ib = sizeof(R) == 4 ? (R)sp.inv_bf : (R)(1.0 / sp.b);
+        const R ic = sizeof(R) == 4 ? (R)sp.inv_cf : (R)(1.0 / sp.c);
         rs = (R)1 / sqrt(ux * ux * ia * ia + uy * uy * ib * ib + uz * uz * ic * ic);
     } else {
         R raw = sh_radius_unclipped<R>(sp, (R)px, (R)py, (R)pz, rr);
@@ -303,7 +305,8 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
                         cph = ux[k] / st;
                         sph = uy[k] / st;
                     }
-                    real_sh_all<R>(sp.lmax, ct, st, cph, sph, [&](int idx, R y) {
+                    const ShTab<R> tb(sp);
+                    real_sh_all<R>(tb, sp.lmax, ct, st, cph, sph, [&](int idx, R y) {
                         if (idx > 0) acc[idx - 1] += w0 * y;
                     });
                     acc[ng - 1] += coef * rs[k] / (R)sp.R0;

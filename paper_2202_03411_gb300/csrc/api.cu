@@ -58,6 +58,37 @@ static void orientation_matrix(double lat, double lon, double rot, double R[9]) 
 
 static long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 
+void finish_shape_params(ShapeParams *sp) {
+    for (int k = 0; k < 9; ++k) sp->Rf[k] = (float)sp->R[k];
+    sp->cxf = (float)sp->cx;
+    sp->cyf = (float)sp->cy;
+    sp->czf = (float)sp->cz;
+    sp->r2f = (float)(sp->r * sp->r);
+    sp->inv_af = sp->a > 0 ? (float)(1.0 / sp->a) : 0.f;
+    sp->inv_bf = sp->b > 0 ? (float)(1.0 / sp->b) : 0.f;
+    sp->inv_cf = sp->c > 0 ? (float)(1.0 / sp->c) : 0.f;
+    const int nlm = (SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1);
+    for (int k = 0; k < nlm; ++k) sp->almf[k] = (float)sp->alm[k];
+    for (int m = 0; m <= SCATMAN_MAX_LMAX; ++m) {
+        sp->sh_d[m] = m > 0 ? -std::sqrt((2.0 * m + 1.0) / (2.0 * m)) : 1.0;
+        sp->sh_e[m] = std::sqrt(2.0 * m + 3.0);
+        sp->sh_df[m] = (float)sp->sh_d[m];
+        sp->sh_ef[m] = (float)sp->sh_e[m];
+        for (int l = m; l <= SCATMAN_MAX_LMAX; ++l) {
+            const int i = l * (l + 1) / 2 + m;
+            double a = 0.0, b = 0.0;
+            if (l >= m + 2) {
+                a = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+                b = std::sqrt(((double)(l - 1) * (l - 1) - (double)m * m) / (4.0 * (l - 1) * (l - 1) - 1.0));
+            }
+            sp->sh_a[i] = a;
+            sp->sh_b[i] = b;
+            sp->sh_af[i] = (float)a;
+            sp->sh_bf[i] = (float)b;
+        }
+    }
+}
+
 }  // namespace scm
 
 using namespace scm;
@@ -267,6 +298,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     sp.cy = s->cy;
     sp.cz = s->cz;
     for (size_t k = 0; k < h->alm.size(); ++k) sp.alm[k] = h->alm[k];
+    finish_shape_params(&sp);
 
     GridParams gp{c.nx, c.ny, c.nz, c.voxel, h->k0, s->delta, s->beta};
     SliceOut so;
@@ -619,6 +651,7 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
     sp.cz = s->cz;
     if (s->kind == SCATMAN_SPHHARM)
         for (int k = 0; k < (s->lmax + 1) * (s->lmax + 1); ++k) sp.alm[k] = s->alm[k];
+    finish_shape_params(&sp);
     GridParams gp{c.nx, c.ny, c.nz, c.voxel, k0, s->delta, s->beta};
     SliceOut so;
     so.layout = kLayoutC32;

@@ -38,8 +38,26 @@ struct ShapeParams {
     double rmin, rmax;              // harmonics radius clip
     double R[9];                    // row-major body->lab rotation
     double cx, cy, cz;              // centre offset
+    float Rf[9];                    // the rotation and the offsets in FP32 (fast path)
+    float cxf, cyf, czf;
+    float r2f, inv_af, inv_bf, inv_cf;   // r^2 and 1/a, 1/b, 1/c in FP32
     double alm[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1)];
+    float almf[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1)];
+    // normalised associated-Legendre recurrence coefficients, index l(l+1)/2 + m
+    // (see real_sh_all): a_lm, b_lm, and the diagonal factors d_m, e_m
+    double sh_a[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 2) / 2];
+    double sh_b[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 2) / 2];
+    double sh_d[SCATMAN_MAX_LMAX + 1];
+    double sh_e[SCATMAN_MAX_LMAX + 1];
+    float sh_af[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 2) / 2];
+    float sh_bf[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 2) / 2];
+    float sh_df[SCATMAN_MAX_LMAX + 1];
+    float sh_ef[SCATMAN_MAX_LMAX + 1];
 };
+
+// Fills the FP32 copies and the harmonic recurrence tables of a ShapeParams
+// whose double fields are set (api.cu).
+void finish_shape_params(ShapeParams *sp);
 
 // Number of geometric gradient parameters: sphere [r]; ellipsoid [a, b, c];
 // harmonics [a_lm for l >= 1, R0].

@@ -48,12 +48,16 @@ constexpr int kVoxThreads = 256;
 constexpr int kMaxRun = 8;          // z values per lane: nz <= 256
 
 // s_j = chi_j T_j with T_j = exp(i k0 dz (n-1) C_j) = e^{-k0 dz beta C} e^{-i k0 dz delta C}.
+// Pass 1 renders chi into shared memory and sums each lane's run of z;
+// a warp-shuffle scan turns the run totals into exclusive prefixes; pass 2
+// walks the run again to form C_j, T_j and s_j.
 template <bool kFp64, typename ScanT>
 __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams sp, GridParams gp,
                                                                     SliceOut out) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int nz = gp.nz;
     using Cx = typename std::conditional<kFp64, double2, float2>::type;
+    using Re = typename std::conditional<kFp64, double, float>::type;
     Cx *s_tile = reinterpret_cast<Cx *>(smem);                                // [nz][32]
     float *chi_tile = reinterpret_cast<float *>(smem + sizeof(Cx) * nz * kLinesPerCta);
 
@@ -67,14 +71,15 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
     for (int yl = warp; yl < kLinesPerCta; yl += kVoxThreads / 32) {
         const int iy = y0 + yl;
         if (iy >= gp.ny) break;
-        double chi[kMaxRun];
+        const int z0 = lane * run;
+        const int z1 = min(nz, z0 + run);
         ScanT local = (ScanT)0;
-#pragma unroll
-        for (int k = 0; k < kMaxRun; ++k) {
-            int iz = lane * run + k;
-            chi[k] = 0.0;
-            if (k < run && iz < nz) chi[k] = occupancy<kFp64>(sp, gp, ix, iy, iz);
-            local += (ScanT)chi[k];
+#pragma unroll 1
+        for (int iz = z0; iz < z1; ++iz) {
+            const double c = occupancy<kFp64>(sp, gp, ix, iy, iz);
+            if (kFp64) s_tile[iz * kLinesPerCta + yl].x = c;         // exact copy until pass 2
+            chi_tile[iz * kLinesPerCta + yl] = (float)c;
+            local += (ScanT)c;
         }
         // warp exclusive scan of the lanes' run totals
         ScanT incl = local;
@@ -84,20 +89,17 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
             if (lane >= o) incl += nb;
         }
         ScanT C = incl - local;
-#pragma unroll
-        for (int k = 0; k < kMaxRun; ++k) {
-            int iz = lane * run + k;
-            if (k < run && iz < nz) {
-                ScanT mag = exp(-a_att * C);
-                ScanT sn, cs;
-                sincos(a_ph * C, &sn, &cs);
-                Cx v;
-                v.x = (decltype(v.x))(chi[k] * (double)(mag * cs));
-                v.y = (decltype(v.y))(-chi[k] * (double)(mag * sn));
-                s_tile[iz * kLinesPerCta + yl] = v;
-                chi_tile[iz * kLinesPerCta + yl] = (float)chi[k];
-                C += (ScanT)chi[k];
-            }
+#pragma unroll 1
+        for (int iz = z0; iz < z1; ++iz) {
+            const Re chi = kFp64 ? (Re)s_tile[iz * kLinesPerCta + yl].x : (Re)chi_tile[iz * kLinesPerCta + yl];
+            const ScanT mag = exp(-a_att * C);
+            ScanT sn, cs;
+            sincos(a_ph * C, &sn, &cs);
+            Cx v;
+            v.x = chi * (Re)(mag * cs);
+            v.y = -chi * (Re)(mag * sn);
+            s_tile[iz * kLinesPerCta + yl] = v;
+            C += (ScanT)chi;
         }
     }
     __syncthreads();
