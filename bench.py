@@ -42,7 +42,144 @@ def parse():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--cpu-sample-pixels", type=int, default=32768)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=0,
+                    help="run the serving mix with this many requests and print its own JSON line")
+    ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--fit-step", type=int, default=0,
+                    help="time this many forward+gradient fit steps of the 96^3 l<=6 workload and print a JSON line")
+    ap.add_argument("--short-serving", type=int, default=240,
+                    help="requests of the short serving run folded into the default line (0: skip)")
     return ap.parse_args()
+
+
+def serving_targets(reqs, precision):
+    """Fit targets: the intensity of each request's perturbed shape, computed by
+    the library with one handle per distinct geometry (untimed set-up)."""
+    import torch
+    import paper_2202_03411_gb300 as sm
+    handles, out = {}, []
+    for r in reqs:
+        g = r.geometry
+        key = (g.nx, g.det_nx)
+        if key not in handles:
+            handles[key] = sm.scatman_create(g, precision, soft=True, soft_width=0.5)
+        h = handles[key]
+        I = torch.empty(g.n_pix, dtype=torch.float32, device="cuda")
+        sm.scatman_voxelise(h, r.target)
+        sm.scatman_forward(h, I)
+        out.append(I)
+    for h in handles.values():
+        sm.scatman_sync(h)
+    res = [t.cpu().numpy() for t in out]
+    for h in handles.values():
+        h.close()
+    return res
+
+
+def serving_run(n_requests, slots, precision, fractions=(0.5, 0.8, 0.95), seed=0):
+    """Serving mix: forward + gradient fit requests over grids {48,64,96,128}^3 and
+    detectors {128,256,512}^2, admitted under a 120 GB budget.  First all
+    requests arrive at once (saturation throughput), then Poisson streams at
+    the given fractions of it.  Latency is submit-to-result."""
+    import numpy as np
+    from paper_2202_03411_gb300.serving import Server, run_stream
+    from workloads import serving_mix
+    reqs = serving_mix(n_requests, rate_per_s=1.0, seed=seed)     # arrival times rescaled below
+    targets = serving_targets(reqs, precision)
+    budget = 120 * (1 << 30)
+    srv = Server(budget, slots=slots, precision=precision)
+    # warm the slots' handles for every geometry (untimed)
+    warm = {}
+    for r, t in zip(reqs, targets):
+        warm.setdefault((r.geometry.nx, r.geometry.det_nx), (r, t))
+    run_stream(srv, [r for r, _ in warm.values()], [t for _, t in warm.values()], time_scale=0.0)
+    _, lat, status, wall = run_stream(srv, reqs, targets, time_scale=0.0)
+    sat = len(reqs) / wall
+    out = {"requests": len(reqs), "slots": slots, "saturation_patterns_per_s": sat,
+           "saturation_p50_ms": 1e3 * float(np.percentile(lat, 50)),
+           "saturation_p99_ms": 1e3 * float(np.percentile(lat, 99)), "failed": int(sum(1 for x in status if x))}
+    runs = []
+    mean_gap = reqs[-1].arrival_s / len(reqs)
+    for f in fractions:
+        scale = 1.0 / (f * sat * mean_gap)          # arrival rate = f * saturation
+        _, lat, status, wall = run_stream(srv, reqs, targets, time_scale=scale)
+        runs.append({"load": f, "offered_per_s": f * sat, "patterns_per_s": len(reqs) / wall,
+                     "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                     "failed": int(sum(1 for x in status if x))})
+    out["poisson"] = runs
+    out["stats"] = srv.stats()
+    srv.close()
+    return out
+
+
+def fit_step_run(n_shapes, precision, warm=2):
+    """Forward + gradient fit steps on the 96^3 / 256^2 l<=6 harmonics workload
+    (soft occupancy, loss sum (I - I_target)^2).  Per step: voxelise,
+    contraction, residual, adjoint (scatman_backward, which synchronises)."""
+    import numpy as np
+    import torch
+    import paper_2202_03411_gb300 as sm
+    from workloads import perturbed, sh_grad_96
+    g, shapes = sh_grad_96(n_shapes=n_shapes)
+    h = sm.scatman_create(g, precision, soft=True, soft_width=0.5)
+    I = torch.empty(g.n_pix, dtype=torch.float32, device="cuda")
+    targets = []
+    for k, s in enumerate(shapes):
+        sm.scatman_voxelise(h, perturbed(s, np.random.default_rng(k)))
+        sm.scatman_forward(h, I)
+        targets.append(I.clone())
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    rows = []
+    for it, (s, t) in enumerate(list(zip(shapes, targets))[:warm] + list(zip(shapes, targets))):
+        ev[0].record(stream)
+        sm.scatman_voxelise(h, s)
+        ev[1].record(stream)
+        sm.scatman_forward(h, I)
+        ev[2].record(stream)
+        w = 2.0 * (I - t)
+        ev[3].record(stream)
+        sm.scatman_backward(h, w)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        if it >= warm:
+            rows.append([ev[i].elapsed_time(ev[i + 1]) for i in range(4)])
+    h.close()
+    a = np.array(rows)
+    tot = a.sum(1)
+    return {"workload": "sh_l6_R36_grid96_det256_45deg_soft", "precision": precision, "steps": len(rows),
+            "fit_steps_per_s": 1e3 / tot.mean(), "p50_ms": float(np.percentile(tot, 50)),
+            "p99_ms": float(np.percentile(tot, 99)),
+            "stage_ms": {"voxelise": float(a[:, 0].mean()), "forward": float(a[:, 1].mean()),
+                         "residual": float(a[:, 2].mean()), "backward": float(a[:, 3].mean())}}
+
+
+def fp32_comparator(g, shapes, n=3):
+    """The plain FP32 CUDA-core MSFT on the same patterns: patterns/s and its
+    rel. L2 difference from the tensor-core result of pattern 0."""
+    import torch
+    import paper_2202_03411_gb300 as sm
+    h = sm.scatman_create(g, "fp32")
+    I = torch.empty(g.n_pix, dtype=torch.float32, device="cuda")
+    sm.scatman_voxelise(h, shapes[0])
+    sm.scatman_forward(h, I)
+    sm.scatman_sync(h)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    for s in shapes[:n]:
+        sm.scatman_voxelise(h, s)
+        sm.scatman_forward(h, I)
+    e1.record(stream)
+    sm.scatman_sync(h)
+    ms = e0.elapsed_time(e1) / n
+    sm.scatman_voxelise(h, shapes[0])
+    sm.scatman_forward(h, I)
+    sm.scatman_sync(h)
+    I0 = I.double().cpu().numpy()
+    h.close()
+    return {"patterns_per_s": 1e3 / ms, "ms_per_pattern": ms}, I0
 
 
 def dist_env():
@@ -189,6 +326,25 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.fit_step > 0:
+        import __graft_entry__
+        __graft_entry__.build()
+        res = fit_step_run(args.fit_step, args.precision)
+        print(json.dumps({"metric": "MSFT forward+gradient fit steps/s (96^3 harmonics, 256^2 detector)",
+                          "value": res["fit_steps_per_s"], "unit": "fit steps/s", "n_gpus": 1,
+                          "higher_is_better": True, "data": "synthetic", "fit_step": res}), flush=True)
+        return
+    if args.serving > 0:
+        import __graft_entry__
+        __graft_entry__.build()
+        res = serving_run(args.serving, args.serving_slots, args.precision)
+        line = {"metric": "MSFT forward+gradient fit requests/s (serving mix, 120 GB budget)",
+                "value": res["saturation_patterns_per_s"], "unit": "requests/s", "n_gpus": 1,
+                "higher_is_better": True, "dtype": "bf16" if "bf16" in args.precision else "f16",
+                "data": "synthetic", "config": {"workload": "serving_mix_grids48-128_det128-512",
+                                                "precision": args.precision}, "serving": res}
+        print(json.dumps(line), flush=True)
+        return
     rank, world, local_rank = dist_env()
     import numpy as np
     import torch
@@ -297,10 +453,19 @@ def main():
     e2e = {"value": world * B * args.steps / e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    I0 = I_all[0].double().cpu().numpy()
+    fp32, I0_fp32 = fp32_comparator(g, shapes)
     cpu = None
     err = None
+    err_fp32 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, err = cpu_baseline(shapes, g, I_all[0].double().cpu().numpy(), args.cpu_sample_pixels)
+        cpu, err = cpu_baseline(shapes, g, I0, args.cpu_sample_pixels)
+        _, err_fp32 = cpu_baseline(shapes, g, I0_fp32, 512)
+    fp32["rel_l2_I_vs_fp64_oracle"] = err_fp32
+    fit = fit_step_run(32, args.precision) if world == 1 else None
+    serving = None
+    if args.short_serving > 0 and world == 1:
+        serving = serving_run(args.short_serving, args.serving_slots, args.precision, fractions=(0.8,))
 
     pat_sorted = sorted(pat_ms)
     p50 = pat_sorted[len(pat_sorted) // 2]
@@ -319,6 +484,9 @@ def main():
         "stage_ms": {"voxelise_scan": statistics.mean(vox_ms), "contraction": statistics.mean(fwd_ms)},
         "error_vs_fp64_oracle": {"rel_l2_I": err, "on": "cpu_baseline sample of pattern 0"},
         "roofline": roofline,
+        "fp32_cuda_core_comparator": fp32,
+        "fit_step_96": fit,
+        "serving_short": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": 2 * B * args.steps,

@@ -214,6 +214,69 @@ SCATMAN_API const char *scatman_last_error(const scatman_handle *h);
 /* Releases every buffer and the owned stream.  Accepts NULL. */
 SCATMAN_API void scatman_destroy(scatman_handle *h);
 
+
+/* ------------------------------------------------------------------------
+ * Serving: many concurrent shape fits (the paper's forward-fitting use,
+ * Sec. 6) multiplexed onto one GPU.  A native scheduler keeps a FIFO of
+ * requests and `slots` worker streams.  A request is admitted as soon as a
+ * slot is free and the device bytes it needs fit under hbm_budget_bytes
+ * (continuous admission: work of admitted requests overlaps on the device).
+ * Each slot keeps the handle of its last geometry, so repeated requests of a
+ * fit reuse their device buffers.  Every request runs the same kernels with
+ * the same fixed reduction orders whatever else is in flight, so its result
+ * does not depend on the mix.
+ * ---------------------------------------------------------------------- */
+typedef struct scatman_server scatman_server;
+
+typedef struct {
+    long long hbm_budget_bytes;   /* device bytes the server may hold (> 0) */
+    int slots;                    /* requests in flight at once, 1..64 */
+    int precision;                /* scatman_precision of every request */
+    double soft_width;            /* requests use soft occupancy of this width (> 0) */
+} scatman_server_config;
+
+/* One fit request.  Input arrays are copied during scatman_server_submit;
+ * output arrays must stay valid until scatman_server_wait returns for it. */
+typedef struct {
+    scatman_config geometry;      /* grid and detector; precision/soft fields ignored */
+    scatman_shape shape;
+    const float *target;          /* host, n_pix floats; loss = sum (I - target)^2 */
+    int want_gradient;            /* 1: also dloss/dparams (scatman_backward order) */
+    float *I_out;                 /* host, n_pix floats, or NULL (intensity as float in every mode) */
+    double *grad_out;             /* host, param count doubles (with want_gradient) */
+    double *loss_out;             /* host, 1 double, or NULL */
+} scatman_request;
+
+typedef struct {
+    long long submitted, completed, failed;
+    long long bytes_reserved, bytes_reserved_peak;
+    int inflight, inflight_peak;
+} scatman_server_stats;
+
+/* Creates the server on the current device.  Errors: ERR_ARG, ERR_CUDA,
+ * ERR_UNSUPPORTED. */
+SCATMAN_API int scatman_server_create(const scatman_server_config *cfg, scatman_server **out);
+
+/* Queues a request; *ticket identifies it.  Returns ERR_ADMISSION if the
+ * request alone needs more than the budget, ERR_ARG for invalid geometry or
+ * shape (the request is not queued then). */
+SCATMAN_API int scatman_server_submit(scatman_server *srv, const scatman_request *req, long long *ticket);
+
+/* Waits up to timeout_s seconds (< 0: forever) for a request.  Returns
+ * ERR_TIMEOUT if it is still running, otherwise OK with *status set to the
+ * request's own status and *latency_s to submit-to-completion time. */
+SCATMAN_API int scatman_server_wait(scatman_server *srv, long long ticket, double timeout_s, int *status,
+                                    double *latency_s);
+
+SCATMAN_API int scatman_server_stats_get(scatman_server *srv, scatman_server_stats *out);
+
+/* Drains queued and running requests, then frees every handle and thread. */
+SCATMAN_API void scatman_server_destroy(scatman_server *srv);
+
+/* Device bytes a handle of this configuration allocates (forward and
+ * backward buffers), as the server's admission uses it.  -1 on bad input. */
+SCATMAN_API long long scatman_footprint_bytes(const scatman_config *cfg);
+
 /*
  * Forward pass that allocates no device memory (the paper has no counterpart;
  * this is a service to callers that cannot call cudaMalloc -- for example a

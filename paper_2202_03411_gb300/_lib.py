@@ -60,6 +60,23 @@ class scatman_shape(ctypes.Structure):
     ]
 
 
+class scatman_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_longlong), ("slots", ctypes.c_int), ("precision", ctypes.c_int),
+                ("soft_width", ctypes.c_double)]
+
+
+class scatman_request(ctypes.Structure):
+    _fields_ = [("geometry", scatman_config), ("shape", scatman_shape), ("target", ctypes.POINTER(ctypes.c_float)),
+                ("want_gradient", ctypes.c_int), ("I_out", ctypes.POINTER(ctypes.c_float)), ("grad_out", _D),
+                ("loss_out", _D)]
+
+
+class scatman_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("bytes_reserved", ctypes.c_longlong), ("bytes_reserved_peak", ctypes.c_longlong),
+                ("inflight", ctypes.c_int), ("inflight_peak", ctypes.c_int)]
+
+
 # name -> (restype, argtypes); every symbol include/scatman.h declares
 SIGNATURES = {
     "scatman_create": (ctypes.c_int, [ctypes.POINTER(scatman_config), ctypes.c_void_p,
@@ -79,6 +96,14 @@ SIGNATURES = {
     "scatman_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "scatman_destroy": (None, [ctypes.c_void_p]),
     "scatman_version": (ctypes.c_char_p, []),
+    "scatman_server_create": (ctypes.c_int, [ctypes.POINTER(scatman_server_config), ctypes.POINTER(ctypes.c_void_p)]),
+    "scatman_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(scatman_request),
+                                             ctypes.POINTER(ctypes.c_longlong)]),
+    "scatman_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
+    "scatman_server_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(scatman_server_stats)]),
+    "scatman_server_destroy": (None, [ctypes.c_void_p]),
+    "scatman_footprint_bytes": (ctypes.c_longlong, [ctypes.POINTER(scatman_config)]),
     "scatman_forward_noalloc": (ctypes.c_int, [ctypes.POINTER(scatman_config), ctypes.POINTER(scatman_shape),
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }

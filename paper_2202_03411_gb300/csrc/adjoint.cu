@@ -110,15 +110,17 @@ cudaError_t launch_adjoint_field(bool fp64, const void *A, const void *dLdI, con
     if (threads > 1024) return cudaErrorInvalidValue;
     const size_t cx = fp64 ? sizeof(double2) : sizeof(float2);
     const size_t smem = cx * (size_t)kAdjPix * (2 + kAdjX + ych);
+    // the largest size (64 y-runs, 1024 threads), so concurrent launches never race on the attribute
+    const int smem_max = (int)(cx * kAdjPix * (2 + kAdjX + 64));
     if (fp64) {
         cudaError_t e = cudaFuncSetAttribute(adjoint_field_kernel<double>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
         adjoint_field_kernel<double><<<grid, threads, smem, st>>>((const double2 *)A, (const double *)dLdI, q, n_pix,
                                                                   nx, ny, nz, voxel, (double2 *)S);
     } else {
         cudaError_t e = cudaFuncSetAttribute(adjoint_field_kernel<float>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
         adjoint_field_kernel<float><<<grid, threads, smem, st>>>((const float2 *)A, (const float *)dLdI, q, n_pix,
                                                                  nx, ny, nz, voxel, (float2 *)S);
@@ -373,6 +375,45 @@ cudaError_t launch_grad_pixels(bool fp64, const void *A, const void *dLdI, long 
         grad_pixel_kernel<double><<<n_blocks, 256, 0, st>>>((const double2 *)A, (const double *)dLdI, n_pix, partials);
     else
         grad_pixel_kernel<float><<<n_blocks, 256, 0, st>>>((const float2 *)A, (const float *)dLdI, n_pix, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace scm
+
+namespace scm {
+
+// Least-squares fit residual: w = dL/dI = 2 (I - target) and per-block
+// partial sums of (I - target)^2 (summed on the host in block order).
+template <typename R>
+__global__ void l2_residual_kernel(const R *__restrict__ I, const float *__restrict__ target, long long n,
+                                   R *__restrict__ w, double *__restrict__ partials) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const R d = I[p] - (R)target[p];
+        w[p] = (R)2 * d;
+        s += (double)d * (double)d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+int l2_residual_blocks(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 256 ? b : 256);
+}
+
+cudaError_t launch_l2_residual(bool fp64, const void *I, const float *target, long long n, void *w, double *partials,
+                               int n_blocks, cudaStream_t st) {
+    if (fp64)
+        l2_residual_kernel<double><<<n_blocks, 256, 0, st>>>((const double *)I, target, n, (double *)w, partials);
+    else
+        l2_residual_kernel<float><<<n_blocks, 256, 0, st>>>((const float *)I, target, n, (float *)w, partials);
     return cudaGetLastError();
 }
 

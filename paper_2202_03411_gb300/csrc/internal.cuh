@@ -164,6 +164,10 @@ int grad_voxel_blocks(const GridParams &gp);
 cudaError_t launch_grad_pixels(bool fp64, const void *A, const void *dLdI, long long n_pix,
                                double *partials, int n_blocks, cudaStream_t st);
 int grad_pixel_blocks(long long n_pix);
+// Fit residual 2 (I - target) and partial sums of (I - target)^2 (adjoint.cu).
+int l2_residual_blocks(long long n);
+cudaError_t launch_l2_residual(bool fp64, const void *I, const float *target, long long n, void *w, double *partials,
+                               int n_blocks, cudaStream_t st);
 
 }  // namespace scm
 

@@ -523,7 +523,10 @@ cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n
     P.I = I;
     P.err = err;
     size_t smem = (size_t)(split ? 2 : 1) * P.nkb * kKBlockBytes + (size_t)P.stages * Nxp * 2 * 128 + tc_fixed_bytes();
-    cudaError_t e = cudaFuncSetAttribute(msft_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The attribute is per function and shared by every thread of the process:
+    // always raise it to the largest size any launch uses, never to this
+    // launch's size, so concurrent launches from other threads stay valid.
+    cudaError_t e = cudaFuncSetAttribute(msft_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e != cudaSuccess) return e;
     int grid = P.num_m_tiles < sm_count ? P.num_m_tiles : sm_count;
     if (grid < 1) grid = 1;

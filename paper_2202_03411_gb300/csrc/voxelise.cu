@@ -146,20 +146,23 @@ cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const S
     dim3 grid(gp.nx, (gp.ny + kLinesPerCta - 1) / kLinesPerCta);
     size_t cx = fp64_mode ? sizeof(double2) : sizeof(float2);
     size_t smem = (cx + sizeof(float)) * (size_t)gp.nz * kLinesPerCta;
+    // per-function attribute shared by all threads: set it to the largest size
+    // (nz = 256) so a concurrent launch from another thread is never rejected
+    const int smem_max = (int)((cx + sizeof(float)) * 32 * kMaxRun * kLinesPerCta);
     cudaError_t e;
     if (fp64_mode) {
         auto k = voxelise_scan_kernel<true, double>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
         k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
     } else if (scan_fp64) {
         auto k = voxelise_scan_kernel<false, double>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
         k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
     } else {
         auto k = voxelise_scan_kernel<false, float>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
         if (e != cudaSuccess) return e;
         k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
     }

@@ -76,3 +76,14 @@ def test_no_device_is_reported(lib):
     code, ptr, msg = _create(lib, Geometry(8, 8, 8, 1.0, 8.0, 30.0, 8, 8), "fp32")
     assert code == _lib.SCATMAN_ERR_UNSUPPORTED and not ptr
     assert msg
+
+
+def test_footprint_is_a_host_calculation(lib):
+    from paper_2202_03411_gb300.serving import footprint_bytes
+    small = Geometry(48, 48, 48, 1.0, 10.0, 45.0, 128, 128)
+    big = Geometry(128, 128, 128, 1.0, 10.0, 45.0, 512, 512)
+    for prec in ("fp64", "fp32", "tc_bf16_split"):
+        assert 0 < footprint_bytes(small, prec) < footprint_bytes(big, prec)
+    assert footprint_bytes(big, "tc_bf16_split") < footprint_bytes(big, "fp64")
+    # the largest serving request fits many times into a 120 GB budget
+    assert footprint_bytes(big, "tc_bf16_split") < (120 << 30) // 100
