@@ -187,6 +187,22 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_batch(rank: int, batch: int):
+    """The independent patterns rank `rank` simulates: its own seeds, no overlap."""
+    from workloads import sh_128
+    return sh_128(n_shapes=batch, seed0=rank * batch)
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The job's time is the slowest rank's (all_reduce MAX); identity for one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def recorded_traffic(kernel: str, source: str):
     """DRAM bytes per launch from the committed ncu summary, if the kernel's
     source is unchanged since that capture (else None)."""
@@ -360,9 +376,7 @@ def main():
     if dist is not None:
         dist.barrier()
     import paper_2202_03411_gb300 as sm
-    from workloads import sh_128
-
-    g, shapes = sh_128(n_shapes=args.batch, seed0=rank * args.batch)
+    g, shapes = rank_batch(rank, args.batch)
     B = len(shapes)
     stream = torch.cuda.current_stream()
     h = sm.scatman_create(g, args.precision)
@@ -408,11 +422,7 @@ def main():
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     value = world * B * args.steps / (total_ms / 1e3)
 
     # roofline of the contraction kernel (the dominant launch)
@@ -443,11 +453,7 @@ def main():
     for _ in range(args.steps):
         for b, s in enumerate(shapes):
             sm.scatman_acquire(h, s, I_host[b].numpy())
-    e_el = time.perf_counter() - e0
-    if dist is not None:
-        t = torch.tensor([e_el], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_el = float(t.item())
+    e_el = max_over_ranks(time.perf_counter() - e0, dist, "cuda")
     h2d = B * (8 * (shapes[0].lmax + 1) ** 2 + 160)      # shape struct + coefficients handed over
     d2h = B * g.n_pix * 4
     e2e = {"value": world * B * args.steps / e_el, "unit": UNIT, "h2d_bytes_per_step": h2d,
