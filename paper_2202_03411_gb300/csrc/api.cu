@@ -138,6 +138,8 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_part);
     cudaFree(h->d_S);
     cudaFree(h->d_partial);
+    cudaFree(h->d_adj_part);
+    cudaFree(h->d_gmax);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (dev_prev >= 0) cudaSetDevice(dev_prev);
     delete h;
@@ -463,10 +465,29 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
         if ((rc = alloc_dev(h, (void **)&h->d_part, need * sizeof(double), "gradient partials"))) return rc;
         h->part_count = need;
     }
-    rc = check_cuda(h, launch_adjoint_field(f64, h->d_A, dLdI_dev, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
-                                            h->d_S, h->stream),
-                    "adjoint field");
-    if (rc) return rc;
+    if (h->tensor_core && adjoint_tc_supported(c.nx, c.ny)) {
+        // adjoint contraction on the tensor cores
+        const int splits = adjoint_tc_splits(h->n_pix, c.nz, h->sm_count);
+        const size_t cnt = (size_t)splits * nvox;
+        if (h->adj_part_count < cnt) {
+            cudaFree(h->d_adj_part);
+            h->d_adj_part = nullptr;
+            if ((rc = alloc_dev(h, (void **)&h->d_adj_part, cnt * sizeof(float2), "adjoint partial fields")))
+                return rc;
+            h->adj_part_count = cnt;
+        }
+        if (!h->d_gmax && (rc = alloc_dev(h, (void **)&h->d_gmax, sizeof(unsigned), "adjoint scale"))) return rc;
+        rc = check_cuda(h, launch_adjoint_tc((const float2 *)h->d_A, (const float *)dLdI_dev, h->d_q, h->n_pix, c.nx,
+                                             c.ny, c.nz, c.voxel, splits, h->d_adj_part, h->d_gmax, (float2 *)h->d_S,
+                                             h->d_err, h->stream),
+                        "adjoint field (tensor cores)");
+        if (rc) return rc;
+    } else {
+        rc = check_cuda(h, launch_adjoint_field(f64, h->d_A, dLdI_dev, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
+                                                h->d_S, h->stream),
+                        "adjoint field");
+        if (rc) return rc;
+    }
     rc = check_cuda(h, launch_grad_voxels(f64, h->sp, gp, h->d_S, h->d_part, nvb, h->stream), "voxel gradient");
     if (rc) return rc;
     rc = check_cuda(h, launch_grad_pixels(f64, h->d_A, dLdI_dev, h->n_pix, h->d_part + (size_t)nvb * (ng + 2), npb,

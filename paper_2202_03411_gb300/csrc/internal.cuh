@@ -117,6 +117,9 @@ struct scatman_handle {
     size_t part_count = 0;
     void *d_S = nullptr;            // backward adjoint field (complex, nvox)
     void *d_partial = nullptr;      // CUDA-core contraction: per-split partial fields
+    float2 *d_adj_part = nullptr;   // tensor-core adjoint: per-pixel-range partial fields
+    size_t adj_part_count = 0;
+    unsigned *d_gmax = nullptr;     // tensor-core adjoint: max |w A| (float bits)
     int splits = 1;
     long long device_bytes = 0;
     CUtensorMap tmap_B;
@@ -164,6 +167,12 @@ int grad_voxel_blocks(const GridParams &gp);
 cudaError_t launch_grad_pixels(bool fp64, const void *A, const void *dLdI, long long n_pix,
                                double *partials, int n_blocks, cudaStream_t st);
 int grad_pixel_blocks(long long n_pix);
+// Tensor-core adjoint field (adjoint_tc.cu).
+bool adjoint_tc_supported(int nx, int ny);
+int adjoint_tc_splits(long long n_pix, int nz, int sm_count);
+cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const double *q, long long n_pix, int nx, int ny, int nz,
+                              double voxel, int splits, float2 *partial, unsigned *gmax_bits, float2 *S, int *err,
+                              cudaStream_t st);
 // Fit residual 2 (I - target) and partial sums of (I - target)^2 (adjoint.cu).
 int l2_residual_blocks(long long n);
 cudaError_t launch_l2_residual(bool fp64, const void *I, const float *target, long long n, void *w, double *partials,
