@@ -207,6 +207,16 @@ SCATMAN_API int scatman_get_occupancy(scatman_handle *h, double *chi_host);
 SCATMAN_API int scatman_get_slices(scatman_handle *h, double *s_host);
 SCATMAN_API int scatman_get_q(scatman_handle *h, double *q_host);
 
+/*
+ * Real floating-point operations of one contraction launch for the current
+ * shape: *issued counts what the tensor-core kernel executes (it skips the
+ * parts of each slice outside the occupied box, and counts both products of
+ * a split-phase mode); *dense is 8 flop per (pixel, voxel) pair times the
+ * number of products.  CUDA-core modes report the dense count for both.
+ * Synchronises.  Errors: ERR_STATE before voxelise.
+ */
+SCATMAN_API int scatman_contraction_flops(scatman_handle *h, double *issued, double *dense);
+
 /* Text of the last error on this handle ("" if none), owned by the handle.
  * With h == NULL: the reason the calling thread's last scatman_create failed. */
 SCATMAN_API const char *scatman_last_error(const scatman_handle *h);

@@ -93,6 +93,7 @@ SIGNATURES = {
     "scatman_get_occupancy": (ctypes.c_int, [ctypes.c_void_p, _D]),
     "scatman_get_slices": (ctypes.c_int, [ctypes.c_void_p, _D]),
     "scatman_get_q": (ctypes.c_int, [ctypes.c_void_p, _D]),
+    "scatman_contraction_flops": (ctypes.c_int, [ctypes.c_void_p, _D, _D]),
     "scatman_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "scatman_destroy": (None, [ctypes.c_void_p]),
     "scatman_version": (ctypes.c_char_p, []),

@@ -177,6 +177,14 @@ def scatman_get_q(h: Handle) -> np.ndarray:
     return out
 
 
+def scatman_contraction_flops(h: Handle):
+    """(issued, dense) real flops of one contraction launch for the current shape."""
+    a = ctypes.c_double()
+    b = ctypes.c_double()
+    _check(_lib.load().scatman_contraction_flops(h.ptr, ctypes.byref(a), ctypes.byref(b)), h)
+    return a.value, b.value
+
+
 def scatman_destroy(h: Handle) -> None:
     h.close()
 

@@ -130,6 +130,7 @@ void scatman_destroy(scatman_handle *h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     cudaFree(h->d_q);
+    cudaFree(h->d_bounds);
     cudaFree(h->d_chi);
     cudaFree(h->d_s);
     cudaFree(h->d_A);
@@ -196,11 +197,11 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
 
     if (h->tensor_core) {
         h->Nxp = (int)round_up(c.nx, 16);
-        h->Nyp = (int)round_up(c.ny, 8);
-        h->Kp = 2 * h->Nyp;
+        h->Nyp = (int)round_up(c.ny, 16);
+        h->Kp = h->Nyp;                       // K extent of one slice-operand row
         if (h->Nxp > 128)
             return fail(set_error(h, SCATMAN_ERR_ARG, "tensor-core modes support nx <= 128"));
-        if (tc_max_stages(h->Kp, h->Nxp, h->split) < 2)
+        if (tc_max_stages(h->Nyp, h->Nxp, h->split) < 2)
             return fail(set_error(h, SCATMAN_ERR_ARG, "ny too large for the tensor-core phase tile"));
         h->b_rows = (size_t)c.nz * 2 * h->Nxp;
     }
@@ -219,6 +220,9 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     int rc;
     if ((rc = alloc_dev(h, (void **)&h->d_q, npix * 3 * sizeof(double), "q buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, (void **)&h->d_chi, nvox * sizeof(float), "occupancy buffer"))) return fail(rc);
+    if (h->tensor_core &&
+        (rc = alloc_dev(h, (void **)&h->d_bounds, 4 * (size_t)c.nz * sizeof(int), "slice bounds")))
+        return fail(rc);
     if (h->tensor_core) {
         h->s_bytes = h->b_rows * (size_t)h->Kp * 2;
     } else {
@@ -312,6 +316,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     so.Kp = h->Kp;
     so.s = h->d_s;
     so.chi = h->d_chi;
+    so.bounds = h->d_bounds;
     double strength = std::fmax(std::fabs(s->delta), std::fabs(s->beta));
     h->scan_fp64 = c.scan_fp64 || (h->k0 * c.voxel * c.nz * strength > 5.0);
     int rc = check_cuda(h, launch_voxelise(sp, gp, so, h->scan_fp64, h->precision == SCATMAN_FP64, h->stream),
@@ -333,8 +338,8 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
     cudaError_t e;
     if (h->tensor_core) {
         e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, h->Kp, c.voxel, str_re,
-                           str_im, h->split, h->bf16, (float2 *)h->d_A, (float *)I_dev, h->d_err, h->sm_count,
-                           h->stream);
+                           str_im, h->split, h->bf16, h->d_bounds, (float2 *)h->d_A, (float *)I_dev, h->d_err,
+                           h->sm_count, h->stream);
     } else {
         e = launch_msft_simt(h->precision == SCATMAN_FP64, h->d_s, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
                              str_re, str_im, h->d_A, I_dev, h->d_partial, h->splits, h->stream);
@@ -429,9 +434,30 @@ int scatman_get_slices(scatman_handle *h, double *s_host) {
                     size_t row_r = (size_t)iz * 2 * h->Nxp + ix;
                     size_t v = ((size_t)iz * c.nx + ix) * c.ny + iy;
                     s_host[2 * v] = half_bits_to_float(B[row_r * h->Kp + iy], h->bf16);
-                    s_host[2 * v + 1] = half_bits_to_float(B[(row_r + h->Nxp) * h->Kp + iy], h->bf16);
+                    s_host[2 * v + 1] = half_bits_to_float(B[(row_r + h->Nxp) * h->Kp + iy], h->bf16);   // Im row
                 }
     }
+    return SCATMAN_OK;
+}
+
+int scatman_contraction_flops(scatman_handle *h, double *issued, double *dense) {
+    if (!h || !issued || !dense) return SCATMAN_ERR_ARG;
+    if (!h->have_shape) return set_error(h, SCATMAN_ERR_STATE, "no voxelised shape");
+    const scatman_config &c = h->cfg;
+    const double dense_pairs = (double)h->n_pix * c.nx * c.ny * c.nz;
+    if (!h->tensor_core) {
+        *dense = 8.0 * dense_pairs;
+        *issued = *dense;
+        return SCATMAN_OK;
+    }
+    std::vector<int> b(4 * (size_t)c.nz);
+    int rc = check_cuda(h, cudaMemcpyAsync(b.data(), h->d_bounds, b.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                                           h->stream),
+                        "bounds download");
+    if (rc) return rc;
+    if ((rc = scatman_sync(h))) return rc;
+    *dense = 8.0 * dense_pairs * (h->split ? 2.0 : 1.0);
+    *issued = tc_issued_flops(b.data(), c.nz, h->Nxp, h->Nyp, h->n_pix, h->split);
     return SCATMAN_OK;
 }
 
@@ -679,6 +705,7 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
     so.Nxp = so.Nyp = so.Kp = 0;
     so.s = d_s;
     so.chi = d_chi;
+    so.bounds = nullptr;
     const double strength = std::fmax(std::fabs(s->delta), std::fabs(s->beta));
     const bool scan_fp64 = c.scan_fp64 || (k0 * c.voxel * c.nz * strength > 5.0);
     e = launch_voxelise(sp, gp, so, scan_fp64, false, st);

@@ -82,9 +82,10 @@ enum SliceLayout { kLayoutC64 = 0, kLayoutC32 = 1, kLayoutTcF16 = 2, kLayoutTcBF
 
 struct SliceOut {
     int layout;
-    int Nxp, Nyp, Kp;               // tensor-core operand: padded x, y and K = 2*Nyp
+    int Nxp, Nyp, Kp;               // tensor-core operand: padded x and y; Kp = Nyp, the K extent of a row
     void *s;                        // C64: double2[nvox]; C32: float2[nvox]; TC: 16-bit [nz*2*Nxp][Kp]
     float *chi;                     // occupancy [z][x][y]
+    int *bounds;                    // per slice [x_lo | x_hi | y_lo | y_hi] of chi != 0 (nz each), or null
 };
 
 }  // namespace scm
@@ -107,6 +108,7 @@ struct scatman_handle {
     size_t b_rows = 0;
     // device buffers
     double *d_q = nullptr;          // [n_pix][3]
+    int *d_bounds = nullptr;        // per-slice occupied box [x_lo | x_hi | y_lo | y_hi], 4*nz ints
     float *d_chi = nullptr;         // [nvox]
     void *d_s = nullptr;            // slices in the contraction's layout
     size_t s_bytes = 0;
@@ -151,11 +153,13 @@ cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long lon
                              int nz, double voxel, double str_re, double str_im, void *A, void *I,
                              void *partial, int splits, cudaStream_t st);
 // Tensor-core contraction (msft_tc.cu).
-int tc_max_stages(int Kp, int Nxp, bool split);
+int tc_max_stages(int Nyp, int Nxp, bool split);
 cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n_pix, int nx, int ny,
                            int nz, int Nxp, int Nyp, int Kp, double voxel, double str_re, double str_im,
-                           bool split, bool bf16, float2 *A, float *I, int *err, int sm_count,
+                           bool split, bool bf16, const int *bounds, float2 *A, float *I, int *err, int sm_count,
                            cudaStream_t st);
+// Real flops one contraction launch issues for the given per-slice boxes.
+double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
 bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, bool bf16, std::string *why);
 // Backward (adjoint.cu).
 cudaError_t launch_adjoint_field(bool fp64, const void *A, const void *dLdI, const double *q, long long n_pix,

@@ -3,21 +3,23 @@
 // Per slice j the 2D sum over (x, y) is factored as
 //   G[q, (j,x)] = sum_y e^{-i q_y y} s_j(x, y)          (dense complex contraction)
 //   A[q]        = (n^2-1) sum_j e^{-i q_z z_j} sum_x e^{-i q_x x} G[q, (j,x)]
-// The first line is one real GEMM per slice, D[m, n] = sum_k P[m, k] B[n, k]:
-//   m  = pixel (128 per tile),  k = [cos part: y | sin part: y]  (K = 2*Nyp),
-//   n  = [Re G: x | Im G: x]  (N = 2*Nxp),
-//   P[m, y] = cos(q_y y),  P[m, Nyp+y] = -sin(q_y y)            (e^{-i q_y y}),
-//   B[(x,re), y] = Re s,  B[(x,re), Nyp+y] = -Im s,
-//   B[(x,im), y] = Im s,  B[(x,im), Nyp+y] = Re s.
-// P is built in shared memory once per pixel tile; with split phases it is
-// held as an FP16/BF16 pair P = P_hi + P_lo and both halves are multiplied
-// into the same FP32 accumulator.  B tiles (one slice per N-tile) stream in
-// through TMA with 128-byte swizzle.  Accumulators live in tensor memory,
-// double buffered, and eight epilogue warps apply the x- and z-phases
+// The first line is a complex GEMM per slice, done as four real MMA chains
+// with K = y and N = x:
+//   Re G += Pr Sr,  Re G += (-Pi) Si,  Im G += Pr Si,  Im G += Pi Sr,
+//   Pr[m, y] = cos(q_y y), Pi[m, y] = -sin(q_y y)   (e^{-i q_y y}),
+//   Sr[x, y] = Re s_j(x, y), Si[x, y] = Im s_j(x, y),
+// the minus sign coming from the instruction descriptor's negate-A bit.
+// The phase operand [Pr | Pi] is built in shared memory once per pixel tile;
+// with split phases it is held as an FP16/BF16 pair P = P_hi + P_lo and both
+// halves accumulate into the same FP32 result.  The slice operand streams in
+// through TMA with 128-byte swizzle, one 16-row box per occupied 16-column x
+// chunk: only each slice's occupied box (x chunks, K steps of 16 y) is loaded
+// and multiplied, and empty slices are skipped.  Accumulators live in tensor
+// memory, double buffered, and eight epilogue warps apply the x- and z-phases
 // (second line) while the next slice's MMAs run.
 //
 // Warp roles (320 threads): warps 0-7 epilogue (two per TMEM lane quarter,
-// each half of the x chunks), warp 8 TMA producer, warp 9 MMA issuer and
+// alternating x chunks), warp 8 TMA producer, warp 9 MMA issuer and
 // tensor-memory owner.  Every wait is bounded: on time-out the kernel sets a
 // bit in the error word, releases its tensor memory and returns.
 #include "internal.cuh"
@@ -37,13 +39,15 @@ constexpr int kMaxSmem = 232448;           // 227 KB opt-in per block
 
 struct TcParams {
     const double *q;
+    const int *bounds;          // per-slice occupied box, or null (dense)
     long long n_pix;
     int nx, ny, nz;
-    int Nxp, Nyp, Kp, nkb;
+    int Nxp, Nyp;               // padded x (multiple of 16) and y (multiple of 16)
+    int nkb_a, nkb_b;           // 64-element K blocks of the phase operand (2 Nyp) and of a slice (Nyp)
     int stages;
     int split, bf16;
     int num_m_tiles;
-    uint32_t idesc;
+    uint32_t idesc;             // without the N field (set per slice)
     uint32_t tmem_cols;
     double voxel;
     float str_re, str_im;
@@ -51,6 +55,39 @@ struct TcParams {
     float *I;
     int *err;
 };
+
+// Which part of slice t the contraction touches: x chunks [c_lo, c_hi) of 16
+// columns and a bit mask over K steps of 16 (cos part y, sin part Nyp + y).
+struct TileSpan {
+    bool empty;
+    int c_lo, c_hi;
+    uint32_t kmask;
+};
+
+__host__ __device__ inline uint32_t kstep_range_mask(int a, int b) {
+    // bits floor(a/16) .. ceil(b/16) - 1
+    const int lo = a >> 4, hi = (b + 15) >> 4;
+    uint32_t m = 0;
+    for (int k = lo; k < hi && k < 32; ++k) m |= 1u << k;
+    return m;
+}
+
+__host__ __device__ inline TileSpan tile_span(const int *bounds, int nz, int t, int Nxp, int Nyp) {
+    TileSpan ts;
+    if (!bounds) {
+        ts.empty = false;
+        ts.c_lo = 0;
+        ts.c_hi = Nxp >> 4;
+        ts.kmask = kstep_range_mask(0, Nyp);
+        return ts;
+    }
+    const int xlo = bounds[t], xhi = bounds[nz + t], ylo = bounds[2 * nz + t], yhi = bounds[3 * nz + t];
+    ts.empty = xlo >= xhi || ylo >= yhi;
+    ts.c_lo = ts.empty ? 0 : xlo >> 4;
+    ts.c_hi = ts.empty ? 0 : (xhi + 15) >> 4;
+    ts.kmask = ts.empty ? 0u : kstep_range_mask(ylo, yhi);
+    return ts;
+}
 
 __device__ __forceinline__ uint16_t to16(float v, int bf16) {
     if (bf16) {
@@ -68,6 +105,10 @@ __device__ __forceinline__ float from16(uint16_t u, int bf16) {
     __half h = *reinterpret_cast<__half *>(&u);
     return __half2float(h);
 }
+
+// Byte offset of K element k (a multiple of 16) from the start of a 128-row
+// operand made of 64-element K blocks: the descriptor start of that K step.
+__device__ __forceinline__ uint32_t a_k_offset(int k) { return (uint32_t)((k >> 6) * kKBlockBytes + (k & 63) * 2); }
 
 // Byte offset of 16-byte chunk `c` (8 elements) of row `m` in K-block `kb`
 // of a 128-row operand laid out for the 128-byte swizzle.
@@ -124,7 +165,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     msft_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const uint32_t a_bytes = (uint32_t)P.nkb * kKBlockBytes;
+    const uint32_t a_bytes = (uint32_t)P.nkb_a * kKBlockBytes;
     uint8_t *sA_hi = base;
     uint8_t *sA_lo = base + a_bytes;
     uint8_t *sB = base + (P.split ? 2 : 1) * a_bytes;
@@ -165,7 +206,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     uint32_t prod_it = 0, mma_it = 0, acc_it = 0, epi_it = 0;
     const int nch = P.Nxp >> 4;                 // 16-column chunks per slice
-    const int nch0 = (nch + 1) >> 1;
 
     for (int mt = blockIdx.x; mt < P.num_m_tiles; mt += gridDim.x) {
         if (warp < kEpiWarps) {
@@ -179,15 +219,26 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (lane == 0) {
                 bool ok = true;
                 for (int t = 0; t < P.nz && ok; ++t) {
-                    for (int kb = 0; kb < P.nkb; ++kb) {
+                    const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
+                    if (ts.empty) continue;
+                    const int nchunks = ts.c_hi - ts.c_lo;
+                    const uint32_t bytes = (uint32_t)(2 * nchunks * 16 * 128);
+                    for (int kb = 0; kb < P.nkb_b; ++kb) {
+                        if (((ts.kmask >> (4 * kb)) & 0xFu) == 0) continue;
                         const uint32_t s = prod_it % P.stages, ph = (prod_it / P.stages) & 1;
                         if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutProducer)) {
                             ok = false;
                             break;
                         }
-                        mbar_arrive_expect_tx(smem_u32(&full[s]), stage_bytes);
-                        tma_load_2d(smem_u32(sB + (size_t)s * stage_bytes), &tmap, smem_u32(&full[s]), kb * kBK,
-                                    t * 2 * P.Nxp);
+                        const uint32_t fb = smem_u32(&full[s]);
+                        mbar_arrive_expect_tx(fb, bytes);
+                        const uint32_t dst = smem_u32(sB + (size_t)s * stage_bytes);
+                        // the occupied 16-row chunks of the Re rows and of the Im rows
+                        for (int c = ts.c_lo; c < ts.c_hi; ++c) {
+                            tma_load_2d(dst + (uint32_t)(16 * c) * 128u, &tmap, fb, kb * kBK, t * 2 * P.Nxp + 16 * c);
+                            tma_load_2d(dst + (uint32_t)(P.Nxp + 16 * c) * 128u, &tmap, fb, kb * kBK,
+                                        t * 2 * P.Nxp + P.Nxp + 16 * c);
+                        }
                         ++prod_it;
                     }
                 }
@@ -198,24 +249,47 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 bool ok = true;
                 const uint32_t a_hi = smem_u32(sA_hi), a_lo = smem_u32(sA_lo), b0 = smem_u32(sB);
                 for (int t = 0; t < P.nz && ok; ++t) {
+                    const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
+                    if (ts.empty) continue;
                     const uint32_t b = acc_it & 1, aph = (acc_it >> 1) & 1;
                     if (!mbar_wait(smem_u32(&tempty[b]), aph ^ 1, abort_flag, P.err, kErrTimeoutMma)) break;
                     tc_fence_after();
-                    const uint32_t d = tmem_base + b * (uint32_t)(2 * P.Nxp);
-                    for (int kb = 0; kb < P.nkb; ++kb) {
+                    // four MMA chains per K step over the occupied x chunks:
+                    // Re G += Pr Sr - Pi Si, Im G += Pr Si + Pi Sr
+                    const uint32_t nr = 16u * (uint32_t)(ts.c_hi - ts.c_lo);
+                    const uint32_t idesc = P.idesc | ((nr >> 3) << 17);
+                    const uint32_t idesc_neg = idesc | (1u << 13);         // negate A
+                    const uint32_t d_re = tmem_base + b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)ts.c_lo;
+                    const uint32_t d_im = d_re + (uint32_t)P.Nxp;
+                    const uint32_t row_re = 16u * (uint32_t)ts.c_lo * 128u;
+                    const uint32_t row_im = row_re + (uint32_t)P.Nxp * 128u;
+                    bool first = true;
+                    for (int kb = 0; kb < P.nkb_b; ++kb) {
+                        const uint32_t kbits = (ts.kmask >> (4 * kb)) & 0xFu;
+                        if (kbits == 0) continue;
                         const uint32_t s = mma_it % P.stages, ph = (mma_it / P.stages) & 1;
                         if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const int ksteps = min(kBK, P.Kp - kb * kBK) >> 4;
                         const uint32_t bs = b0 + s * stage_bytes;
-                        for (int kk = 0; kk < ksteps; ++kk) {
-                            const uint64_t bdesc = sw128_desc(bs + kk * 32);
-                            const uint32_t aoff = kb * kKBlockBytes + kk * 32;
-                            mma_f16(d, sw128_desc(a_hi + aoff), bdesc, P.idesc, (kb | kk) != 0);
-                            if (P.split) mma_f16(d, sw128_desc(a_lo + aoff), bdesc, P.idesc, 1u);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            if (!((kbits >> kk) & 1u)) continue;
+                            const int y0 = 64 * kb + 16 * kk;                  // first y of this K step
+                            const uint32_t off_r = a_k_offset(y0), off_i = a_k_offset(P.Nyp + y0);
+                            const uint64_t bsr = sw128_desc(bs + row_re + kk * 32);
+                            const uint64_t bsi = sw128_desc(bs + row_im + kk * 32);
+                            const uint32_t accum = first ? 0u : 1u;
+                            for (int part = 0; part < (P.split ? 2 : 1); ++part) {
+                                const uint32_t ab = part ? a_lo : a_hi;
+                                const uint64_t pr = sw128_desc(ab + off_r), pi = sw128_desc(ab + off_i);
+                                mma_f16(d_re, pr, bsr, idesc, part ? 1u : accum);
+                                mma_f16(d_re, pi, bsi, idesc_neg, 1u);
+                                mma_f16(d_im, pr, bsi, idesc, part ? 1u : accum);
+                                mma_f16(d_im, pi, bsr, idesc, 1u);
+                            }
+                            first = false;
                         }
                         mma_commit(smem_u32(&empty[s]));
                         ++mma_it;
@@ -234,56 +308,55 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const bool valid = p < P.n_pix;
             const double qx = valid ? P.q[3 * p] : 0.0;
             const double qz = valid ? P.q[3 * p + 2] : 0.0;
-            const int c_begin = half ? nch0 : 0;
-            const int c_end = half ? nch : nch0;
             float2 W[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) W[k] = expmi_f(qx, k * P.voxel);
-            float2 E[4];
+            float2 E[8];                                  // e^{-i q_x x0} of each 16-column chunk
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int x0 = 16 * (c_begin + i);
-                E[i] = expmi_f(qx, (x0 - 0.5 * (P.nx - 1)) * P.voxel);
-            }
+            for (int c = 0; c < 8; ++c) E[c] = expmi_f(qx, (16 * c - 0.5 * (P.nx - 1)) * P.voxel);
             const float2 Zstep = expmi_f(qz, P.voxel);
             float2 Z = expmi_f(qz, (0 - 0.5 * (P.nz - 1)) * P.voxel);
             float2 acc = make_float2(0.f, 0.f);
             const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
             for (int t = 0; t < P.nz; ++t) {
-                const uint32_t b = epi_it & 1, ph = (epi_it >> 1) & 1;
-                if (!mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue)) break;
-                tc_fence_after();
-                float2 acct = make_float2(0.f, 0.f);
+                const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
+                if (!ts.empty) {
+                    const uint32_t b = epi_it & 1, ph = (epi_it >> 1) & 1;
+                    if (!mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue)) break;
+                    tc_fence_after();
+                    float2 acct = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (c_begin + i < c_end) {
-                        const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)(c_begin + i);
-                        float gr[16], gi[16];
-                        tmem_ld16(lane_base + col, gr);
-                        tmem_ld16(lane_base + col + (uint32_t)P.Nxp, gi);
-                        tmem_ld_wait(gr, gi);
-                        float hr = 0.f, hi = 0.f;
+                    for (int c = 0; c < 8; ++c) {
+                        // chunks alternate between the two halves
+                        if (c < nch && c >= ts.c_lo && c < ts.c_hi && (c & 1) == half) {
+                            const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)c;
+                            float gr[16], gi[16];
+                            tmem_ld16(lane_base + col, gr);
+                            tmem_ld16(lane_base + col + (uint32_t)P.Nxp, gi);
+                            tmem_ld_wait(gr, gi);
+                            float hr = 0.f, hi = 0.f;
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            hr = fmaf(W[k].x, gr[k], hr);
-                            hr = fmaf(-W[k].y, gi[k], hr);
-                            hi = fmaf(W[k].x, gi[k], hi);
-                            hi = fmaf(W[k].y, gr[k], hi);
+                            for (int k = 0; k < 16; ++k) {
+                                hr = fmaf(W[k].x, gr[k], hr);
+                                hr = fmaf(-W[k].y, gi[k], hr);
+                                hi = fmaf(W[k].x, gi[k], hi);
+                                hi = fmaf(W[k].y, gr[k], hi);
+                            }
+                            acct.x = fmaf(E[c].x, hr, fmaf(-E[c].y, hi, acct.x));
+                            acct.y = fmaf(E[c].x, hi, fmaf(E[c].y, hr, acct.y));
                         }
-                        acct.x = fmaf(E[i].x, hr, fmaf(-E[i].y, hi, acct.x));
-                        acct.y = fmaf(E[i].x, hi, fmaf(E[i].y, hr, acct.y));
                     }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+                    acc.x = fmaf(Z.x, acct.x, fmaf(-Z.y, acct.y, acc.x));
+                    acc.y = fmaf(Z.x, acct.y, fmaf(Z.y, acct.x, acc.y));
+                    ++epi_it;
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
-                acc.x = fmaf(Z.x, acct.x, fmaf(-Z.y, acct.y, acc.x));
-                acc.y = fmaf(Z.x, acct.y, fmaf(Z.y, acct.x, acc.y));
                 if (((t + 1) & 15) == 0)
                     Z = expmi_f(qz, ((t + 1) - 0.5 * (P.nz - 1)) * P.voxel);
                 else
                     Z = cmul(Z, Zstep);
-                ++epi_it;
             }
             if (half == 1) red[m] = acc;
             named_bar_sync(kEpiWarps * 32);
@@ -325,14 +398,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // ---- host side ------------------------------------------------------------------
 static size_t tc_fixed_bytes() { return 1024 /*align*/ + kBM * sizeof(float2) + 256 /*barriers*/; }
 
-static int tc_nkb(int Kp) { return (Kp + kBK - 1) / kBK; }
+static int tc_nkb(int K) { return (K + kBK - 1) / kBK; }
 
-int tc_max_stages(int Kp, int Nxp, bool split) {
-    size_t a = (size_t)(split ? 2 : 1) * tc_nkb(Kp) * kKBlockBytes;
+int tc_max_stages(int Nyp, int Nxp, bool split) {
+    size_t a = (size_t)(split ? 2 : 1) * tc_nkb(2 * Nyp) * kKBlockBytes;
     size_t stage = (size_t)Nxp * 2 * 128;
     if (a + tc_fixed_bytes() + 2 * stage > (size_t)kMaxSmem) return 0;
     size_t s = ((size_t)kMaxSmem - a - tc_fixed_bytes()) / stage;
     return (int)(s > (size_t)kMaxStages ? kMaxStages : s);
+}
+
+double tc_issued_flops(const int *bounds, int nz, int Nxp, int Nyp, long long n_pix, bool split) {
+    const long long m_tiles = (n_pix + kBM - 1) / kBM;
+    double per_tile = 0.0;
+    for (int t = 0; t < nz; ++t) {
+        const TileSpan ts = tile_span(bounds, nz, t, Nxp, Nyp);
+        if (ts.empty) continue;
+        const int nsteps = __builtin_popcount(ts.kmask);
+        // four real MMAs of 128 x (16 * chunks) x 16 per K step
+        per_tile += 4.0 * 2.0 * kBM * (16.0 * (ts.c_hi - ts.c_lo)) * 16.0 * nsteps;
+    }
+    return per_tile * (double)m_tiles * (split ? 2.0 : 1.0);
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -341,6 +427,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapFloatOOBfill);
 
 bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, bool bf16, std::string *why) {
+    (void)Nxp;
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         void *ptr = nullptr;
@@ -355,7 +442,7 @@ bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, b
     }
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)(2 * Nxp)};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, 16u};            // one 16-row x chunk per copy
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims,
                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -369,24 +456,28 @@ bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, b
 
 cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n_pix, int nx, int ny, int nz,
                            int Nxp, int Nyp, int Kp, double voxel, double str_re, double str_im, bool split,
-                           bool bf16, float2 *A, float *I, int *err, int sm_count, cudaStream_t st) {
+                           bool bf16, const int *bounds, float2 *A, float *I, int *err, int sm_count,
+                           cudaStream_t st) {
     TcParams P;
     P.q = q;
+    P.bounds = bounds;
     P.n_pix = n_pix;
     P.nx = nx;
     P.ny = ny;
     P.nz = nz;
+    (void)Kp;
     P.Nxp = Nxp;
     P.Nyp = Nyp;
-    P.Kp = Kp;
-    P.nkb = tc_nkb(Kp);
-    P.stages = tc_max_stages(Kp, Nxp, split);
-    if (P.stages < 2 || Nxp % 16 != 0 || Nxp > 128 || Kp % 16 != 0) return cudaErrorInvalidValue;
+    P.nkb_a = tc_nkb(2 * Nyp);
+    P.nkb_b = tc_nkb(Nyp);
+    P.stages = tc_max_stages(Nyp, Nxp, split);
+    if (P.stages < 2 || Nxp % 16 != 0 || Nxp > 128 || Nyp % 16 != 0) return cudaErrorInvalidValue;
     P.split = split ? 1 : 0;
     P.bf16 = bf16 ? 1 : 0;
     P.num_m_tiles = (int)((n_pix + kBM - 1) / kBM);
     const uint32_t N = (uint32_t)(2 * Nxp), M = kBM;
-    P.idesc = (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+    (void)N;
+    P.idesc = (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((M >> 4) << 24);
     uint32_t cols = 32;
     while (cols < (uint32_t)(4 * Nxp)) cols <<= 1;
     P.tmem_cols = cols;
@@ -396,7 +487,7 @@ cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n
     P.A = A;
     P.I = I;
     P.err = err;
-    size_t smem = (size_t)(split ? 2 : 1) * P.nkb * kKBlockBytes + (size_t)P.stages * Nxp * 2 * 128 + tc_fixed_bytes();
+    size_t smem = (size_t)(split ? 2 : 1) * P.nkb_a * kKBlockBytes + (size_t)P.stages * Nxp * 2 * 128 + tc_fixed_bytes();
     // The attribute is per function and shared by every thread of the process:
     // always raise it to the largest size any launch uses, never to this
     // launch's size, so concurrent launches from other threads stay valid.

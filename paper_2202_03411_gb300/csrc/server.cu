@@ -304,13 +304,14 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     const long long cx = f64 ? 16 : 8;
     long long s_bytes;
     if (tc) {
-        const long long Nxp = (c->nx + 15) / 16 * 16, Nyp = (c->ny + 7) / 8 * 8;
-        s_bytes = (long long)c->nz * 2 * Nxp * 2 * Nyp * 2;
+        const long long Nxp = (c->nx + 15) / 16 * 16, Nyp = (c->ny + 15) / 16 * 16;
+        s_bytes = (long long)c->nz * 2 * Nxp * Nyp * 2;
     } else {
         s_bytes = nvox * cx;
     }
     long long b = 0;
     b += round_2mib(npix * 24);                 // q
+    if (tc) b += round_2mib(16LL * c->nz);      // slice bounds
     b += round_2mib(nvox * 4);                  // occupancy
     b += round_2mib(s_bytes);                   // slices
     b += round_2mib(npix * cx);                 // field cache

@@ -106,6 +106,23 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
 
     const int ny_here = min(kLinesPerCta, gp.ny - y0);
     const long long nxy = (long long)gp.nx * gp.ny;
+    if (out.bounds) {
+        // occupied box of each slice (order-independent min/max)
+        for (int iz = threadIdx.x; iz < nz; iz += kVoxThreads) {
+            int lo = kLinesPerCta, hi = -1;
+            for (int yl = 0; yl < ny_here; ++yl)
+                if (chi_tile[iz * kLinesPerCta + yl] != 0.f) {
+                    lo = min(lo, yl);
+                    hi = yl;
+                }
+            if (hi >= 0) {
+                atomicMin(&out.bounds[iz], ix);
+                atomicMax(&out.bounds[nz + iz], ix + 1);
+                atomicMin(&out.bounds[2 * nz + iz], y0 + lo);
+                atomicMax(&out.bounds[3 * nz + iz], y0 + hi + 1);
+            }
+        }
+    }
     for (int it = threadIdx.x; it < nz * kLinesPerCta; it += kVoxThreads) {
         const int iz = it / kLinesPerCta, yl = it % kLinesPerCta;
         if (yl >= ny_here) continue;
@@ -118,31 +135,36 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
         } else if (out.layout == kLayoutC32) {
             reinterpret_cast<float2 *>(out.s)[vidx] = make_float2((float)v.x, (float)v.y);
         } else {
-            // tensor-core operand rows: (j, x, re) at j*2Nxp + x, (j, x, im) at j*2Nxp + Nxp + x;
-            // K index y holds the cos part, Nyp + y the sin part (see msft_tc.cu).
+            // tensor-core slice operand: row j*2Nxp + x holds Re s(j, x, y) over y,
+            // row j*2Nxp + Nxp + x holds Im s(j, x, y) (see msft_tc.cu)
             const size_t row_r = (size_t)iz * 2 * out.Nxp + ix;
             const size_t row_i = row_r + out.Nxp;
             const float sr = (float)v.x, si = (float)v.y;
             if (out.layout == kLayoutTcF16) {
                 __half *B = reinterpret_cast<__half *>(out.s);
                 B[row_r * out.Kp + iy] = __float2half_rn(sr);
-                B[row_r * out.Kp + out.Nyp + iy] = __float2half_rn(-si);
                 B[row_i * out.Kp + iy] = __float2half_rn(si);
-                B[row_i * out.Kp + out.Nyp + iy] = __float2half_rn(sr);
             } else {
                 __nv_bfloat16 *B = reinterpret_cast<__nv_bfloat16 *>(out.s);
                 B[row_r * out.Kp + iy] = __float2bfloat16_rn(sr);
-                B[row_r * out.Kp + out.Nyp + iy] = __float2bfloat16_rn(-si);
                 B[row_i * out.Kp + iy] = __float2bfloat16_rn(si);
-                B[row_i * out.Kp + out.Nyp + iy] = __float2bfloat16_rn(sr);
             }
         }
+    }
+}
+
+__global__ void bounds_init_kernel(int *b, int nz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 4 * nz) {
+        const int part = i / nz;
+        b[i] = (part == 0 || part == 2) ? 0x7fffffff : 0;     // lo parts start high, hi parts low
     }
 }
 
 cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const SliceOut &out, bool scan_fp64,
                             bool fp64_mode, cudaStream_t st) {
     if (gp.nz > 32 * kMaxRun) return cudaErrorInvalidValue;
+    if (out.bounds) bounds_init_kernel<<<(4 * gp.nz + 255) / 256, 256, 0, st>>>(out.bounds, gp.nz);
     dim3 grid(gp.nx, (gp.ny + kLinesPerCta - 1) / kLinesPerCta);
     size_t cx = fp64_mode ? sizeof(double2) : sizeof(float2);
     size_t smem = (cx + sizeof(float)) * (size_t)gp.nz * kLinesPerCta;

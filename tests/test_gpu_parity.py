@@ -236,3 +236,24 @@ def test_errors_on_device():
     h.close()
     with pytest.raises(sm.ScatmanError):
         sm.scatman_create(Geometry(200, 16, 16, 1.0, 6.0, 30.0, 8, 8), "tc_f16_split")
+
+
+@pytest.mark.parametrize("prec", ["tc_f16_split", "tc_bf16_split", "tc_f16"])
+def test_forward_tensor_core_occupied_box_skipping(prec):
+    """Shapes whose slices are partly or wholly empty and whose boxes start and
+    end off the 16-column / 16-row grid: the skipped work must not change A."""
+    import paper_2202_03411_gb300 as sm
+    g = Geometry(70, 52, 40, 1.0, 7.0, 50.0, 61, 47)
+    shapes = [
+        Shape(SPHERE, r=6.2, cx=21.3, cy=-15.6, cz=11.0, delta=0.02, beta=0.004),        # corner
+        Shape(ELLIPSOID, a=20.0, b=14.0, c=1.6, delta=0.02, beta=0.004, latitude=-90,    # thin disk: few slices
+              longitude=0, rotation=30, cx=-3.3),
+        Shape(ELLIPSOID, a=3.0, b=22.0, c=9.0, delta=0.02, beta=0.004, latitude=10, longitude=70, rotation=5),
+    ]
+    for s in shapes:
+        I, A, h = run_gpu(g, s, prec, want_A=True)
+        issued, dense = sm.scatman_contraction_flops(h)
+        h.close()
+        Ir, Ar = oracle_field(g, s)
+        assert rel_l2(I, Ir) < TOL[prec], (s.kind, rel_l2(I, Ir))
+        assert 0 < issued < dense
