@@ -154,6 +154,66 @@ def fit_step_run(n_shapes, precision, warm=2):
                          "residual": float(a[:, 2].mean()), "backward": float(a[:, 3].mean())}}
 
 
+def time_mode(g, shapes, precision, reps=1):
+    """Mean ms per pattern (voxelise + forward) and the intensity of shapes[0]."""
+    import torch
+    import paper_2202_03411_gb300 as sm
+    h = sm.scatman_create(g, precision)
+    f64 = precision == "fp64"
+    I = torch.empty(g.n_pix, dtype=torch.float64 if f64 else torch.float32, device="cuda")
+    sm.scatman_voxelise(h, shapes[0])
+    sm.scatman_forward(h, I)
+    sm.scatman_sync(h)
+    I0 = I.double().cpu().numpy()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        for s_ in shapes:
+            sm.scatman_voxelise(h, s_)
+            sm.scatman_forward(h, I)
+    e1.record(stream)
+    sm.scatman_sync(h)
+    h.close()
+    ms = e0.elapsed_time(e1) / (reps * len(shapes))
+    return ms, I0
+
+
+def plain_configs():
+    """The FP64 sphere (32^3, 64^2 to 30 deg) and the FP32-vs-FP64 ellipsoids
+    (96^3, 256^2 to 45 deg); errors against the oracle are added by the CPU leg."""
+    from workloads import ellipsoid_96, sphere_32
+    g1, s1 = sphere_32()
+    ms1, I1 = time_mode(g1, s1, "fp64", reps=20)
+    g2, s2 = ellipsoid_96(n_shapes=64)
+    ms32, I2_32 = time_mode(g2, s2[:16], "fp32")
+    ms64, I2_64 = time_mode(g2, s2[:4], "fp64")
+    out = {"sphere_32_fp64": {"patterns_per_s": 1e3 / ms1, "ms_per_pattern": ms1},
+           "ellipsoid_96": {"fp32": {"patterns_per_s": 1e3 / ms32, "ms_per_pattern": ms32, "shapes_timed": 16},
+                            "fp64": {"patterns_per_s": 1e3 / ms64, "ms_per_pattern": ms64, "shapes_timed": 4}}}
+    return out, (g1, s1[0], I1), (g2, s2[0], I2_32, I2_64)
+
+
+def plain_config_errors(c1, c2, n_sample=1024):
+    """CPU leg: the oracle's answers for the two plain configurations (the
+    sphere on the full detector, the ellipsoid on a pixel sample)."""
+    import numpy as np
+
+    import oracle
+    g1, s1, I1 = c1
+    Iref1, _ = oracle.forward(s1, g1)
+    g2, s2, I32, I64 = c2
+    sample = np.sort(np.random.default_rng(0).choice(g2.n_pix, size=n_sample, replace=False))
+    chi, _ = oracle.voxelise(s2, g2)
+    rho = oracle.slices(chi, g2, s2.delta, s2.beta)
+    Iref2 = np.abs(oracle.msft(rho, oracle.detector_q(g2)[sample], g2.voxel)) ** 2
+    return {"sphere_32_fp64_rel_l2": oracle.relative_l2(I1, Iref1),
+            "ellipsoid_96_fp32_rel_l2": oracle.relative_l2(I32[sample], Iref2),
+            "ellipsoid_96_fp64_rel_l2": oracle.relative_l2(I64[sample], Iref2),
+            "ellipsoid_sample_pixels": n_sample}
+
+
 def fp32_comparator(g, shapes, n=3):
     """The plain FP32 CUDA-core MSFT on the same patterns: patterns/s and its
     rel. L2 difference from the tensor-core result of pattern 0."""
@@ -478,8 +538,10 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, err = cpu_baseline(shapes, g, I0, args.cpu_sample_pixels)
         _, err_fp32 = cpu_baseline(shapes, g, I0_fp32, 512)
+        plain["errors_vs_fp64_oracle"] = plain_config_errors(c1, c2)
     fp32["rel_l2_I_vs_fp64_oracle"] = err_fp32
     fit = fit_step_run(32, args.precision) if world == 1 else None
+    plain, c1, c2 = plain_configs() if world == 1 else (None, None, None)
     serving = None
     if args.short_serving > 0 and world == 1:
         serving = serving_run(args.short_serving, args.serving_slots, args.precision, fractions=(0.8,))
@@ -503,6 +565,7 @@ def main():
         "roofline": roofline,
         "fp32_cuda_core_comparator": fp32,
         "fit_step_96": fit,
+        "plain_configs": plain,
         "serving_short": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
