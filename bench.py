@@ -214,6 +214,22 @@ def plain_config_errors(c1, c2, n_sample=1024):
             "ellipsoid_sample_pixels": n_sample}
 
 
+def fig8b_run(radii=(3.0, 5.0, 10.0, 20.0), dets=(256, 512, 1024, 2048), precision="fp32", reps=5):
+    """Sec. 6 timing study (Fig. 8b): the Listing-2 harmonics shape scaled to a mean
+    radius of 3/5/10/20 wavelengths on the paper's uniform-q virtual detector of
+    256^2 ... 2048^2 pixels at 30 deg (voxel = lambda / (2 sin 30 deg) = lambda)."""
+    from workloads import fig8b_case
+    table = []
+    for R in radii:
+        for det in dets:
+            g, shape = fig8b_case(R, det)
+            ms, _ = time_mode(g, [shape], precision, reps=reps)
+            table.append({"radius_lambda": R, "grid": g.nx, "detector": det, "ms_per_pattern": ms,
+                          "patterns_per_s": 1e3 / ms})
+    return {"precision": precision, "detector": "uniform-q (the paper's virtual detector), separable sums",
+            "cases": table}
+
+
 def fp32_comparator(g, shapes, n=3):
     """The plain FP32 CUDA-core MSFT on the same patterns: patterns/s and its
     rel. L2 difference from the tensor-core result of pattern 0."""
@@ -532,16 +548,18 @@ def main():
 
     I0 = I_all[0].double().cpu().numpy()
     fp32, I0_fp32 = fp32_comparator(g, shapes)
+    fit = fit_step_run(32, args.precision) if world == 1 else None
+    plain, c1, c2 = plain_configs() if world == 1 else (None, None, None)
+    fig8b = fig8b_run() if world == 1 else None
     cpu = None
     err = None
     err_fp32 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, err = cpu_baseline(shapes, g, I0, args.cpu_sample_pixels)
         _, err_fp32 = cpu_baseline(shapes, g, I0_fp32, 512)
-        plain["errors_vs_fp64_oracle"] = plain_config_errors(c1, c2)
+        if plain is not None:
+            plain["errors_vs_fp64_oracle"] = plain_config_errors(c1, c2)
     fp32["rel_l2_I_vs_fp64_oracle"] = err_fp32
-    fit = fit_step_run(32, args.precision) if world == 1 else None
-    plain, c1, c2 = plain_configs() if world == 1 else (None, None, None)
     serving = None
     if args.short_serving > 0 and world == 1:
         serving = serving_run(args.short_serving, args.serving_slots, args.precision, fractions=(0.8,))
@@ -566,6 +584,7 @@ def main():
         "fp32_cuda_core_comparator": fp32,
         "fit_step_96": fit,
         "plain_configs": plain,
+        "fig8b_uniform_q": fig8b,
         "serving_short": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,

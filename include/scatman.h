@@ -64,6 +64,14 @@ typedef enum {
 
 enum { SCATMAN_SPHERE = 0, SCATMAN_ELLIPSOID = 1, SCATMAN_SPHHARM = 2 };
 
+/* Detector geometry. */
+enum {
+    SCATMAN_DETECTOR_FLAT = 0,      /* flat detector normal to z; theta_max at the edge midpoints */
+    SCATMAN_DETECTOR_UNIFORM_Q = 1  /* the paper's virtual detector: pixels uniform in (q_x, q_y) up to
+                                       k0 sin(theta_max); q_z on the Ewald sphere (Eq. 3); pixels with
+                                       q_x^2 + q_y^2 > k0^2 carry zero */
+};
+
 /* Maximum harmonic degree accepted for SCATMAN_SPHHARM. */
 #define SCATMAN_MAX_LMAX 12
 
@@ -85,6 +93,10 @@ enum { SCATMAN_SPHERE = 0, SCATMAN_ELLIPSOID = 1, SCATMAN_SPHHARM = 2 };
  *  scan_fp64       1 forces the transmission scan into FP64 (always on in
  *                  SCATMAN_FP64; switched on automatically when
  *                  k0 * voxel * nz * max(delta, beta) > 5)
+ *  detector        SCATMAN_DETECTOR_FLAT (0) or SCATMAN_DETECTOR_UNIFORM_Q; the
+ *                  uniform-q detector runs the separable transverse sum (q_x
+ *                  depends on the pixel column only, q_y on the row only) in
+ *                  SCATMAN_FP32 or SCATMAN_FP64, nz <= 128
  */
 typedef struct {
     int nx, ny, nz;
@@ -98,6 +110,7 @@ typedef struct {
     int soft;
     double soft_width;
     int scan_fp64;
+    int detector;
 } scatman_config;
 
 /*

@@ -66,6 +66,8 @@ def _load():
         lib.orc_slices.argtypes = [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]
         lib.orc_detector_q.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]
+        lib.orc_detector_q_uniform.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D,
+                                               ctypes.POINTER(ctypes.c_int)]
         lib.orc_msft.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                  _D, ctypes.c_long, _D, _D]
         lib.orc_intensity.argtypes = [_D, _D, ctypes.c_long, _D]
@@ -135,10 +137,27 @@ def slices(chi: np.ndarray, g: Geometry, delta: float, beta: float) -> np.ndarra
 
 
 def detector_q(g: Geometry) -> np.ndarray:
-    """q = k_out - k_in of every flat-detector pixel (Eq. 3), [pixel][3]."""
+    """q = k_out - k_in of every detector pixel (Eq. 3), [pixel][3]: the flat
+    detector, or the uniform-q virtual detector when g.detector says so."""
     q = np.zeros((g.n_pix, 3))
+    if getattr(g, "detector", 0) == 1:
+        valid = np.zeros(g.n_pix, dtype=np.int32)
+        _load().orc_detector_q_uniform(g.det_nx, g.det_ny, g.theta_max_deg, g.wavelength, _p(q),
+                                       valid.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return q
     _load().orc_detector_q(g.det_nx, g.det_ny, g.theta_max_deg, g.wavelength, _p(q))
     return q
+
+
+def detector_valid(g: Geometry) -> np.ndarray:
+    """Pixels with a scattering direction (all of them on the flat detector)."""
+    if getattr(g, "detector", 0) != 1:
+        return np.ones(g.n_pix, dtype=bool)
+    q = np.zeros((g.n_pix, 3))
+    valid = np.zeros(g.n_pix, dtype=np.int32)
+    _load().orc_detector_q_uniform(g.det_nx, g.det_ny, g.theta_max_deg, g.wavelength, _p(q),
+                                   valid.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return valid.astype(bool)
 
 
 def msft(rho: np.ndarray, q: np.ndarray, voxel: float = 1.0) -> np.ndarray:
@@ -173,6 +192,8 @@ def forward(shape: Shape, g: Geometry, q: Optional[np.ndarray] = None, soft: boo
     chi, _ = voxelise(shape, g, soft, width)
     rho = slices(chi, g, shape.delta, shape.beta)
     A = msft(rho, q, g.voxel)
+    if getattr(g, "detector", 0) == 1 and len(A) == g.n_pix:
+        A = np.where(detector_valid(g), A, 0.0)       # no scattering direction: no field
     return np.abs(A) ** 2, A
 
 

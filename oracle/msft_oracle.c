@@ -317,6 +317,39 @@ void orc_detector_q(int det_nx, int det_ny, double theta_max_deg, double wavelen
 }
 
 /*
+ * The paper's own virtual detector (Block 1; Block 6's per-slice DFT on a
+ * uniform grid): pixel centres uniform in the transverse momentum,
+ * q_x(u) = q_max (2u+1-Nx)/Nx, q_y(v) likewise, q_max = k0 sin(theta_max),
+ * and q_z on the Ewald sphere from Eq. 3, q_z = k0 (cos(theta) - 1) with
+ * cos(theta) = sqrt(1 - (q_x^2 + q_y^2)/k0^2).  Pixels with
+ * q_x^2 + q_y^2 > k0^2 have no scattering direction: valid[p] = 0 there
+ * (and q_z is set to -k0).
+ */
+void orc_detector_q_uniform(int det_nx, int det_ny, double theta_max_deg, double wavelength, double *q,
+                            int *valid)
+{
+    double k0 = 2.0 * ORC_PI / wavelength;
+    double qmax = k0 * sin(theta_max_deg * ORC_PI / 180.0);
+    for (int v = 0; v < det_ny; ++v)
+        for (int u = 0; u < det_nx; ++u) {
+            size_t p = (size_t)v * det_nx + u;
+            double qx = qmax * (2.0 * u + 1.0 - det_nx) / det_nx;
+            double qy = qmax * (2.0 * v + 1.0 - det_ny) / det_ny;
+            double s2 = (qx * qx + qy * qy) / (k0 * k0);
+            q[3 * p + 0] = qx;
+            q[3 * p + 1] = qy;
+            if (s2 <= 1.0) {
+                double cth = sqrt(1.0 - s2);
+                q[3 * p + 2] = k0 * (cth - 1.0);
+                valid[p] = 1;
+            } else {
+                q[3 * p + 2] = -k0;
+                valid[p] = 0;
+            }
+        }
+}
+
+/*
  * Eq. 9 (Blocks 6-8, 10): the scattered field at each q,
  *   A(q) = sum_j e^{-i q_z z_j} F[rho_j](q_x, q_y),
  *   F[rho_j](q_x, q_y) = sum_{x,y} rho_j(x,y) e^{-i (q_x x + q_y y)},

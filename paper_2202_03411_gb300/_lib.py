@@ -45,7 +45,7 @@ class scatman_config(ctypes.Structure):
         ("det_nx", ctypes.c_int), ("det_ny", ctypes.c_int),
         ("q_list", _D), ("n_q", ctypes.c_longlong),
         ("precision", ctypes.c_int), ("soft", ctypes.c_int), ("soft_width", ctypes.c_double),
-        ("scan_fp64", ctypes.c_int),
+        ("scan_fp64", ctypes.c_int), ("detector", ctypes.c_int),
     ]
 
 

@@ -76,6 +76,7 @@ def make_config(geometry, precision, soft: bool = False, soft_width: float = 0.5
     cfg.soft = int(bool(soft))
     cfg.soft_width = float(soft_width)
     cfg.scan_fp64 = int(bool(scan_fp64))
+    cfg.detector = int(getattr(g, "detector", 0))
     return cfg, keep
 
 

@@ -139,6 +139,7 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_part);
     cudaFree(h->d_S);
     cudaFree(h->d_partial);
+    cudaFree(h->d_H);
     cudaFree(h->d_adj_part);
     cudaFree(h->d_gmax);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -178,6 +179,13 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
             return fail(set_error(h, SCATMAN_ERR_ARG, "theta_max_deg must lie in (0, 90)"));
         h->n_pix = (long long)c.det_nx * c.det_ny;
     }
+    if (c.detector != SCATMAN_DETECTOR_FLAT && c.detector != SCATMAN_DETECTOR_UNIFORM_Q)
+        return fail(set_error(h, SCATMAN_ERR_ARG, "unknown detector"));
+    h->uniform_q = c.detector == SCATMAN_DETECTOR_UNIFORM_Q && !cfg->q_list;
+    if (h->uniform_q && (c.precision != SCATMAN_FP32 && c.precision != SCATMAN_FP64))
+        return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector runs in SCATMAN_FP32 or SCATMAN_FP64"));
+    if (h->uniform_q && c.nz > 128)
+        return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector supports nz <= 128"));
     h->precision = c.precision;
     h->tensor_core = is_tc(c.precision);
     h->split = (c.precision == SCATMAN_TC_F16_SPLIT || c.precision == SCATMAN_TC_BF16_SPLIT);
@@ -233,7 +241,9 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if ((rc = alloc_dev(h, &h->d_A, npix * cx, "field buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, &h->d_I, npix * (f64 ? 8 : 4), "intensity buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, (void **)&h->d_err, sizeof(int), "error word"))) return fail(rc);
-    if (!h->tensor_core) {
+    if (h->uniform_q) {
+        if ((rc = alloc_dev(h, &h->d_H, (size_t)c.det_ny * nvox / c.ny * cx, "y-contracted slices"))) return fail(rc);
+    } else if (!h->tensor_core) {
         h->splits = simt_splits(h->n_pix, c.nx, c.nz, h->sm_count);
         if ((rc = alloc_dev(h, &h->d_partial, (size_t)h->splits * npix * cx, "partial fields"))) return fail(rc);
     }
@@ -247,7 +257,10 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
         if (rc) return fail(rc);
         if ((rc = check_cuda(h, cudaStreamSynchronize(h->stream), "q upload"))) return fail(rc);
     } else {
-        rc = check_cuda(h, launch_detector_q(c.det_nx, c.det_ny, c.theta_max_deg, h->k0, h->d_q, h->stream),
+        rc = check_cuda(h, h->uniform_q ? launch_detector_q_uniform(c.det_nx, c.det_ny, c.theta_max_deg, h->k0,
+                                                                    h->d_q, h->stream)
+                                         : launch_detector_q(c.det_nx, c.det_ny, c.theta_max_deg, h->k0, h->d_q,
+                                                             h->stream),
                         "detector q");
         if (rc) return fail(rc);
     }
@@ -336,7 +349,10 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
     const double str_re = -2.0 * d + d * d - b * b;
     const double str_im = 2.0 * b - 2.0 * d * b;
     cudaError_t e;
-    if (h->tensor_core) {
+    if (h->uniform_q) {
+        e = launch_msft_uniform(h->precision == SCATMAN_FP64, h->d_s, c.nx, c.ny, c.nz, c.det_nx, c.det_ny,
+                                c.theta_max_deg, h->k0, c.voxel, str_re, str_im, h->d_H, h->d_A, I_dev, h->stream);
+    } else if (h->tensor_core) {
         e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, h->Kp, c.voxel, str_re,
                            str_im, h->split, h->bf16, h->d_bounds, (float2 *)h->d_A, (float *)I_dev, h->d_err,
                            h->sm_count, h->stream);

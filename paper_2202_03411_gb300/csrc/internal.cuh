@@ -119,6 +119,8 @@ struct scatman_handle {
     size_t part_count = 0;
     void *d_S = nullptr;            // backward adjoint field (complex, nvox)
     void *d_partial = nullptr;      // CUDA-core contraction: per-split partial fields
+    void *d_H = nullptr;            // uniform-q detector: y-contracted slices [v][z][x]
+    bool uniform_q = false;
     float2 *d_adj_part = nullptr;   // tensor-core adjoint: per-pixel-range partial fields
     size_t adj_part_count = 0;
     unsigned *d_gmax = nullptr;     // tensor-core adjoint: max |w A| (float bits)
@@ -147,6 +149,12 @@ cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const S
 // Detector q (voxelise.cu).
 cudaError_t launch_detector_q(int det_nx, int det_ny, double theta_max_deg, double k0, double *q,
                               cudaStream_t st);
+// Uniform-q virtual detector (msft_uniform.cu).
+cudaError_t launch_detector_q_uniform(int det_nx, int det_ny, double theta_max_deg, double k0, double *q,
+                                      cudaStream_t st);
+cudaError_t launch_msft_uniform(bool fp64, const void *s, int nx, int ny, int nz, int det_nx, int det_ny,
+                                double theta_max_deg, double k0, double voxel, double str_re, double str_im,
+                                void *H, void *A, void *I, cudaStream_t st);
 // CUDA-core contraction (msft_simt.cu).
 int simt_splits(long long n_pix, int nx, int nz, int sm_count);
 cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long long n_pix, int nx, int ny,

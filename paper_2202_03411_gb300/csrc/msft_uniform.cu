@@ -1,0 +1,228 @@
+// msft_uniform.cu -- Eq. 9 on the paper's uniform-q virtual detector (Block 1,
+// Block 6's per-slice DFT), where q_x depends on the pixel column u only and
+// q_y on the row v only, so the transverse sum separates:
+//   U1:  H[v][j][x] = sum_y s_j(x, y) e^{-i q_y(v) y}
+//   U2:  A(u, v)    = (n^2-1) sum_j e^{-i q_z(u,v) z_j} sum_x e^{-i q_x(u) x} H[v][j][x]
+// Both stages are shared-memory tiled complex GEMMs on the CUDA cores (FP32
+// or FP64); U2 applies the per-pixel slice phase e^{-i q_z z_j} and reduces
+// over j in a fixed order.  Pixels with q_x^2 + q_y^2 > k0^2 have no
+// scattering direction and get A = 0.
+#include "internal.cuh"
+
+namespace scm {
+
+template <typename R> struct UC;
+template <> struct UC<float> { using T = float2; };
+template <> struct UC<double> { using T = double2; };
+template <typename R> __device__ __forceinline__ typename UC<R>::T uexp(double q, double c);
+template <> __device__ __forceinline__ float2 uexp<float>(double q, double c) { return expmi_f(q, c); }
+template <> __device__ __forceinline__ double2 uexp<double>(double q, double c) { return expmi_d(q, c); }
+
+// Transverse momentum of pixel index i of n on the uniform grid.
+__device__ __forceinline__ double uq_of(int i, int n, double qmax) {
+    return qmax * (double)(2 * i + 1 - n) / (double)n;
+}
+
+// a1 for the uniform-q detector: q for every pixel (q_z = -k0 where the pixel
+// has no scattering direction).
+__global__ void detector_q_uniform_kernel(int det_nx, int det_ny, double qmax, double k0, double *q) {
+    long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (long long)det_nx * det_ny) return;
+    const int u = (int)(p % det_nx), v = (int)(p / det_nx);
+    const double qx = uq_of(u, det_nx, qmax), qy = uq_of(v, det_ny, qmax);
+    const double s2 = __ddiv_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(k0, k0));
+    q[3 * p] = qx;
+    q[3 * p + 1] = qy;
+    q[3 * p + 2] = s2 <= 1.0 ? k0 * (sqrt(1.0 - s2) - 1.0) : -k0;
+}
+
+cudaError_t launch_detector_q_uniform(int det_nx, int det_ny, double theta_max_deg, double k0, double *q,
+                                      cudaStream_t st) {
+    const double qmax = k0 * sin(theta_max_deg * kPi / 180.0);
+    const long long n = (long long)det_nx * det_ny;
+    detector_q_uniform_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(det_nx, det_ny, qmax, k0, q);
+    return cudaGetLastError();
+}
+
+constexpr int kUT = 64;        // tile edge
+constexpr int kUK = 16;        // K chunk
+
+// U1: H[v][c] = sum_y s[c][y] P(v, y), c = (j, x).  Block tile 64 v x 64 c,
+// thread 4 v x 4 c (c strided by 16 so shared reads are conflict-free).
+template <typename R>
+__global__ void __launch_bounds__(256) uq_y_kernel(const typename UC<R>::T *__restrict__ s, int ny, int ncol,
+                                                   int ndv, double qmax, double voxel,
+                                                   typename UC<R>::T *__restrict__ H) {
+    using C = typename UC<R>::T;
+    __shared__ C Ps[kUK][kUT];
+    __shared__ C Ss[kUK][kUT];
+    const int v0 = blockIdx.y * kUT, c0 = blockIdx.x * kUT;
+    const int tv = threadIdx.x / 16, tc = threadIdx.x % 16;
+    C acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b].x = acc[a][b].y = (R)0;
+    for (int y0 = 0; y0 < ny; y0 += kUK) {
+        __syncthreads();
+        for (int it = threadIdx.x; it < kUK * kUT; it += 256) {
+            const int k = it / kUT, i = it % kUT;
+            const int y = y0 + k;
+            C pv, sv;
+            pv.x = pv.y = sv.x = sv.y = (R)0;
+            if (y < ny) {
+                if (v0 + i < ndv) pv = uexp<R>(uq_of(v0 + i, ndv, qmax), (y - 0.5 * (ny - 1)) * voxel);
+                if (c0 + i < ncol) sv = s[(size_t)(c0 + i) * ny + y];
+            }
+            Ps[k][i] = pv;
+            Ss[k][i] = sv;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < kUK; ++k) {
+            C p[4], q[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) p[a] = Ps[k][4 * tv + a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) q[b] = Ss[k][tc + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    acc[a][b].x = fma(p[a].x, q[b].x, fma(-p[a].y, q[b].y, acc[a][b].x));
+                    acc[a][b].y = fma(p[a].x, q[b].y, fma(p[a].y, q[b].x, acc[a][b].y));
+                }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int v = v0 + 4 * tv + a;
+        if (v >= ndv) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int c = c0 + tc + 16 * b;
+            if (c < ncol) H[(size_t)v * ncol + c] = acc[a][b];
+        }
+    }
+}
+
+// U2: for one detector row v and 64 columns u: F[u][j] = sum_x E(u, x) H[v][j][x],
+// then A(u, v) = str * sum_j e^{-i q_z(u,v) z_j} F[u][j].  Thread: 4 u x JP j.
+template <typename R, int JP, int KC>
+__global__ void __launch_bounds__(256) uq_xz_kernel(const typename UC<R>::T *__restrict__ H, int nx, int nz,
+                                                    int ndu, int ndv, double qmax, double k0, double voxel,
+                                                    R str_re, R str_im, typename UC<R>::T *__restrict__ A,
+                                                    R *__restrict__ I) {
+    using C = typename UC<R>::T;
+    __shared__ C Es[KC][kUT];
+    __shared__ C Hs[KC][16 * JP];
+    __shared__ C red[16][kUT + 1];
+    const int v = blockIdx.y, u0 = blockIdx.x * kUT;
+    const int tu = threadIdx.x % 16, tj = threadIdx.x / 16;     // u = u0 + tu + 16 a ; j = tj + 16 b
+    C acc[4][JP];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < JP; ++b) acc[a][b].x = acc[a][b].y = (R)0;
+    const C *Hv = H + (size_t)v * nz * nx;
+    for (int x0 = 0; x0 < nx; x0 += KC) {
+        __syncthreads();
+        for (int it = threadIdx.x; it < KC * kUT; it += 256) {
+            const int k = it / kUT, i = it % kUT;
+            C e;
+            e.x = e.y = (R)0;
+            if (x0 + k < nx && u0 + i < ndu) e = uexp<R>(uq_of(u0 + i, ndu, qmax), (x0 + k - 0.5 * (nx - 1)) * voxel);
+            Es[k][i] = e;
+        }
+        for (int it = threadIdx.x; it < KC * 16 * JP; it += 256) {
+            const int j = it / KC, k = it % KC;
+            C h;
+            h.x = h.y = (R)0;
+            if (x0 + k < nx && j < nz) h = Hv[(size_t)j * nx + x0 + k];
+            Hs[k][j] = h;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < KC; ++k) {
+            C e[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) e[a] = Es[k][tu + 16 * a];
+#pragma unroll
+            for (int b = 0; b < JP; ++b) {
+                const C h = Hs[k][tj + 16 * b];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    acc[a][b].x = fma(e[a].x, h.x, fma(-e[a].y, h.y, acc[a][b].x));
+                    acc[a][b].y = fma(e[a].x, h.y, fma(e[a].y, h.x, acc[a][b].y));
+                }
+            }
+        }
+    }
+    // slice phases and the sum over this thread's j
+    const double qy = uq_of(v, ndv, qmax);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int u = u0 + tu + 16 * a;
+        const double qx = uq_of(u < ndu ? u : 0, ndu, qmax);
+        const double s2 = __ddiv_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(k0, k0));
+        const double qz = s2 <= 1.0 ? k0 * (sqrt(1.0 - s2) - 1.0) : -k0;
+        C part;
+        part.x = part.y = (R)0;
+#pragma unroll
+        for (int b = 0; b < JP; ++b) {
+            const int j = tj + 16 * b;
+            if (j < nz) {
+                const C z = uexp<R>(qz, (j - 0.5 * (nz - 1)) * voxel);
+                part.x = fma(z.x, acc[a][b].x, fma(-z.y, acc[a][b].y, part.x));
+                part.y = fma(z.x, acc[a][b].y, fma(z.y, acc[a][b].x, part.y));
+            }
+        }
+        red[tj][tu + 16 * a] = part;
+    }
+    __syncthreads();
+    if (threadIdx.x < kUT) {
+        const int i = threadIdx.x, u = u0 + i;
+        if (u < ndu) {
+            C sum;
+            sum.x = sum.y = (R)0;
+            for (int t = 0; t < 16; ++t) {
+                sum.x += red[t][i].x;
+                sum.y += red[t][i].y;
+            }
+            const double qx = uq_of(u, ndu, qmax);
+            const double s2 = __ddiv_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(k0, k0));
+            C out;
+            if (s2 <= 1.0) {
+                out.x = str_re * sum.x - str_im * sum.y;
+                out.y = str_re * sum.y + str_im * sum.x;
+            } else {
+                out.x = out.y = (R)0;
+            }
+            const size_t p = (size_t)v * ndu + u;
+            A[p] = out;
+            I[p] = out.x * out.x + out.y * out.y;
+        }
+    }
+}
+
+cudaError_t launch_msft_uniform(bool fp64, const void *s, int nx, int ny, int nz, int det_nx, int det_ny,
+                                double theta_max_deg, double k0, double voxel, double str_re, double str_im,
+                                void *H, void *A, void *I, cudaStream_t st) {
+    const double qmax = k0 * sin(theta_max_deg * kPi / 180.0);
+    const int ncol = nx * nz;
+    dim3 g1((ncol + kUT - 1) / kUT, (det_ny + kUT - 1) / kUT);
+    dim3 g2((det_nx + kUT - 1) / kUT, det_ny);
+    if (nz > 128) return cudaErrorInvalidValue;
+    if (fp64) {
+        uq_y_kernel<double><<<g1, 256, 0, st>>>((const double2 *)s, ny, ncol, det_ny, qmax, voxel, (double2 *)H);
+        uq_xz_kernel<double, 8, 8><<<g2, 256, 0, st>>>((const double2 *)H, nx, nz, det_nx, det_ny, qmax, k0, voxel,
+                                                        str_re, str_im, (double2 *)A, (double *)I);
+    } else {
+        uq_y_kernel<float><<<g1, 256, 0, st>>>((const float2 *)s, ny, ncol, det_ny, qmax, voxel, (float2 *)H);
+        uq_xz_kernel<float, 8, 16><<<g2, 256, 0, st>>>((const float2 *)H, nx, nz, det_nx, det_ny, qmax, k0, voxel,
+                                                        (float)str_re, (float)str_im, (float2 *)A, (float *)I);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace scm

@@ -363,3 +363,26 @@ def test_gradient_central_differences(kind):
         Lm = _loss_and_grad(_bump(s, name, k, -h), g, target, width)[0]
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - grad[i]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(grad).max()), (name, k, fd, grad[i])
+
+
+# --- The paper's uniform-q virtual detector (Block 1, Block 6) -------------------------
+
+def test_uniform_q_detector():
+    from workloads import DETECTOR_UNIFORM_Q
+    g = Geometry(8, 8, 8, 1.0, 4.0, 60.0, 21, 17, DETECTOR_UNIFORM_Q)
+    q = oracle.detector_q(g).reshape(17, 21, 3)
+    valid = oracle.detector_valid(g).reshape(17, 21)
+    k0 = 2 * math.pi / g.wavelength
+    qmax = k0 * math.sin(math.radians(60.0))
+    # separable: q_x depends on the column only, q_y on the row only, uniform spacing
+    assert np.all(q[:, :, 0] == q[:1, :, 0]) and np.all(q[:, :, 1] == q[:, :1, 1])
+    np.testing.assert_allclose(np.diff(q[0, :, 0]), 2 * qmax / 21, rtol=1e-12)
+    np.testing.assert_allclose(q[0, -1, 0] + qmax / 21, qmax, rtol=1e-14)       # outer pixel edge at theta_max
+    # Ewald sphere on the valid pixels; corners beyond k0 are invalid at 60 deg
+    kout = q + np.array([0, 0, k0])
+    np.testing.assert_allclose(np.linalg.norm(kout[valid], axis=-1), k0, rtol=1e-13)
+    assert not valid.all() and valid[8, 10]
+    np.testing.assert_array_equal(valid, q[:, :, 0] ** 2 + q[:, :, 1] ** 2 <= k0 ** 2)
+    s = Shape(SPHERE, r=2.5, delta=0.02, beta=0.004)
+    I, _ = oracle.forward(s, g)
+    assert np.all(I.reshape(17, 21)[~valid] == 0) and np.all(I.reshape(17, 21)[valid] > 0)

@@ -35,6 +35,7 @@ from typing import List, Optional
 import numpy as np
 
 SPHERE, ELLIPSOID, SPHHARM = 0, 1, 2
+DETECTOR_FLAT, DETECTOR_UNIFORM_Q = 0, 1
 KIND_NAMES = {SPHERE: "sphere", ELLIPSOID: "ellipsoid", SPHHARM: "sphharm"}
 
 
@@ -89,6 +90,7 @@ class Geometry:
     theta_max_deg: float
     det_nx: int
     det_ny: int
+    detector: int = 0                   # DETECTOR_FLAT or DETECTOR_UNIFORM_Q (the paper's virtual detector)
 
     @property
     def n_pix(self) -> int:
@@ -220,6 +222,34 @@ def serving_mix(n_requests: int = 2000, rate_per_s: float = 100.0, seed: int = 0
         tgt = perturbed(s, rng)
         out.append(Request(rid, t, g, s, tgt))
     return out
+
+
+def listing2_sphharm(mean_radius: float, lmax_keep: int = 9) -> Shape:
+    """The harmonics shape of Listing 2 (triplets [l, m, c] in nm: [0,0,200],
+    [3,2,20], [6,4,4], [9,6,2]; delta 0.01, beta 0.001, latitude 30,
+    longitude -40) rescaled so its mean radius is `mean_radius`."""
+    trip = [(0, 0, 200.0), (3, 2, 20.0), (6, 4, 4.0), (9, 6, 2.0)]
+    c00 = trip[0][2]
+    lmax = min(lmax_keep, max(t[0] for t in trip))
+    alm = np.zeros((lmax + 1) ** 2)
+    for l, m, c in trip[1:]:
+        if l <= lmax:
+            alm[l * l + l + m] = c / c00 * math.sqrt(4 * math.pi)   # a_lm = c_lm / R0, R0 = c_00 Y_00
+    return Shape(SPHHARM, R0=mean_radius, lmax=lmax, alm=alm, delta=0.01, beta=0.001, latitude=30.0,
+                 longitude=-40.0, rotation=0.0)
+
+
+def fig8b_case(radius_wavelengths: float, det: int, theta_max_deg: float = 30.0):
+    """Timing study of Sec. 6 (Fig. 8b): the Listing-2 harmonics shape scaled to a
+    mean radius of 3/5/10/20 wavelengths, uniform-q detector of det^2 pixels.
+    Length unit = wavelength; voxel = lambda / (2 sin theta_max), the spacing
+    whose Nyquist limit is the detector's q_max (Block 3)."""
+    lam = 1.0
+    voxel = lam / (2.0 * math.sin(math.radians(theta_max_deg)))
+    R = radius_wavelengths * lam
+    n = int(math.ceil(2.0 * 1.3 * R / voxel)) + 4
+    g = Geometry(n, n, n, voxel, lam, theta_max_deg, det, det, DETECTOR_UNIFORM_Q)
+    return g, listing2_sphharm(R)
 
 
 def random_slices(rng: np.random.Generator, nz: int, nx: int, ny: int) -> np.ndarray:
