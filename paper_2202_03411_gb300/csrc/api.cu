@@ -209,9 +209,9 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
         h->Kp = h->Nyp;                       // K extent of one slice-operand row
         if (h->Nxp > 128)
             return fail(set_error(h, SCATMAN_ERR_ARG, "tensor-core modes support nx <= 128"));
-        if (tc_max_stages(h->Nyp, h->Nxp, h->split) < 2)
+        if (tc_ring_bytes(h->Nyp, h->Nxp, h->split) == 0)
             return fail(set_error(h, SCATMAN_ERR_ARG, "ny too large for the tensor-core phase tile"));
-        h->b_rows = (size_t)c.nz * 2 * h->Nxp;
+        h->b_rows = (size_t)c.nz * 3 * h->Nxp;   // planes -Im, Re, Im of every slice
     }
 
     if (cuda_stream) {
@@ -266,7 +266,7 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     }
     if (h->tensor_core) {
         std::string why;
-        if (!encode_tmap_B(&h->tmap_B, h->d_s, h->Kp, h->b_rows, h->Nxp, h->bf16, &why))
+        if (!encode_tmap_B(&h->tmap_B, h->d_s, h->Kp, h->Nxp, c.nz, h->bf16, &why))
             return fail(set_error(h, SCATMAN_ERR_CUDA, why));
         h->have_tmap = true;
     }
@@ -353,7 +353,7 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
         e = launch_msft_uniform(h->precision == SCATMAN_FP64, h->d_s, c.nx, c.ny, c.nz, c.det_nx, c.det_ny,
                                 c.theta_max_deg, h->k0, c.voxel, str_re, str_im, h->d_H, h->d_A, I_dev, h->stream);
     } else if (h->tensor_core) {
-        e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, h->Kp, c.voxel, str_re,
+        e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, c.voxel, str_re,
                            str_im, h->split, h->bf16, h->d_bounds, (float2 *)h->d_A, (float *)I_dev, h->d_err,
                            h->sm_count, h->stream);
     } else {
@@ -447,10 +447,10 @@ int scatman_get_slices(scatman_handle *h, double *s_host) {
         for (int iz = 0; iz < c.nz; ++iz)
             for (int ix = 0; ix < c.nx; ++ix)
                 for (int iy = 0; iy < c.ny; ++iy) {
-                    size_t row_r = (size_t)iz * 2 * h->Nxp + ix;
+                    size_t row_r = ((size_t)iz * 3 + 1) * h->Nxp + ix;     // Re plane; Im plane follows
                     size_t v = ((size_t)iz * c.nx + ix) * c.ny + iy;
                     s_host[2 * v] = half_bits_to_float(B[row_r * h->Kp + iy], h->bf16);
-                    s_host[2 * v + 1] = half_bits_to_float(B[(row_r + h->Nxp) * h->Kp + iy], h->bf16);   // Im row
+                    s_host[2 * v + 1] = half_bits_to_float(B[(row_r + h->Nxp) * h->Kp + iy], h->bf16);
                 }
     }
     return SCATMAN_OK;

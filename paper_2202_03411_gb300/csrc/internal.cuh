@@ -80,10 +80,17 @@ struct GridParams {
 // Where the voxeliser writes s = chi*T.
 enum SliceLayout { kLayoutC64 = 0, kLayoutC32 = 1, kLayoutTcF16 = 2, kLayoutTcBF16 = 3 };
 
+// Tensor maps of the tensor-core slice operand, one per span width of 16k
+// rows (k = 1 .. kTcMaxChunks).
+constexpr int kTcMaxChunks = 8;
+struct TcMaps {
+    CUtensorMap m[kTcMaxChunks];
+};
+
 struct SliceOut {
     int layout;
     int Nxp, Nyp, Kp;               // tensor-core operand: padded x and y; Kp = Nyp, the K extent of a row
-    void *s;                        // C64: double2[nvox]; C32: float2[nvox]; TC: 16-bit [nz*2*Nxp][Kp]
+    void *s;                        // C64: double2[nvox]; C32: float2[nvox]; TC: 16-bit [nz*3*Nxp][Kp]
     float *chi;                     // occupancy [z][x][y]
     int *bounds;                    // per slice [x_lo | x_hi | y_lo | y_hi] of chi != 0 (nz each), or null
 };
@@ -126,7 +133,7 @@ struct scatman_handle {
     unsigned *d_gmax = nullptr;     // tensor-core adjoint: max |w A| (float bits)
     int splits = 1;
     long long device_bytes = 0;
-    CUtensorMap tmap_B;
+    scm::TcMaps tmap_B;
     bool have_tmap = false;
     // state
     bool have_shape = false;
@@ -161,14 +168,14 @@ cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long lon
                              int nz, double voxel, double str_re, double str_im, void *A, void *I,
                              void *partial, int splits, cudaStream_t st);
 // Tensor-core contraction (msft_tc.cu).
-int tc_max_stages(int Nyp, int Nxp, bool split);
-cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n_pix, int nx, int ny,
-                           int nz, int Nxp, int Nyp, int Kp, double voxel, double str_re, double str_im,
-                           bool split, bool bf16, const int *bounds, float2 *A, float *I, int *err, int sm_count,
+size_t tc_ring_bytes(int Nyp, int Nxp, bool split);
+cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
+                           int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
+                           bool bf16, const int *bounds, float2 *A, float *I, int *err, int sm_count,
                            cudaStream_t st);
 // Real flops one contraction launch issues for the given per-slice boxes.
 double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
-bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, bool bf16, std::string *why);
+bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why);
 // Backward (adjoint.cu).
 cudaError_t launch_adjoint_field(bool fp64, const void *A, const void *dLdI, const double *q, long long n_pix,
                                  int nx, int ny, int nz, double voxel, void *S, cudaStream_t st);

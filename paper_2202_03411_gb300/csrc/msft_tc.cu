@@ -3,38 +3,47 @@
 // Per slice j the 2D sum over (x, y) is factored as
 //   G[q, (j,x)] = sum_y e^{-i q_y y} s_j(x, y)          (dense complex contraction)
 //   A[q]        = (n^2-1) sum_j e^{-i q_z z_j} sum_x e^{-i q_x x} G[q, (j,x)]
-// The first line is a complex GEMM per slice, done as four real MMA chains
-// with K = y and N = x:
-//   Re G += Pr Sr,  Re G += (-Pi) Si,  Im G += Pr Si,  Im G += Pi Sr,
+// The first line is a complex GEMM per slice with K = y.  Its output columns
+// are [Re G | Im G] over the slice's occupied x span, and each K step takes
+// two real MMAs with N = 2 x span:
+//   [Re G | Im G] += Pr [Sr | Si] + Pi [-Si | Sr],
 //   Pr[m, y] = cos(q_y y), Pi[m, y] = -sin(q_y y)   (e^{-i q_y y}),
-//   Sr[x, y] = Re s_j(x, y), Si[x, y] = Im s_j(x, y),
-// the minus sign coming from the instruction descriptor's negate-A bit.
-// The phase operand [Pr | Pi] is built in shared memory once per pixel tile;
-// with split phases it is held as an FP16/BF16 pair P = P_hi + P_lo and both
-// halves accumulate into the same FP32 result.  The slice operand streams in
-// through TMA with 128-byte swizzle, one 16-row box per occupied 16-column x
-// chunk: only each slice's occupied box (x chunks, K steps of 16 y) is loaded
-// and multiplied, and empty slices are skipped.  Accumulators live in tensor
-// memory, double buffered, and eight epilogue warps apply the x- and z-phases
+//   Sr[x, y] = Re s_j(x, y), Si[x, y] = Im s_j(x, y).
+// The slice operand is stored as three planes [-Si | Sr | Si], so both B
+// operands are windows of one staged block (rows [span, 3 span) and
+// [0, 2 span)).  The phase operand [Pr | Pi] is built in shared memory once
+// per pixel tile; with split phases it is held as an FP16/BF16 pair
+// P = P_hi + P_lo and both halves accumulate into the same FP32 result.  Each
+// stage is one 3D TMA box (64 y x span rows x 3 planes, 128-byte swizzle) of
+// the slice's occupied x chunks, placed in a shared-memory byte ring whose
+// stages are as large as the span; K steps of 16 y outside the occupied y
+// range and empty slices are skipped.  Accumulators live in tensor memory,
+// double buffered, and eight epilogue warps apply the x- and z-phases
 // (second line) while the next slice's MMAs run.
 //
-// Warp roles (320 threads): warps 0-7 epilogue (two per TMEM lane quarter,
-// alternating x chunks), warp 8 TMA producer, warp 9 MMA issuer and
-// tensor-memory owner.  Every wait is bounded: on time-out the kernel sets a
-// bit in the error word, releases its tensor memory and returns.
+// Warp roles (320 threads): warps 0-7 build the phase tile and run the
+// epilogue (two per TMEM lane quarter, alternating x chunks), warp 8 is the
+// TMA producer, warp 9 issues the MMAs and owns the tensor memory.  The roles
+// meet only at mbarriers, so the producer runs ahead across pixel tiles.
+// Every wait is bounded: on time-out the kernel sets a bit in the error word,
+// releases its tensor memory and returns.
 #include "internal.cuh"
 #include "tc_ptx.cuh"
+
+#include <cstring>
 
 namespace scm {
 
 constexpr int kTcThreads = 320;
 constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProducerWarp = 8;
 constexpr int kMmaWarp = 9;
 constexpr int kBM = 128;
 constexpr int kBK = 64;                    // 64 x 16-bit = one 128-byte swizzle row
 constexpr int kKBlockBytes = kBM * 128;    // one 128 x 64 operand block
-constexpr int kMaxStages = 8;
+constexpr int kSlots = 8;                  // stages in flight at most
+constexpr int kPlanes = 3;                 // slice operand planes: -Im, Re, Im
 constexpr int kMaxSmem = 232448;           // 227 KB opt-in per block
 
 struct TcParams {
@@ -44,7 +53,7 @@ struct TcParams {
     int nx, ny, nz;
     int Nxp, Nyp;               // padded x (multiple of 16) and y (multiple of 16)
     int nkb_a, nkb_b;           // 64-element K blocks of the phase operand (2 Nyp) and of a slice (Nyp)
-    int stages;
+    uint32_t ring_bytes;        // slice-stage ring (multiple of 1024)
     int split, bf16;
     int num_m_tiles;
     uint32_t idesc;             // without the N field (set per slice)
@@ -57,7 +66,7 @@ struct TcParams {
 };
 
 // Which part of slice t the contraction touches: x chunks [c_lo, c_hi) of 16
-// columns and a bit mask over K steps of 16 (cos part y, sin part Nyp + y).
+// columns and a bit mask over K steps of 16 y.
 struct TileSpan {
     bool empty;
     int c_lo, c_hi;
@@ -89,6 +98,12 @@ __host__ __device__ inline TileSpan tile_span(const int *bounds, int nz, int t, 
     return ts;
 }
 
+// Placement of a stage of `sz` bytes in the ring: a stage never wraps, it
+// starts over at offset 0 when it does not fit before the end.
+__device__ __forceinline__ uint32_t ring_start(uint32_t head_off, uint32_t sz, uint32_t ring) {
+    return head_off + sz > ring ? 0u : head_off;
+}
+
 __device__ __forceinline__ uint16_t to16(float v, int bf16) {
     if (bf16) {
         __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -117,16 +132,23 @@ __device__ __forceinline__ uint32_t a_chunk_offset(int m, int k) {
     return (uint32_t)(kb * kKBlockBytes + m * 128 + ((c ^ (m & 7)) << 4));
 }
 
-// Phase operand P[m, k] of one pixel tile (and its low part when split).
+// Phase operand P[m, k] of one pixel tile (and its low part when split),
+// built by the kEpiThreads epilogue threads.  Thread `tid` always serves pixel
+// row m = tid % 128; each group of 8 consecutive y starts from one reduced
+// sincos and advances by the rotation e^{-i q_y dy} (FP32 complex products,
+// a few ulp over 8 steps, far below the 16-bit operands' resolution).
 __device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint8_t *sA_hi, uint8_t *sA_lo,
-                                                 int tid, int nthreads) {
+                                                 int tid) {
     const int ny8 = P.Nyp >> 3;
-    for (int it = tid; it < kBM * ny8; it += nthreads) {
-        const int m = it % kBM, y8 = it / kBM;
-        const long long p = (long long)mt * kBM + m;
-        const double qy = p < P.n_pix ? P.q[3 * p + 1] : 0.0;
-        const float qh = (float)qy, ql = (float)(qy - (double)qh);
-        const float yoff = 0.5f * (float)(P.ny - 1), vox = (float)P.voxel;
+    const int m = tid % kBM;
+    const long long p = (long long)mt * kBM + m;
+    const bool valid = p < P.n_pix;
+    const double qy = valid ? P.q[3 * p + 1] : 0.0;
+    const float qh = (float)qy, ql = (float)(qy - (double)qh);
+    const float yoff = 0.5f * (float)(P.ny - 1), vox = (float)P.voxel;
+    const float2 step = expmi_fs(qh, ql, vox);
+    for (int y8 = tid / kBM; y8 < ny8; y8 += kEpiThreads / kBM) {
+        float2 ph = expmi_fs(qh, ql, ((float)(8 * y8) - yoff) * vox);
         uint32_t re_hi[4], im_hi[4], re_lo[4], im_lo[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
@@ -134,10 +156,10 @@ __device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int y = 8 * y8 + e + u;
-                float2 ph = make_float2(0.f, 0.f);
-                if (y < P.ny && p < P.n_pix) ph = expmi_fs(qh, ql, ((float)y - yoff) * vox);
-                cr[u] = ph.x;
-                ci[u] = ph.y;
+                const bool in = valid && y < P.ny;
+                cr[u] = in ? ph.x : 0.f;
+                ci[u] = in ? ph.y : 0.f;
+                ph = cmul(ph, step);
             }
             uint16_t rh0 = to16(cr[0], P.bf16), rh1 = to16(cr[1], P.bf16);
             uint16_t ih0 = to16(ci[0], P.bf16), ih1 = to16(ci[1], P.bf16);
@@ -162,28 +184,29 @@ __device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)
-    msft_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcParams P) {
+    msft_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t a_bytes = (uint32_t)P.nkb_a * kKBlockBytes;
     uint8_t *sA_hi = base;
     uint8_t *sA_lo = base + a_bytes;
-    uint8_t *sB = base + (P.split ? 2 : 1) * a_bytes;
-    const uint32_t stage_bytes = (uint32_t)P.Nxp * 2 * 128;
-    float2 *red = reinterpret_cast<float2 *>(sB + (size_t)P.stages * stage_bytes);
+    uint8_t *ring = base + (P.split ? 2 : 1) * a_bytes;
+    const uint32_t R = P.ring_bytes;
+    float2 *red = reinterpret_cast<float2 *>(ring + R);
     uint64_t *bars = reinterpret_cast<uint64_t *>(red + kBM);
     uint64_t *full = bars;
-    uint64_t *empty = bars + kMaxStages;
-    uint64_t *tfull = bars + 2 * kMaxStages;
+    uint64_t *empty = bars + kSlots;
+    uint64_t *tfull = bars + 2 * kSlots;
     uint64_t *tempty = tfull + 2;
     uint64_t *drain = tempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *a_full = drain + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_full + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < P.stages; ++s) {
+        for (int s = 0; s < kSlots; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
@@ -192,6 +215,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(smem_u32(&tempty[b]), kEpiWarps);
         }
         mbar_init(smem_u32(drain), 1);
+        mbar_init(smem_u32(a_full), kEpiThreads);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -204,90 +228,99 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    uint32_t prod_it = 0, mma_it = 0, acc_it = 0, epi_it = 0;
+    uint32_t prod_it = 0, oldest = 0, mma_it = 0, acc_it = 0, epi_it = 0;
     const int nch = P.Nxp >> 4;                 // 16-column chunks per slice
 
-    for (int mt = blockIdx.x; mt < P.num_m_tiles; mt += gridDim.x) {
-        if (warp < kEpiWarps) {
-            build_phase_tile(P, mt, sA_hi, sA_lo, threadIdx.x, kEpiWarps * 32);
-            fence_async_smem();
-        }
-        __syncthreads();
-        if (*abort_flag) break;
-
-        if (warp == kProducerWarp) {
-            if (lane == 0) {
-                bool ok = true;
+    if (warp == kProducerWarp) {
+        // ---------------- TMA producer: every tile, slice and occupied K block ----------------
+        if (lane == 0) {
+            bool ok = true;
+            unsigned long long head = 0, tail = 0;     // unwrapped ring positions
+            unsigned long long ends[kSlots];            // end of each stage in flight, by slot
+            uint32_t head_off = 0;                      // head modulo the ring
+            for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x) {
                 for (int t = 0; t < P.nz && ok; ++t) {
                     const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
                     if (ts.empty) continue;
                     const int nchunks = ts.c_hi - ts.c_lo;
-                    const uint32_t bytes = (uint32_t)(2 * nchunks * 16 * 128);
+                    const uint32_t sz = (uint32_t)(kPlanes * 16 * nchunks * 128);
+                    const CUtensorMap *map = &maps.m[nchunks - 1];
                     for (int kb = 0; kb < P.nkb_b; ++kb) {
                         if (((ts.kmask >> (4 * kb)) & 0xFu) == 0) continue;
-                        const uint32_t s = prod_it % P.stages, ph = (prod_it / P.stages) & 1;
-                        if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutProducer)) {
-                            ok = false;
-                            break;
+                        const uint32_t off = ring_start(head_off, sz, R);
+                        const unsigned long long start = head + (off == head_off ? 0u : R - head_off);
+                        // reclaim consumed stages until this one has a slot and its bytes are free
+                        while (oldest < prod_it && (prod_it - oldest >= (uint32_t)kSlots || start + sz > tail + R)) {
+                            const uint32_t so = oldest % kSlots;
+                            if (!mbar_wait(smem_u32(&empty[so]), (oldest / kSlots) & 1, abort_flag, P.err,
+                                           kErrTimeoutProducer)) {
+                                ok = false;
+                                break;
+                            }
+                            tail = ends[so];
+                            ++oldest;
                         }
+                        if (!ok) break;
+                        const uint32_t s = prod_it % kSlots;
+                        ends[s] = start + sz;
+                        head = start + sz;
+                        head_off = off + sz;
                         const uint32_t fb = smem_u32(&full[s]);
-                        mbar_arrive_expect_tx(fb, bytes);
-                        const uint32_t dst = smem_u32(sB + (size_t)s * stage_bytes);
-                        // the occupied 16-row chunks of the Re rows and of the Im rows
-                        for (int c = ts.c_lo; c < ts.c_hi; ++c) {
-                            tma_load_2d(dst + (uint32_t)(16 * c) * 128u, &tmap, fb, kb * kBK, t * 2 * P.Nxp + 16 * c);
-                            tma_load_2d(dst + (uint32_t)(P.Nxp + 16 * c) * 128u, &tmap, fb, kb * kBK,
-                                        t * 2 * P.Nxp + P.Nxp + 16 * c);
-                        }
+                        mbar_arrive_expect_tx(fb, sz);
+                        tma_load_3d(smem_u32(ring + off), map, fb, kb * kBK, 16 * ts.c_lo, kPlanes * t);
                         ++prod_it;
                     }
                 }
             }
-            __syncwarp();
-        } else if (warp == kMmaWarp) {
-            if (lane == 0) {
-                bool ok = true;
-                const uint32_t a_hi = smem_u32(sA_hi), a_lo = smem_u32(sA_lo), b0 = smem_u32(sB);
+        }
+        __syncwarp();
+    } else if (warp == kMmaWarp) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            bool ok = true;
+            const uint64_t ahi0 = sw128_desc(smem_u32(sA_hi)), alo0 = sw128_desc(smem_u32(sA_lo));
+            const uint64_t ring0 = sw128_desc(smem_u32(ring));
+            uint32_t head_off = 0;
+            uint32_t tl = 0;
+            for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x, ++tl) {
+                if (!mbar_wait(smem_u32(a_full), tl & 1, abort_flag, P.err, kErrTimeoutMma)) break;
+                tc_fence_after();
                 for (int t = 0; t < P.nz && ok; ++t) {
                     const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
                     if (ts.empty) continue;
+                    const uint32_t nr = 16u * (uint32_t)(ts.c_hi - ts.c_lo);
+                    const uint32_t sz = (uint32_t)kPlanes * nr * 128u;
+                    const uint32_t idesc = P.idesc | (((2u * nr) >> 3) << 17);
                     const uint32_t b = acc_it & 1, aph = (acc_it >> 1) & 1;
                     if (!mbar_wait(smem_u32(&tempty[b]), aph ^ 1, abort_flag, P.err, kErrTimeoutMma)) break;
                     tc_fence_after();
-                    // four MMA chains per K step over the occupied x chunks:
-                    // Re G += Pr Sr - Pi Si, Im G += Pr Si + Pi Sr
-                    const uint32_t nr = 16u * (uint32_t)(ts.c_hi - ts.c_lo);
-                    const uint32_t idesc = P.idesc | ((nr >> 3) << 17);
-                    const uint32_t idesc_neg = idesc | (1u << 13);         // negate A
-                    const uint32_t d_re = tmem_base + b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)ts.c_lo;
-                    const uint32_t d_im = d_re + (uint32_t)P.Nxp;
-                    const uint32_t row_re = 16u * (uint32_t)ts.c_lo * 128u;
-                    const uint32_t row_im = row_re + (uint32_t)P.Nxp * 128u;
+                    const uint32_t d = tmem_base + b * (uint32_t)(2 * P.Nxp);
                     bool first = true;
                     for (int kb = 0; kb < P.nkb_b; ++kb) {
                         const uint32_t kbits = (ts.kmask >> (4 * kb)) & 0xFu;
                         if (kbits == 0) continue;
-                        const uint32_t s = mma_it % P.stages, ph = (mma_it / P.stages) & 1;
+                        const uint32_t off = ring_start(head_off, sz, R);
+                        head_off = off + sz;
+                        const uint32_t s = mma_it % kSlots, ph = (mma_it / kSlots) & 1;
                         if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t bs = b0 + s * stage_bytes;
+                        // descriptors advance by encoded (>> 4) byte offsets
+                        const uint64_t w2 = ring0 + (uint64_t)(off >> 4);          // rows [0, 2 nr): [-Si | Sr]
+                        const uint64_t w1 = w2 + (uint64_t)((nr * 128u) >> 4);    // rows [nr, 3 nr): [Sr | Si]
+#pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             if (!((kbits >> kk) & 1u)) continue;
-                            const int y0 = 64 * kb + 16 * kk;                  // first y of this K step
-                            const uint32_t off_r = a_k_offset(y0), off_i = a_k_offset(P.Nyp + y0);
-                            const uint64_t bsr = sw128_desc(bs + row_re + kk * 32);
-                            const uint64_t bsi = sw128_desc(bs + row_im + kk * 32);
-                            const uint32_t accum = first ? 0u : 1u;
-                            for (int part = 0; part < (P.split ? 2 : 1); ++part) {
-                                const uint32_t ab = part ? a_lo : a_hi;
-                                const uint64_t pr = sw128_desc(ab + off_r), pi = sw128_desc(ab + off_i);
-                                mma_f16(d_re, pr, bsr, idesc, part ? 1u : accum);
-                                mma_f16(d_re, pi, bsi, idesc_neg, 1u);
-                                mma_f16(d_im, pr, bsi, idesc, part ? 1u : accum);
-                                mma_f16(d_im, pi, bsr, idesc, 1u);
+                            const int y0 = 64 * kb + 16 * kk;                    // first y of this K step
+                            const uint64_t off_r = a_k_offset(y0) >> 4, off_i = a_k_offset(P.Nyp + y0) >> 4;
+                            const uint64_t b1 = w1 + (uint64_t)(kk * 2), b2 = w2 + (uint64_t)(kk * 2);
+                            mma_f16(d, ahi0 + off_r, b1, idesc, first ? 0u : 1u);
+                            mma_f16(d, ahi0 + off_i, b2, idesc, 1u);
+                            if (P.split) {
+                                mma_f16(d, alo0 + off_r, b1, idesc, 1u);
+                                mma_f16(d, alo0 + off_i, b2, idesc, 1u);
                             }
                             first = false;
                         }
@@ -299,11 +332,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     ++acc_it;
                 }
             }
-            __syncwarp();
-        } else {
-            // ---------------- epilogue warps ----------------
-            const int quarter = warp & 3, half = warp >> 2;
-            const int m = quarter * 32 + lane;
+        }
+        __syncwarp();
+    } else {
+        // ---------------- phase tile + epilogue warps ----------------
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = quarter * 32 + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        // Every epilogue thread runs every tile iteration (after an abort the
+        // waits return at once), so the named barriers below always meet.
+        for (int mt = blockIdx.x; mt < P.num_m_tiles; mt += gridDim.x) {
+            // The tensor core is done with the previous tile's phase operand:
+            // this thread has seen the completion of its last slice.
+            if (!*abort_flag) build_phase_tile(P, mt, sA_hi, sA_lo, threadIdx.x);
+            fence_async_smem();
+            mbar_arrive(smem_u32(a_full));
+
             const long long p = (long long)mt * kBM + m;
             const bool valid = p < P.n_pix;
             const double qx = valid ? P.q[3 * p] : 0.0;
@@ -317,22 +361,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const float2 Zstep = expmi_f(qz, P.voxel);
             float2 Z = expmi_f(qz, (0 - 0.5 * (P.nz - 1)) * P.voxel);
             float2 acc = make_float2(0.f, 0.f);
-            const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
             for (int t = 0; t < P.nz; ++t) {
                 const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
                 if (!ts.empty) {
                     const uint32_t b = epi_it & 1, ph = (epi_it >> 1) & 1;
-                    if (!mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue)) break;
+                    // one decision per warp: the lanes below meet at __syncwarp
+                    const bool got = mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue);
+                    if (!__all_sync(0xffffffffu, got)) break;
                     tc_fence_after();
+                    const uint32_t nr = 16u * (uint32_t)(ts.c_hi - ts.c_lo);
                     float2 acct = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         // chunks alternate between the two halves
                         if (c < nch && c >= ts.c_lo && c < ts.c_hi && (c & 1) == half) {
-                            const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)c;
+                            const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)(c - ts.c_lo);
                             float gr[16], gi[16];
                             tmem_ld16(lane_base + col, gr);
-                            tmem_ld16(lane_base + col + (uint32_t)P.Nxp, gi);
+                            tmem_ld16(lane_base + col + nr, gi);
                             tmem_ld_wait(gr, gi);
                             float hr = 0.f, hi = 0.f;
 #pragma unroll
@@ -359,7 +405,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     Z = cmul(Z, Zstep);
             }
             if (half == 1) red[m] = acc;
-            named_bar_sync(kEpiWarps * 32);
+            named_bar_sync(kEpiThreads);
             if (half == 0 && valid) {
                 const float2 o = red[m];
                 float2 a = make_float2(acc.x + o.x, acc.y + o.y);
@@ -367,8 +413,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 P.A[p] = a;
                 P.I[p] = a.x * a.x + a.y * a.y;
             }
+            named_bar_sync(kEpiThreads);
         }
-        __syncthreads();
     }
 
     // ---- teardown: make sure no tensor-core or TMA work is in flight ----
@@ -381,9 +427,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         if (warp == kProducerWarp && lane == 0) {
             volatile int dummy = 0;
-            const uint32_t first = prod_it > (uint32_t)P.stages ? prod_it - P.stages : 0;
-            for (uint32_t it = first; it < prod_it; ++it) {
-                const uint32_t s = it % P.stages, ph = (it / P.stages) & 1;
+            for (uint32_t it = oldest; it < prod_it; ++it) {
+                const uint32_t s = it % kSlots, ph = (it / kSlots) & 1;
                 mbar_wait(smem_u32(&full[s]), ph, &dummy, P.err, kErrTimeoutDrain);
             }
         }
@@ -400,12 +445,14 @@ static size_t tc_fixed_bytes() { return 1024 /*align*/ + kBM * sizeof(float2) + 
 
 static int tc_nkb(int K) { return (K + kBK - 1) / kBK; }
 
-int tc_max_stages(int Nyp, int Nxp, bool split) {
-    size_t a = (size_t)(split ? 2 : 1) * tc_nkb(2 * Nyp) * kKBlockBytes;
-    size_t stage = (size_t)Nxp * 2 * 128;
-    if (a + tc_fixed_bytes() + 2 * stage > (size_t)kMaxSmem) return 0;
-    size_t s = ((size_t)kMaxSmem - a - tc_fixed_bytes()) / stage;
-    return (int)(s > (size_t)kMaxStages ? kMaxStages : s);
+// Bytes of the slice-stage ring left beside the phase operand, or 0 when two
+// full-width stages do not fit.
+size_t tc_ring_bytes(int Nyp, int Nxp, bool split) {
+    const size_t a = (size_t)(split ? 2 : 1) * tc_nkb(2 * Nyp) * kKBlockBytes;
+    const size_t full_stage = (size_t)kPlanes * Nxp * 128;
+    if (a + tc_fixed_bytes() >= (size_t)kMaxSmem) return 0;
+    const size_t r = ((size_t)kMaxSmem - a - tc_fixed_bytes()) / 1024 * 1024;
+    return r >= 2 * full_stage ? r : 0;
 }
 
 double tc_issued_flops(const int *bounds, int nz, int Nxp, int Nyp, long long n_pix, bool split) {
@@ -415,8 +462,8 @@ double tc_issued_flops(const int *bounds, int nz, int Nxp, int Nyp, long long n_
         const TileSpan ts = tile_span(bounds, nz, t, Nxp, Nyp);
         if (ts.empty) continue;
         const int nsteps = __builtin_popcount(ts.kmask);
-        // four real MMAs of 128 x (16 * chunks) x 16 per K step
-        per_tile += 4.0 * 2.0 * kBM * (16.0 * (ts.c_hi - ts.c_lo)) * 16.0 * nsteps;
+        // two real MMAs of 128 x (2 * 16 * chunks) x 16 per K step
+        per_tile += 2.0 * 2.0 * kBM * (2.0 * 16.0 * (ts.c_hi - ts.c_lo)) * 16.0 * nsteps;
     }
     return per_tile * (double)m_tiles * (split ? 2.0 : 1.0);
 }
@@ -426,8 +473,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                   CUtensorMapFloatOOBfill);
 
-bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, bool bf16, std::string *why) {
-    (void)Nxp;
+// One map per span width: map k-1 copies a box of 64 y x 16k rows x the
+// three planes of one slice.
+bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why) {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         void *ptr = nullptr;
@@ -440,22 +488,30 @@ bool encode_tmap_B(CUtensorMap *map, void *base, int Kp, size_t rows, int Nxp, b
         }
         fn = reinterpret_cast<EncodeTiledFn>(ptr);
     }
-    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, 16u};            // one 16-row x chunk per copy
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims,
-                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+    std::memset(maps, 0, sizeof(TcMaps));
+    const int nch = Nxp / 16;
+    if (nch < 1 || nch > kTcMaxChunks) {
+        *why = "slice width outside the tensor-core range";
         return false;
+    }
+    for (int k = 1; k <= nch; ++k) {
+        cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)Nxp, (cuuint64_t)kPlanes * nz};
+        cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Nxp * Kp * 2};
+        cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)(16 * k), (cuuint32_t)kPlanes};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = fn(&maps->m[k - 1], bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                        base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+            return false;
+        }
     }
     return true;
 }
 
-cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n_pix, int nx, int ny, int nz,
-                           int Nxp, int Nyp, int Kp, double voxel, double str_re, double str_im, bool split,
+cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
+                           int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
                            bool bf16, const int *bounds, float2 *A, float *I, int *err, int sm_count,
                            cudaStream_t st) {
     TcParams P;
@@ -465,18 +521,17 @@ cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n
     P.nx = nx;
     P.ny = ny;
     P.nz = nz;
-    (void)Kp;
     P.Nxp = Nxp;
     P.Nyp = Nyp;
     P.nkb_a = tc_nkb(2 * Nyp);
     P.nkb_b = tc_nkb(Nyp);
-    P.stages = tc_max_stages(Nyp, Nxp, split);
-    if (P.stages < 2 || Nxp % 16 != 0 || Nxp > 128 || Nyp % 16 != 0) return cudaErrorInvalidValue;
+    const size_t ring = tc_ring_bytes(Nyp, Nxp, split);
+    if (ring == 0 || Nxp % 16 != 0 || Nxp > 16 * kTcMaxChunks || Nyp % 16 != 0) return cudaErrorInvalidValue;
+    P.ring_bytes = (uint32_t)ring;
     P.split = split ? 1 : 0;
     P.bf16 = bf16 ? 1 : 0;
     P.num_m_tiles = (int)((n_pix + kBM - 1) / kBM);
-    const uint32_t N = (uint32_t)(2 * Nxp), M = kBM;
-    (void)N;
+    const uint32_t M = kBM;
     P.idesc = (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((M >> 4) << 24);
     uint32_t cols = 32;
     while (cols < (uint32_t)(4 * Nxp)) cols <<= 1;
@@ -487,7 +542,7 @@ cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n
     P.A = A;
     P.I = I;
     P.err = err;
-    size_t smem = (size_t)(split ? 2 : 1) * P.nkb_a * kKBlockBytes + (size_t)P.stages * Nxp * 2 * 128 + tc_fixed_bytes();
+    const size_t smem = (size_t)(split ? 2 : 1) * P.nkb_a * kKBlockBytes + ring + tc_fixed_bytes();
     // The attribute is per function and shared by every thread of the process:
     // always raise it to the largest size any launch uses, never to this
     // launch's size, so concurrent launches from other threads stay valid.
@@ -495,7 +550,7 @@ cudaError_t launch_msft_tc(const CUtensorMap &tmap, const double *q, long long n
     if (e != cudaSuccess) return e;
     int grid = P.num_m_tiles < sm_count ? P.num_m_tiles : sm_count;
     if (grid < 1) grid = 1;
-    msft_tc_kernel<<<grid, kTcThreads, smem, st>>>(tmap, P);
+    msft_tc_kernel<<<grid, kTcThreads, smem, st>>>(maps, P);
     return cudaGetLastError();
 }
 

@@ -305,7 +305,7 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     long long s_bytes;
     if (tc) {
         const long long Nxp = (c->nx + 15) / 16 * 16, Nyp = (c->ny + 15) / 16 * 16;
-        s_bytes = (long long)c->nz * 2 * Nxp * Nyp * 2;
+        s_bytes = (long long)c->nz * 3 * Nxp * Nyp * 2;   // planes -Im, Re, Im
     } else {
         s_bytes = nvox * cx;
     }

@@ -135,17 +135,21 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
         } else if (out.layout == kLayoutC32) {
             reinterpret_cast<float2 *>(out.s)[vidx] = make_float2((float)v.x, (float)v.y);
         } else {
-            // tensor-core slice operand: row j*2Nxp + x holds Re s(j, x, y) over y,
-            // row j*2Nxp + Nxp + x holds Im s(j, x, y) (see msft_tc.cu)
-            const size_t row_r = (size_t)iz * 2 * out.Nxp + ix;
+            // tensor-core slice operand: three planes per slice, rows
+            // (3j + 0) Nxp + x = -Im s, (3j + 1) Nxp + x = Re s, (3j + 2) Nxp + x = Im s,
+            // each row running over y (msft_tc.cu reads [Re | Im] and [-Im | Re] windows)
+            const size_t row_n = (size_t)iz * 3 * out.Nxp + ix;
+            const size_t row_r = row_n + out.Nxp;
             const size_t row_i = row_r + out.Nxp;
             const float sr = (float)v.x, si = (float)v.y;
             if (out.layout == kLayoutTcF16) {
                 __half *B = reinterpret_cast<__half *>(out.s);
+                B[row_n * out.Kp + iy] = __float2half_rn(-si);
                 B[row_r * out.Kp + iy] = __float2half_rn(sr);
                 B[row_i * out.Kp + iy] = __float2half_rn(si);
             } else {
                 __nv_bfloat16 *B = reinterpret_cast<__nv_bfloat16 *>(out.s);
+                B[row_n * out.Kp + iy] = __float2bfloat16_rn(-si);
                 B[row_r * out.Kp + iy] = __float2bfloat16_rn(sr);
                 B[row_i * out.Kp + iy] = __float2bfloat16_rn(si);
             }
