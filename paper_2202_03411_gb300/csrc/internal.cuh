@@ -115,7 +115,8 @@ struct scatman_handle {
     size_t b_rows = 0;
     // device buffers
     double *d_q = nullptr;          // [n_pix][3]
-    int *d_bounds = nullptr;        // per-slice occupied box [x_lo | x_hi | y_lo | y_hi], 4*nz ints
+    int *d_bounds = nullptr;        // per-slice occupied box [x_lo | x_hi | y_lo | y_hi], 4*nz ints,
+                                    // then nz packed spans for the tensor-core kernel
     float *d_chi = nullptr;         // [nvox]
     void *d_s = nullptr;            // slices in the contraction's layout
     size_t s_bytes = 0;
@@ -171,8 +172,8 @@ cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long lon
 size_t tc_ring_bytes(int Nyp, int Nxp, bool split);
 cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
                            int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
-                           bool bf16, const int *bounds, float2 *A, float *I, int *err, int sm_count,
-                           cudaStream_t st);
+                           bool bf16, const int *bounds, uint32_t *spans, float2 *A, float *I, int *err,
+                           int sm_count, cudaStream_t st);
 // Real flops one contraction launch issues for the given per-slice boxes.
 double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
 bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why);

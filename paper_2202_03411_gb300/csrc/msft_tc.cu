@@ -21,9 +21,10 @@
 // double buffered, and eight epilogue warps apply the x- and z-phases
 // (second line) while the next slice's MMAs run.
 //
-// Warp roles (320 threads): warps 0-7 build the phase tile and run the
+// Warp roles (352 threads): warps 0-7 build the phase tile and run the
 // epilogue (two per TMEM lane quarter, alternating x chunks), warp 8 is the
-// TMA producer, warp 9 issues the MMAs and owns the tensor memory.  The roles
+// TMA producer, warps 9 and 10 issue the MMAs of alternate slices (warp 9
+// owns the tensor memory).  The roles
 // meet only at mbarriers, so the producer runs ahead across pixel tiles.
 // Every wait is bounded: on time-out the kernel sets a bit in the error word,
 // releases its tensor memory and returns.
@@ -34,11 +35,11 @@
 
 namespace scm {
 
-constexpr int kTcThreads = 320;
+constexpr int kTcThreads = 352;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kProducerWarp = 8;
-constexpr int kMmaWarp = 9;
+constexpr int kMmaWarp = 9;                // MMA warps 9 and 10 take alternate slices
 constexpr int kBM = 128;
 constexpr int kBK = 64;                    // 64 x 16-bit = one 128-byte swizzle row
 constexpr int kKBlockBytes = kBM * 128;    // one 128 x 64 operand block
@@ -48,7 +49,7 @@ constexpr int kMaxSmem = 232448;           // 227 KB opt-in per block
 
 struct TcParams {
     const double *q;
-    const int *bounds;          // per-slice occupied box, or null (dense)
+    const uint32_t *spans;      // per-slice packed span (pack_span), 0 = empty
     long long n_pix;
     int nx, ny, nz;
     int Nxp, Nyp;               // padded x (multiple of 16) and y (multiple of 16)
@@ -98,6 +99,16 @@ __host__ __device__ inline TileSpan tile_span(const int *bounds, int nz, int t, 
     return ts;
 }
 
+// One word per slice for the kernel's roles: c_lo | c_hi << 4 | kmask << 8
+// (c_hi >= 1 for an occupied slice, so 0 means empty).
+__host__ __device__ inline uint32_t pack_span(const TileSpan &ts) {
+    return ts.empty ? 0u : (uint32_t)ts.c_lo | ((uint32_t)ts.c_hi << 4) | (ts.kmask << 8);
+}
+
+__global__ void pack_spans_kernel(const int *bounds, int nz, int Nxp, int Nyp, uint32_t *spans) {
+    for (int t = threadIdx.x; t < nz; t += blockDim.x) spans[t] = pack_span(tile_span(bounds, nz, t, Nxp, Nyp));
+}
+
 // Placement of a stage of `sz` bytes in the ring: a stage never wraps, it
 // starts over at offset 0 when it does not fit before the end.
 __device__ __forceinline__ uint32_t ring_start(uint32_t head_off, uint32_t sz, uint32_t ring) {
@@ -134,9 +145,9 @@ __device__ __forceinline__ uint32_t a_chunk_offset(int m, int k) {
 
 // Phase operand P[m, k] of one pixel tile (and its low part when split),
 // built by the kEpiThreads epilogue threads.  Thread `tid` always serves pixel
-// row m = tid % 128; each group of 8 consecutive y starts from one reduced
-// sincos and advances by the rotation e^{-i q_y dy} (FP32 complex products,
-// a few ulp over 8 steps, far below the 16-bit operands' resolution).
+// row m = tid % 128; each group of 8 consecutive y takes one reduced sincos
+// and FP32 complex products with the rotations e^{-i q_y k dy}, k = 1..4 (a
+// few ulp, far below the 16-bit operands' resolution).
 __device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint8_t *sA_hi, uint8_t *sA_lo,
                                                  int tid) {
     const int ny8 = P.Nyp >> 3;
@@ -146,9 +157,15 @@ __device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint
     const double qy = valid ? P.q[3 * p + 1] : 0.0;
     const float qh = (float)qy, ql = (float)(qy - (double)qh);
     const float yoff = 0.5f * (float)(P.ny - 1), vox = (float)P.voxel;
-    const float2 step = expmi_fs(qh, ql, vox);
+    // rotations by 1..3 and 4 voxels: each group of 8 phases is two levels deep
+    const float2 s1 = expmi_fs(qh, ql, vox);
+    const float2 s2 = cmul(s1, s1), s3 = cmul(s2, s1), s4 = cmul(s2, s2);
+#pragma unroll 2
     for (int y8 = tid / kBM; y8 < ny8; y8 += kEpiThreads / kBM) {
-        float2 ph = expmi_fs(qh, ql, ((float)(8 * y8) - yoff) * vox);
+        const float2 p0 = expmi_fs(qh, ql, ((float)(8 * y8) - yoff) * vox);
+        const float2 p4 = cmul(p0, s4);
+        const float2 phs[8] = {p0, cmul(p0, s1), cmul(p0, s2), cmul(p0, s3),
+                               p4, cmul(p4, s1), cmul(p4, s2), cmul(p4, s3)};
         uint32_t re_hi[4], im_hi[4], re_lo[4], im_lo[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
@@ -157,9 +174,8 @@ __device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint
             for (int u = 0; u < 2; ++u) {
                 const int y = 8 * y8 + e + u;
                 const bool in = valid && y < P.ny;
-                cr[u] = in ? ph.x : 0.f;
-                ci[u] = in ? ph.y : 0.f;
-                ph = cmul(ph, step);
+                cr[u] = in ? phs[e + u].x : 0.f;
+                ci[u] = in ? phs[e + u].y : 0.f;
             }
             uint16_t rh0 = to16(cr[0], P.bf16), rh1 = to16(cr[1], P.bf16);
             uint16_t ih0 = to16(ci[0], P.bf16), ih1 = to16(ci[1], P.bf16);
@@ -214,7 +230,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(smem_u32(&tfull[b]), 1);
             mbar_init(smem_u32(&tempty[b]), kEpiWarps);
         }
-        mbar_init(smem_u32(drain), 1);
+        mbar_init(smem_u32(drain), 2);
         mbar_init(smem_u32(a_full), kEpiThreads);
         *abort_flag = 0;
         fence_barrier_init();
@@ -233,107 +249,134 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     if (warp == kProducerWarp) {
         // ---------------- TMA producer: every tile, slice and occupied K block ----------------
-        if (lane == 0) {
-            bool ok = true;
-            unsigned long long head = 0, tail = 0;     // unwrapped ring positions
-            unsigned long long ends[kSlots];            // end of each stage in flight, by slot
-            uint32_t head_off = 0;                      // head modulo the ring
-            for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x) {
-                for (int t = 0; t < P.nz && ok; ++t) {
-                    const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
-                    if (ts.empty) continue;
-                    const int nchunks = ts.c_hi - ts.c_lo;
-                    const uint32_t sz = (uint32_t)(kPlanes * 16 * nchunks * 128);
-                    const CUtensorMap *map = &maps.m[nchunks - 1];
-                    for (int kb = 0; kb < P.nkb_b; ++kb) {
-                        if (((ts.kmask >> (4 * kb)) & 0xFu) == 0) continue;
-                        const uint32_t off = ring_start(head_off, sz, R);
-                        const unsigned long long start = head + (off == head_off ? 0u : R - head_off);
-                        // reclaim consumed stages until this one has a slot and its bytes are free
-                        while (oldest < prod_it && (prod_it - oldest >= (uint32_t)kSlots || start + sz > tail + R)) {
-                            const uint32_t so = oldest % kSlots;
-                            if (!mbar_wait(smem_u32(&empty[so]), (oldest / kSlots) & 1, abort_flag, P.err,
-                                           kErrTimeoutProducer)) {
-                                ok = false;
-                                break;
-                            }
-                            tail = ends[so];
-                            ++oldest;
-                        }
-                        if (!ok) break;
-                        const uint32_t s = prod_it % kSlots;
-                        ends[s] = start + sz;
-                        head = start + sz;
-                        head_off = off + sz;
-                        const uint32_t fb = smem_u32(&full[s]);
-                        mbar_arrive_expect_tx(fb, sz);
-                        tma_load_3d(smem_u32(ring + off), map, fb, kb * kBK, 16 * ts.c_lo, kPlanes * t);
-                        ++prod_it;
-                    }
-                }
-            }
-        }
-        __syncwarp();
-    } else if (warp == kMmaWarp) {
-        // ---------------- MMA issuer ----------------
-        if (lane == 0) {
-            bool ok = true;
-            const uint64_t ahi0 = sw128_desc(smem_u32(sA_hi)), alo0 = sw128_desc(smem_u32(sA_lo));
-            const uint64_t ring0 = sw128_desc(smem_u32(ring));
-            uint32_t head_off = 0;
-            uint32_t tl = 0;
-            for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x, ++tl) {
-                if (!mbar_wait(smem_u32(a_full), tl & 1, abort_flag, P.err, kErrTimeoutMma)) break;
-                tc_fence_after();
-                for (int t = 0; t < P.nz && ok; ++t) {
-                    const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
-                    if (ts.empty) continue;
-                    const uint32_t nr = 16u * (uint32_t)(ts.c_hi - ts.c_lo);
-                    const uint32_t sz = (uint32_t)kPlanes * nr * 128u;
-                    const uint32_t idesc = P.idesc | (((2u * nr) >> 3) << 17);
-                    const uint32_t b = acc_it & 1, aph = (acc_it >> 1) & 1;
-                    if (!mbar_wait(smem_u32(&tempty[b]), aph ^ 1, abort_flag, P.err, kErrTimeoutMma)) break;
-                    tc_fence_after();
-                    const uint32_t d = tmem_base + b * (uint32_t)(2 * P.Nxp);
-                    bool first = true;
-                    for (int kb = 0; kb < P.nkb_b; ++kb) {
-                        const uint32_t kbits = (ts.kmask >> (4 * kb)) & 0xFu;
-                        if (kbits == 0) continue;
-                        const uint32_t off = ring_start(head_off, sz, R);
-                        head_off = off + sz;
-                        const uint32_t s = mma_it % kSlots, ph = (mma_it / kSlots) & 1;
-                        if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) {
+        // The whole warp runs the loop (uniform values); one elected lane issues.
+        bool ok = true;
+        unsigned long long head = 0, tail = 0;     // unwrapped ring positions
+        unsigned long long ends[kSlots];            // end of each stage in flight, by slot
+        uint32_t head_off = 0;                      // head modulo the ring
+        for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x) {
+            uint32_t nxt = __ldg(&P.spans[0]);
+            for (int t = 0; t < P.nz && ok; ++t) {
+                const uint32_t w = nxt;
+                if (t + 1 < P.nz) nxt = __ldg(&P.spans[t + 1]);
+                if (w == 0) continue;
+                const int c_lo = (int)(w & 15u), nchunks = (int)((w >> 4) & 15u) - c_lo;
+                const uint32_t kmask = w >> 8;
+                const uint32_t sz = (uint32_t)(kPlanes * 16 * nchunks * 128);
+                const CUtensorMap *map = &maps.m[nchunks - 1];
+                for (int kb = 0; kb < P.nkb_b; ++kb) {
+                    if (((kmask >> (4 * kb)) & 0xFu) == 0) continue;
+                    const uint32_t off = ring_start(head_off, sz, R);
+                    const unsigned long long start = head + (off == head_off ? 0u : R - head_off);
+                    // reclaim consumed stages until this one has a slot and its bytes are free
+                    while (oldest < prod_it && (prod_it - oldest >= (uint32_t)kSlots || start + sz > tail + R)) {
+                        const uint32_t so = oldest % kSlots;
+                        if (!warp_wait(smem_u32(&empty[so]), (oldest / kSlots) & 1, abort_flag, P.err,
+                                       kErrTimeoutProducer)) {
                             ok = false;
                             break;
                         }
-                        tc_fence_after();
-                        // descriptors advance by encoded (>> 4) byte offsets
-                        const uint64_t w2 = ring0 + (uint64_t)(off >> 4);          // rows [0, 2 nr): [-Si | Sr]
-                        const uint64_t w1 = w2 + (uint64_t)((nr * 128u) >> 4);    // rows [nr, 3 nr): [Sr | Si]
+                        tail = ends[so];
+                        ++oldest;
+                    }
+                    if (!ok) break;
+                    const uint32_t s = prod_it % kSlots;
+                    ends[s] = start + sz;
+                    head = start + sz;
+                    head_off = off + sz;
+                    if (elect_one()) {
+                        const uint32_t fb = smem_u32(&full[s]);
+                        mbar_arrive_expect_tx(fb, sz);
+                        tma_load_3d(smem_u32(ring + off), map, fb, kb * kBK, 16 * c_lo, kPlanes * t);
+                    }
+                    __syncwarp();
+                    ++prod_it;
+                }
+            }
+        }
+    } else if (warp == kMmaWarp || warp == kMmaWarp + 1) {
+        // ---------------- MMA issuers (warp-wide loops, one elected lane issues) ----------------
+        // Warp kMmaWarp + r takes the occupied slices with acc_it % 2 == r, so one
+        // warp's waits and bookkeeping overlap the other's MMAs; both walk every
+        // stage to keep the ring placement in step with the producer.
+        const uint32_t mine = (uint32_t)(warp - kMmaWarp);
+        bool ok = true;
+        const uint64_t ahi0 = sw128_desc(smem_u32(sA_hi)), alo0 = sw128_desc(smem_u32(sA_lo));
+        const uint64_t ring0 = sw128_desc(smem_u32(ring));
+        uint32_t head_off = 0;
+        uint32_t tl = 0;
+        for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x, ++tl) {
+            if (!warp_wait(smem_u32(a_full), tl & 1, abort_flag, P.err, kErrTimeoutMma)) break;
+            tc_fence_after();
+            uint32_t nxt = __ldg(&P.spans[0]);
+            for (int t = 0; t < P.nz && ok; ++t) {
+                const uint32_t w = nxt;
+                if (t + 1 < P.nz) nxt = __ldg(&P.spans[t + 1]);
+                if (w == 0) continue;
+                const uint32_t nr = 16u * (((w >> 4) & 15u) - (w & 15u));
+                const uint32_t kmask = w >> 8;
+                const uint32_t sz = (uint32_t)kPlanes * nr * 128u;
+                const uint32_t idesc = P.idesc | (((2u * nr) >> 3) << 17);
+                const uint32_t b = acc_it & 1, aph = (acc_it >> 1) & 1;
+                if (b != mine) {
+                    // the other warp's slice: only advance the ring and stage counters
+                    for (int kb = 0; kb < P.nkb_b; ++kb) {
+                        if (((kmask >> (4 * kb)) & 0xFu) == 0) continue;
+                        head_off = ring_start(head_off, sz, R) + sz;
+                        ++mma_it;
+                    }
+                    ++acc_it;
+                    continue;
+                }
+                if (!warp_wait(smem_u32(&tempty[b]), aph ^ 1, abort_flag, P.err, kErrTimeoutMma)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + b * (uint32_t)(2 * P.Nxp);
+                bool first = true;
+                for (int kb = 0; kb < P.nkb_b; ++kb) {
+                    const uint32_t kbits = (kmask >> (4 * kb)) & 0xFu;
+                    if (kbits == 0) continue;
+                    const uint32_t off = ring_start(head_off, sz, R);
+                    head_off = off + sz;
+                    const uint32_t s = mma_it % kSlots, ph = (mma_it / kSlots) & 1;
+                    if (!warp_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // descriptors advance by encoded (>> 4) byte offsets
+                    const uint64_t w2 = ring0 + (uint64_t)(off >> 4);          // rows [0, 2 nr): [-Si | Sr]
+                    const uint64_t w1 = w2 + (uint64_t)((nr * 128u) >> 4);    // rows [nr, 3 nr): [Sr | Si]
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            if (!((kbits >> kk) & 1u)) continue;
-                            const int y0 = 64 * kb + 16 * kk;                    // first y of this K step
-                            const uint64_t off_r = a_k_offset(y0) >> 4, off_i = a_k_offset(P.Nyp + y0) >> 4;
-                            const uint64_t b1 = w1 + (uint64_t)(kk * 2), b2 = w2 + (uint64_t)(kk * 2);
-                            mma_f16(d, ahi0 + off_r, b1, idesc, first ? 0u : 1u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        if (!((kbits >> kk) & 1u)) continue;
+                        const int y0 = 64 * kb + 16 * kk;                    // first y of this K step
+                        const uint64_t off_r = a_k_offset(y0) >> 4, off_i = a_k_offset(P.Nyp + y0) >> 4;
+                        const uint64_t b1 = w1 + (uint64_t)(kk * 2), b2 = w2 + (uint64_t)(kk * 2);
+                        const uint32_t acc0 = first ? 0u : 1u;
+                        if (elect_one()) {
+                            mma_f16(d, ahi0 + off_r, b1, idesc, acc0);
                             mma_f16(d, ahi0 + off_i, b2, idesc, 1u);
                             if (P.split) {
                                 mma_f16(d, alo0 + off_r, b1, idesc, 1u);
                                 mma_f16(d, alo0 + off_i, b2, idesc, 1u);
                             }
-                            first = false;
                         }
-                        mma_commit(smem_u32(&empty[s]));
-                        ++mma_it;
+                        __syncwarp();
+                        first = false;
                     }
-                    if (!ok) break;
-                    mma_commit(smem_u32(&tfull[b]));
-                    ++acc_it;
+                    if (elect_one()) mma_commit(smem_u32(&empty[s]));
+                    __syncwarp();
+                    ++mma_it;
                 }
+                if (!ok) break;
+                if (elect_one()) mma_commit(smem_u32(&tfull[b]));
+                __syncwarp();
+                ++acc_it;
             }
         }
-        __syncwarp();
     } else {
         // ---------------- phase tile + epilogue warps ----------------
         const int quarter = warp & 3, half = warp >> 2;
@@ -361,21 +404,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const float2 Zstep = expmi_f(qz, P.voxel);
             float2 Z = expmi_f(qz, (0 - 0.5 * (P.nz - 1)) * P.voxel);
             float2 acc = make_float2(0.f, 0.f);
+            uint32_t nxt = __ldg(&P.spans[0]);
             for (int t = 0; t < P.nz; ++t) {
-                const TileSpan ts = tile_span(P.bounds, P.nz, t, P.Nxp, P.Nyp);
-                if (!ts.empty) {
+                const uint32_t w = nxt;
+                if (t + 1 < P.nz) nxt = __ldg(&P.spans[t + 1]);
+                if (w != 0) {
+                    const int c_lo = (int)(w & 15u), c_hi = (int)((w >> 4) & 15u);
                     const uint32_t b = epi_it & 1, ph = (epi_it >> 1) & 1;
                     // one decision per warp: the lanes below meet at __syncwarp
                     const bool got = mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue);
                     if (!__all_sync(0xffffffffu, got)) break;
                     tc_fence_after();
-                    const uint32_t nr = 16u * (uint32_t)(ts.c_hi - ts.c_lo);
+                    const uint32_t nr = 16u * (uint32_t)(c_hi - c_lo);
                     float2 acct = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         // chunks alternate between the two halves
-                        if (c < nch && c >= ts.c_lo && c < ts.c_hi && (c & 1) == half) {
-                            const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)(c - ts.c_lo);
+                        if (c < nch && c >= c_lo && c < c_hi && (c & 1) == half) {
+                            const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)(c - c_lo);
                             float gr[16], gi[16];
                             tmem_ld16(lane_base + col, gr);
                             tmem_ld16(lane_base + col + nr, gi);
@@ -420,8 +466,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- teardown: make sure no tensor-core or TMA work is in flight ----
     __syncthreads();
     if (*abort_flag) {
-        if (warp == kMmaWarp && lane == 0) {
-            mma_commit(smem_u32(drain));
+        if ((warp == kMmaWarp || warp == kMmaWarp + 1) && lane == 0) {
+            mma_commit(smem_u32(drain));       // one arrival per MMA warp
             volatile int dummy = 0;
             mbar_wait(smem_u32(drain), 0, &dummy, P.err, kErrTimeoutDrain);
         }
@@ -512,11 +558,11 @@ bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16,
 
 cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
                            int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
-                           bool bf16, const int *bounds, float2 *A, float *I, int *err, int sm_count,
-                           cudaStream_t st) {
+                           bool bf16, const int *bounds, uint32_t *spans, float2 *A, float *I, int *err,
+                           int sm_count, cudaStream_t st) {
     TcParams P;
     P.q = q;
-    P.bounds = bounds;
+    P.spans = spans;
     P.n_pix = n_pix;
     P.nx = nx;
     P.ny = ny;
@@ -548,6 +594,7 @@ cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix,
     // launch's size, so concurrent launches from other threads stay valid.
     cudaError_t e = cudaFuncSetAttribute(msft_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e != cudaSuccess) return e;
+    pack_spans_kernel<<<1, 256, 0, st>>>(bounds, nz, Nxp, Nyp, spans);
     int grid = P.num_m_tiles < sm_count ? P.num_m_tiles : sm_count;
     if (grid < 1) grid = 1;
     msft_tc_kernel<<<grid, kTcThreads, smem, st>>>(maps, P);

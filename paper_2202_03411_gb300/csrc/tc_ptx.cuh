@@ -35,11 +35,10 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait on a phase parity.  Returns false when the wait gave up (time
-// limit, or another role already gave up).
-static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err,
-                                       int code) {
-    if (mbar_try_wait(bar, parity)) return true;
+// Bounded wait on a phase parity (slow path, out of line).  Returns false when
+// the wait gave up (time limit, or another role already gave up).
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                                   int *err, int code) {
     const unsigned long long t0 = global_ns();
     while (true) {
         for (int i = 0; i < 32; ++i)
@@ -51,6 +50,28 @@ static __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, vol
             return false;
         }
     }
+}
+// Bounded wait: the common case (phase already complete) stays inline.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                          int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    return mbar_wait_slow(bar, parity, abort_flag, err, code);
+}
+// The same wait taken by a whole converged warp, with one outcome for all lanes.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int *err,
+                                          int code) {
+    const bool r = mbar_wait(bar, parity, abort_flag, err, code);
+    return __all_sync(0xffffffffu, r);
+}
+// One lane of a converged warp (the issuer of single-thread instructions).
+__device__ __forceinline__ bool elect_one() {
+    uint32_t pred = 0;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "elect.sync _|p, 0xffffffff;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(pred));
+    return pred != 0;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
     asm volatile(
