@@ -229,7 +229,7 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if ((rc = alloc_dev(h, (void **)&h->d_q, npix * 3 * sizeof(double), "q buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, (void **)&h->d_chi, nvox * sizeof(float), "occupancy buffer"))) return fail(rc);
     if (h->tensor_core &&
-        (rc = alloc_dev(h, (void **)&h->d_bounds, 5 * (size_t)c.nz * sizeof(int), "slice bounds")))
+        (rc = alloc_dev(h, (void **)&h->d_bounds, (6 * (size_t)c.nz + 2) * sizeof(int), "slice bounds")))
         return fail(rc);
     if (h->tensor_core) {
         h->s_bytes = h->b_rows * (size_t)h->Kp * 2;
@@ -354,7 +354,7 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
                                 c.theta_max_deg, h->k0, c.voxel, str_re, str_im, h->d_H, h->d_A, I_dev, h->stream);
     } else if (h->tensor_core) {
         e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, c.voxel, str_re,
-                           str_im, h->split, h->bf16, h->d_bounds, (uint32_t *)(h->d_bounds + 4 * c.nz), (float2 *)h->d_A,
+                           str_im, h->split, h->bf16, h->d_bounds, (uint2 *)(h->d_bounds + 4 * c.nz), (float2 *)h->d_A,
                            (float *)I_dev, h->d_err,
                            h->sm_count, h->stream);
     } else {

@@ -116,7 +116,7 @@ struct scatman_handle {
     // device buffers
     double *d_q = nullptr;          // [n_pix][3]
     int *d_bounds = nullptr;        // per-slice occupied box [x_lo | x_hi | y_lo | y_hi], 4*nz ints,
-                                    // then nz packed spans for the tensor-core kernel
+                                    // then the tensor-core kernel's occupied-slice list (nz + 1 uint2)
     float *d_chi = nullptr;         // [nvox]
     void *d_s = nullptr;            // slices in the contraction's layout
     size_t s_bytes = 0;
@@ -172,7 +172,7 @@ cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long lon
 size_t tc_ring_bytes(int Nyp, int Nxp, bool split);
 cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
                            int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
-                           bool bf16, const int *bounds, uint32_t *spans, float2 *A, float *I, int *err,
+                           bool bf16, const int *bounds, uint2 *list, float2 *A, float *I, int *err,
                            int sm_count, cudaStream_t st);
 // Real flops one contraction launch issues for the given per-slice boxes.
 double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);

@@ -49,7 +49,7 @@ constexpr int kMaxSmem = 232448;           // 227 KB opt-in per block
 
 struct TcParams {
     const double *q;
-    const uint32_t *spans;      // per-slice packed span (pack_span), 0 = empty
+    const uint2 *list;          // [0].x = occupied slices; [1 + i] = {slice t, pack_span}, t ascending
     long long n_pix;
     int nx, ny, nz;
     int Nxp, Nyp;               // padded x (multiple of 16) and y (multiple of 16)
@@ -105,8 +105,32 @@ __host__ __device__ inline uint32_t pack_span(const TileSpan &ts) {
     return ts.empty ? 0u : (uint32_t)ts.c_lo | ((uint32_t)ts.c_hi << 4) | (ts.kmask << 8);
 }
 
-__global__ void pack_spans_kernel(const int *bounds, int nz, int Nxp, int Nyp, uint32_t *spans) {
-    for (int t = threadIdx.x; t < nz; t += blockDim.x) spans[t] = pack_span(tile_span(bounds, nz, t, Nxp, Nyp));
+// Compacts the occupied slices into list[1 + i] = {t, pack_span}, in slice
+// order, and writes their count to list[0].x.  One block.
+__global__ void pack_spans_kernel(const int *bounds, int nz, int Nxp, int Nyp, uint2 *list) {
+    __shared__ int s_count[32];
+    __shared__ int s_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (threadIdx.x == 0) s_base = 0;
+    __syncthreads();
+    for (int t0 = 0; t0 < nz; t0 += blockDim.x) {
+        const int t = t0 + threadIdx.x;
+        const uint32_t w = t < nz ? pack_span(tile_span(bounds, nz, t, Nxp, Nyp)) : 0u;
+        const unsigned ball = __ballot_sync(0xffffffffu, w != 0);
+        if (lane == 0) s_count[wid] = __popc(ball);
+        __syncthreads();
+        int off = s_base;
+        for (int k = 0; k < wid; ++k) off += s_count[k];
+        if (w != 0) list[1 + off + __popc(ball & ((1u << lane) - 1u))] = make_uint2((uint32_t)t, w);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = s_base;
+            for (int k = 0; k < nw; ++k) tot += s_count[k];
+            s_base = tot;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) list[0] = make_uint2((uint32_t)s_base, 0u);
 }
 
 // Placement of a stage of `sz` bytes in the ring: a stage never wraps, it
@@ -115,21 +139,23 @@ __device__ __forceinline__ uint32_t ring_start(uint32_t head_off, uint32_t sz, u
     return head_off + sz > ring ? 0u : head_off;
 }
 
-__device__ __forceinline__ uint16_t to16(float v, int bf16) {
+// Two values as a packed 16-bit pair (first value in the low half) and the
+// packed pair of their remainders: v = hi + lo to about twice the format's
+// precision.  One packed conversion per pair and part.
+__device__ __forceinline__ void split_pair(float a, float b, int bf16, uint32_t *hi, uint32_t *lo) {
     if (bf16) {
-        __nv_bfloat16 h = __float2bfloat16_rn(v);
-        return *reinterpret_cast<uint16_t *>(&h);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 back = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(a - back.x, b - back.y);
+        *hi = *reinterpret_cast<const uint32_t *>(&h);
+        *lo = *reinterpret_cast<const uint32_t *>(&l);
+    } else {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 back = __half22float2(h);
+        const __half2 l = __floats2half2_rn(a - back.x, b - back.y);
+        *hi = *reinterpret_cast<const uint32_t *>(&h);
+        *lo = *reinterpret_cast<const uint32_t *>(&l);
     }
-    __half h = __float2half_rn(v);
-    return *reinterpret_cast<uint16_t *>(&h);
-}
-__device__ __forceinline__ float from16(uint16_t u, int bf16) {
-    if (bf16) {
-        __nv_bfloat16 h = *reinterpret_cast<__nv_bfloat16 *>(&u);
-        return __bfloat162float(h);
-    }
-    __half h = *reinterpret_cast<__half *>(&u);
-    return __half2float(h);
 }
 
 // Byte offset of K element k (a multiple of 16) from the start of a 128-row
@@ -148,13 +174,10 @@ __device__ __forceinline__ uint32_t a_chunk_offset(int m, int k) {
 // row m = tid % 128; each group of 8 consecutive y takes one reduced sincos
 // and FP32 complex products with the rotations e^{-i q_y k dy}, k = 1..4 (a
 // few ulp, far below the 16-bit operands' resolution).
-__device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint8_t *sA_hi, uint8_t *sA_lo,
-                                                 int tid) {
+__device__ __forceinline__ void build_phase_tile(const TcParams &P, double qy, bool valid, uint8_t *sA_hi,
+                                                 uint8_t *sA_lo, int tid) {
     const int ny8 = P.Nyp >> 3;
     const int m = tid % kBM;
-    const long long p = (long long)mt * kBM + m;
-    const bool valid = p < P.n_pix;
-    const double qy = valid ? P.q[3 * p + 1] : 0.0;
     const float qh = (float)qy, ql = (float)(qy - (double)qh);
     const float yoff = 0.5f * (float)(P.ny - 1), vox = (float)P.voxel;
     // rotations by 1..3 and 4 voxels: each group of 8 phases is two levels deep
@@ -169,24 +192,10 @@ __device__ __forceinline__ void build_phase_tile(const TcParams &P, int mt, uint
         uint32_t re_hi[4], im_hi[4], re_lo[4], im_lo[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
-            float cr[2], ci[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int y = 8 * y8 + e + u;
-                const bool in = valid && y < P.ny;
-                cr[u] = in ? phs[e + u].x : 0.f;
-                ci[u] = in ? phs[e + u].y : 0.f;
-            }
-            uint16_t rh0 = to16(cr[0], P.bf16), rh1 = to16(cr[1], P.bf16);
-            uint16_t ih0 = to16(ci[0], P.bf16), ih1 = to16(ci[1], P.bf16);
-            re_hi[e >> 1] = (uint32_t)rh0 | ((uint32_t)rh1 << 16);
-            im_hi[e >> 1] = (uint32_t)ih0 | ((uint32_t)ih1 << 16);
-            uint16_t rl0 = to16(cr[0] - from16(rh0, P.bf16), P.bf16);
-            uint16_t rl1 = to16(cr[1] - from16(rh1, P.bf16), P.bf16);
-            uint16_t il0 = to16(ci[0] - from16(ih0, P.bf16), P.bf16);
-            uint16_t il1 = to16(ci[1] - from16(ih1, P.bf16), P.bf16);
-            re_lo[e >> 1] = (uint32_t)rl0 | ((uint32_t)rl1 << 16);
-            im_lo[e >> 1] = (uint32_t)il0 | ((uint32_t)il1 << 16);
+            const int y = 8 * y8 + e;
+            const bool in0 = valid && y < P.ny, in1 = valid && y + 1 < P.ny;
+            split_pair(in0 ? phs[e].x : 0.f, in1 ? phs[e + 1].x : 0.f, P.bf16, &re_hi[e >> 1], &re_lo[e >> 1]);
+            split_pair(in0 ? phs[e].y : 0.f, in1 ? phs[e + 1].y : 0.f, P.bf16, &im_hi[e >> 1], &im_lo[e >> 1]);
         }
         const uint32_t o_re = a_chunk_offset(m, 8 * y8);
         const uint32_t o_im = a_chunk_offset(m, P.Nyp + 8 * y8);
@@ -254,12 +263,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         unsigned long long head = 0, tail = 0;     // unwrapped ring positions
         unsigned long long ends[kSlots];            // end of each stage in flight, by slot
         uint32_t head_off = 0;                      // head modulo the ring
+        const int n_occ = (int)__ldg(&P.list[0].x);
         for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x) {
-            uint32_t nxt = __ldg(&P.spans[0]);
-            for (int t = 0; t < P.nz && ok; ++t) {
-                const uint32_t w = nxt;
-                if (t + 1 < P.nz) nxt = __ldg(&P.spans[t + 1]);
-                if (w == 0) continue;
+            uint2 nxt = n_occ > 0 ? __ldg(&P.list[1]) : make_uint2(0u, 0u);
+            for (int i = 0; i < n_occ && ok; ++i) {
+                const int t = (int)nxt.x;
+                const uint32_t w = nxt.y;
+                if (i + 1 < n_occ) nxt = __ldg(&P.list[i + 2]);
                 const int c_lo = (int)(w & 15u), nchunks = (int)((w >> 4) & 15u) - c_lo;
                 const uint32_t kmask = w >> 8;
                 const uint32_t sz = (uint32_t)(kPlanes * 16 * nchunks * 128);
@@ -305,14 +315,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint64_t ring0 = sw128_desc(smem_u32(ring));
         uint32_t head_off = 0;
         uint32_t tl = 0;
+        const int n_occ = (int)__ldg(&P.list[0].x);
         for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x, ++tl) {
             if (!warp_wait(smem_u32(a_full), tl & 1, abort_flag, P.err, kErrTimeoutMma)) break;
             tc_fence_after();
-            uint32_t nxt = __ldg(&P.spans[0]);
-            for (int t = 0; t < P.nz && ok; ++t) {
-                const uint32_t w = nxt;
-                if (t + 1 < P.nz) nxt = __ldg(&P.spans[t + 1]);
-                if (w == 0) continue;
+            uint2 nxt = n_occ > 0 ? __ldg(&P.list[1]) : make_uint2(0u, 0u);
+            for (int i = 0; i < n_occ && ok; ++i) {
+                const uint32_t w = nxt.y;
+                if (i + 1 < n_occ) nxt = __ldg(&P.list[i + 2]);
                 const uint32_t nr = 16u * (((w >> 4) & 15u) - (w & 15u));
                 const uint32_t kmask = w >> 8;
                 const uint32_t sz = (uint32_t)kPlanes * nr * 128u;
@@ -384,71 +394,98 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         // Every epilogue thread runs every tile iteration (after an abort the
         // waits return at once), so the named barriers below always meet.
+        const int n_occ = (int)__ldg(&P.list[0].x);
+        // q of this thread's pixel, loaded one tile ahead
+        double nq0 = 0.0, nq1 = 0.0, nq2 = 0.0;
+        {
+            const long long p0 = (long long)blockIdx.x * kBM + m;
+            if (p0 < P.n_pix) {
+                nq0 = P.q[3 * p0];
+                nq1 = P.q[3 * p0 + 1];
+                nq2 = P.q[3 * p0 + 2];
+            }
+        }
         for (int mt = blockIdx.x; mt < P.num_m_tiles; mt += gridDim.x) {
+            const long long p = (long long)mt * kBM + m;
+            const bool valid = p < P.n_pix;
+            const double qx = nq0, qy = nq1, qz = nq2;
+            {
+                const long long pn = (long long)(mt + gridDim.x) * kBM + m;
+                if (pn < P.n_pix) {
+                    nq0 = P.q[3 * pn];
+                    nq1 = P.q[3 * pn + 1];
+                    nq2 = P.q[3 * pn + 2];
+                }
+            }
             // The tensor core is done with the previous tile's phase operand:
             // this thread has seen the completion of its last slice.
-            if (!*abort_flag) build_phase_tile(P, mt, sA_hi, sA_lo, threadIdx.x);
+            if (!*abort_flag) build_phase_tile(P, qy, valid, sA_hi, sA_lo, threadIdx.x);
             fence_async_smem();
             mbar_arrive(smem_u32(a_full));
 
-            const long long p = (long long)mt * kBM + m;
-            const bool valid = p < P.n_pix;
-            const double qx = valid ? P.q[3 * p] : 0.0;
-            const double qz = valid ? P.q[3 * p + 2] : 0.0;
+            // q split once into an FP32 pair; every coordinate below is FP32
+            // (FP64 throughput is a small fraction of FP32 on this part)
+            const float qxh = (float)qx, qxl = (float)(qx - (double)qxh);
+            const float qzh = (float)qz, qzl = (float)(qz - (double)qzh);
+            const float vf = (float)P.voxel;
+            const float xoff = 0.5f * (float)(P.nx - 1), zoff = 0.5f * (float)(P.nz - 1);
             float2 W[16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) W[k] = expmi_f(qx, k * P.voxel);
+            for (int k = 0; k < 16; ++k) W[k] = expmi_fs(qxh, qxl, (float)k * vf);
             float2 E[8];                                  // e^{-i q_x x0} of each 16-column chunk
 #pragma unroll
-            for (int c = 0; c < 8; ++c) E[c] = expmi_f(qx, (16 * c - 0.5 * (P.nx - 1)) * P.voxel);
-            const float2 Zstep = expmi_f(qz, P.voxel);
-            float2 Z = expmi_f(qz, (0 - 0.5 * (P.nz - 1)) * P.voxel);
+            for (int c = 0; c < 8; ++c) E[c] = expmi_fs(qxh, qxl, ((float)(16 * c) - xoff) * vf);
+            const float2 Zstep = expmi_fs(qzh, qzl, vf);
+            float2 Z = make_float2(1.f, 0.f);
+            int t_prev = -2;
             float2 acc = make_float2(0.f, 0.f);
-            uint32_t nxt = __ldg(&P.spans[0]);
-            for (int t = 0; t < P.nz; ++t) {
-                const uint32_t w = nxt;
-                if (t + 1 < P.nz) nxt = __ldg(&P.spans[t + 1]);
-                if (w != 0) {
-                    const int c_lo = (int)(w & 15u), c_hi = (int)((w >> 4) & 15u);
-                    const uint32_t b = epi_it & 1, ph = (epi_it >> 1) & 1;
-                    // one decision per warp: the lanes below meet at __syncwarp
-                    const bool got = mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue);
-                    if (!__all_sync(0xffffffffu, got)) break;
-                    tc_fence_after();
-                    const uint32_t nr = 16u * (uint32_t)(c_hi - c_lo);
-                    float2 acct = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        // chunks alternate between the two halves
-                        if (c < nch && c >= c_lo && c < c_hi && (c & 1) == half) {
-                            const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)(c - c_lo);
-                            float gr[16], gi[16];
-                            tmem_ld16(lane_base + col, gr);
-                            tmem_ld16(lane_base + col + nr, gi);
-                            tmem_ld_wait(gr, gi);
-                            float hr = 0.f, hi = 0.f;
-#pragma unroll
-                            for (int k = 0; k < 16; ++k) {
-                                hr = fmaf(W[k].x, gr[k], hr);
-                                hr = fmaf(-W[k].y, gi[k], hr);
-                                hi = fmaf(W[k].x, gi[k], hi);
-                                hi = fmaf(W[k].y, gr[k], hi);
-                            }
-                            acct.x = fmaf(E[c].x, hr, fmaf(-E[c].y, hi, acct.x));
-                            acct.y = fmaf(E[c].x, hi, fmaf(E[c].y, hr, acct.y));
-                        }
-                    }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
-                    acc.x = fmaf(Z.x, acct.x, fmaf(-Z.y, acct.y, acc.x));
-                    acc.y = fmaf(Z.x, acct.y, fmaf(Z.y, acct.x, acc.y));
-                    ++epi_it;
-                }
-                if (((t + 1) & 15) == 0)
-                    Z = expmi_f(qz, ((t + 1) - 0.5 * (P.nz - 1)) * P.voxel);
-                else
+            uint2 nxt = n_occ > 0 ? __ldg(&P.list[1]) : make_uint2(0u, 0u);
+            for (int i = 0; i < n_occ; ++i) {
+                const int t = (int)nxt.x;
+                const uint32_t w = nxt.y;
+                if (i + 1 < n_occ) nxt = __ldg(&P.list[i + 2]);
+                // e^{-i q_z z_t}: advanced by one slice step, re-anchored after a
+                // gap and every 16 occupied slices
+                if (t == t_prev + 1 && (i & 15) != 0)
                     Z = cmul(Z, Zstep);
+                else
+                    Z = expmi_fs(qzh, qzl, ((float)t - zoff) * vf);
+                t_prev = t;
+                const int c_lo = (int)(w & 15u), c_hi = (int)((w >> 4) & 15u);
+                const uint32_t b = epi_it & 1, ph = (epi_it >> 1) & 1;
+                // one decision per warp: the lanes below meet at __syncwarp
+                const bool got = mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue);
+                if (!__all_sync(0xffffffffu, got)) break;
+                tc_fence_after();
+                const uint32_t nr = 16u * (uint32_t)(c_hi - c_lo);
+                float2 acct = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    // chunks alternate between the two halves
+                    if (c < nch && c >= c_lo && c < c_hi && (c & 1) == half) {
+                        const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)(c - c_lo);
+                        float gr[16], gi[16];
+                        tmem_ld16(lane_base + col, gr);
+                        tmem_ld16(lane_base + col + nr, gi);
+                        tmem_ld_wait(gr, gi);
+                        float hr = 0.f, hi = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            hr = fmaf(W[k].x, gr[k], hr);
+                            hr = fmaf(-W[k].y, gi[k], hr);
+                            hi = fmaf(W[k].x, gi[k], hi);
+                            hi = fmaf(W[k].y, gr[k], hi);
+                        }
+                        acct.x = fmaf(E[c].x, hr, fmaf(-E[c].y, hi, acct.x));
+                        acct.y = fmaf(E[c].x, hi, fmaf(E[c].y, hr, acct.y));
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+                acc.x = fmaf(Z.x, acct.x, fmaf(-Z.y, acct.y, acc.x));
+                acc.y = fmaf(Z.x, acct.y, fmaf(Z.y, acct.x, acc.y));
+                ++epi_it;
             }
             if (half == 1) red[m] = acc;
             named_bar_sync(kEpiThreads);
@@ -558,11 +595,11 @@ bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16,
 
 cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
                            int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
-                           bool bf16, const int *bounds, uint32_t *spans, float2 *A, float *I, int *err,
+                           bool bf16, const int *bounds, uint2 *list, float2 *A, float *I, int *err,
                            int sm_count, cudaStream_t st) {
     TcParams P;
     P.q = q;
-    P.spans = spans;
+    P.list = list;
     P.n_pix = n_pix;
     P.nx = nx;
     P.ny = ny;
@@ -594,7 +631,7 @@ cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix,
     // launch's size, so concurrent launches from other threads stay valid.
     cudaError_t e = cudaFuncSetAttribute(msft_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e != cudaSuccess) return e;
-    pack_spans_kernel<<<1, 256, 0, st>>>(bounds, nz, Nxp, Nyp, spans);
+    pack_spans_kernel<<<1, 256, 0, st>>>(bounds, nz, Nxp, Nyp, list);
     int grid = P.num_m_tiles < sm_count ? P.num_m_tiles : sm_count;
     if (grid < 1) grid = 1;
     msft_tc_kernel<<<grid, kTcThreads, smem, st>>>(maps, P);
