@@ -49,6 +49,9 @@ def parse():
                     help="time this many forward+gradient fit steps of the 96^3 l<=6 workload and print a JSON line")
     ap.add_argument("--short-serving", type=int, default=240,
                     help="requests of the short serving run folded into the default line (0: skip)")
+    ap.add_argument("--main-only", action="store_true",
+                    help="time the main step only (no comparator, fit step, plain configs, timing study, "
+                         "CPU baseline or serving); for profiler runs")
     return ap.parse_args()
 
 
@@ -413,6 +416,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def launches_per_pattern(precision: str) -> int:
+    """Kernels one voxelise + forward launches: tensor-core modes reset the
+    slice boxes, voxelise with the scan, pack the occupied-slice list and run
+    the contraction; the CUDA-core modes voxelise and run the contraction with
+    its fixed-order partial-sum reduction."""
+    return 4 if precision.startswith("tc_") else 3
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -547,21 +558,23 @@ def main():
            "d2h_bytes_per_step": d2h}
 
     I0 = I_all[0].double().cpu().numpy()
-    fp32, I0_fp32 = fp32_comparator(g, shapes)
-    fit = fit_step_run(32, args.precision) if world == 1 else None
-    plain, c1, c2 = plain_configs() if world == 1 else (None, None, None)
-    fig8b = fig8b_run() if world == 1 else None
+    extras = world == 1 and not args.main_only
+    fp32, I0_fp32 = fp32_comparator(g, shapes) if not args.main_only else (None, None)
+    fit = fit_step_run(32, args.precision) if extras else None
+    plain, c1, c2 = plain_configs() if extras else (None, None, None)
+    fig8b = fig8b_run() if extras else None
     cpu = None
     err = None
     err_fp32 = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and extras and not args.no_cpu_baseline:
         cpu, err = cpu_baseline(shapes, g, I0, args.cpu_sample_pixels)
         _, err_fp32 = cpu_baseline(shapes, g, I0_fp32, 512)
         if plain is not None:
             plain["errors_vs_fp64_oracle"] = plain_config_errors(c1, c2)
-    fp32["rel_l2_I_vs_fp64_oracle"] = err_fp32
+    if fp32 is not None:
+        fp32["rel_l2_I_vs_fp64_oracle"] = err_fp32
     serving = None
-    if args.short_serving > 0 and world == 1:
+    if args.short_serving > 0 and extras:
         serving = serving_run(args.short_serving, args.serving_slots, args.precision, fractions=(0.8,))
 
     pat_sorted = sorted(pat_ms)
@@ -588,7 +601,7 @@ def main():
         "serving_short": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": 2 * B * args.steps,
+        "gpu_launches": launches_per_pattern(args.precision) * B * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }
