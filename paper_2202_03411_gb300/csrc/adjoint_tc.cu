@@ -12,7 +12,9 @@
 //   B[(y,im), 2p] = Im R, B[(y,im), 2p+1] = Re R.
 // Both operands depend on the pixel chunk, so eight generator warps build them
 // in shared memory (phase recurrences, FP16 with |L|, |R| <= 1) while one MMA
-// warp consumes the previous stages.  A CTA owns two slices (two TMEM
+// warp consumes the previous stages.  Per-pixel constants (q split into FP32
+// pairs, one-voxel rotations) come from a table built once per handle, so the
+// generators do no FP64 work and one reduced sincos per operand anchor.  A CTA owns two slices (two TMEM
 // accumulators sharing every R tile) and a contiguous range of pixels; the
 // pixel ranges' partial fields are summed in a fixed order afterwards.
 #include "internal.cuh"
@@ -24,15 +26,16 @@ constexpr int kAdjGenWarps = 8;
 constexpr int kAdjMmaWarp = 8;
 constexpr int kAdjThreads = (kAdjGenWarps + 1) * 32;
 constexpr int kAdjChunk = 32;                 // pixels per K block (64 real K = 128 bytes)
-constexpr int kAdjStages = 3;
+constexpr int kAdjMaxStages = 6;
 constexpr int kAdjRows = 128;                 // M: x rows
 constexpr int kAdjTileA = kAdjRows * 128;     // one A tile: 128 rows x 128 bytes
 constexpr int kAdjMaxSplits = 8;             // bounds the partial-field memory to 8 fields
 
 struct AdjParams {
+    const float4 *tab;          // per pixel: (qxh, qxl, qyh, qyl), (qzh, qzl, e^{+i qx dv}), (e^{+i qy dv}, e^{+i qz dv})
+    int stages;
     const float2 *A;            // forward field (FP32)
     const float *w;             // dL/dI
-    const double *q;
     const unsigned *gmax_bits;  // max |w A| as float bits
     long long n_pix;
     int nx, ny, nz, Nyp;
@@ -56,16 +59,39 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// Per-pixel constants of the generators: q as FP32 pairs and e^{+i q dv}.
+__global__ void adj_pixel_table_kernel(const double *__restrict__ q, long long n, double voxel,
+                                       float4 *__restrict__ tab) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+    const float qxh = (float)qx, qxl = (float)(qx - (double)qxh);
+    const float qyh = (float)qy, qyl = (float)(qy - (double)qyh);
+    const float qzh = (float)qz, qzl = (float)(qz - (double)qzh);
+    const float vf = (float)voxel;
+    // e^{+i t} = conj(e^{-i t}) = expmi(q, -c)
+    const float2 ex = expmi_fs(qxh, qxl, -vf), ey = expmi_fs(qyh, qyl, -vf), ez = expmi_fs(qzh, qzl, -vf);
+    tab[3 * p] = make_float4(qxh, qxl, qyh, qyl);
+    tab[3 * p + 1] = make_float4(qzh, qzl, ex.x, ex.y);
+    tab[3 * p + 2] = make_float4(ey.x, ey.y, ez.x, ez.y);
+}
+
+cudaError_t launch_adj_pixel_table(const double *q, long long n, double voxel, float4 *tab, cudaStream_t st) {
+    adj_pixel_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q, n, voxel, tab);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int Nn = 2 * P.Nyp;                               // real output columns per slice
     const uint32_t b_bytes = (uint32_t)Nn * 128;
     const uint32_t stage_bytes = 2 * kAdjTileA + b_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(base + kAdjStages * stage_bytes);
+    const int NS = P.stages;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + NS * stage_bytes);
     uint64_t *full = bars;
-    uint64_t *empty = bars + kAdjStages;
-    uint64_t *done = bars + 2 * kAdjStages;
+    uint64_t *empty = bars + kAdjMaxStages;
+    uint64_t *done = bars + 2 * kAdjMaxStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -76,7 +102,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
     const int n_chunks = p_end > p_begin ? (int)((p_end - p_begin + kAdjChunk - 1) / kAdjChunk) : 0;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kAdjStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&full[s]), kAdjGenWarps);
             mbar_init(smem_u32(&empty[s]), 1);
         }
@@ -94,28 +120,28 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == kAdjMmaWarp) {
-        if (lane == 0) {
-            const uint32_t d0 = tmem_base, d1 = tmem_base + (uint32_t)Nn;
-            const uint32_t sb = smem_u32(base);
-            bool ok = true;
-            for (int c = 0; c < n_chunks && ok; ++c) {
-                const uint32_t s = c % kAdjStages, ph = (c / kAdjStages) & 1;
-                if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t a0 = sb + s * stage_bytes, a1 = a0 + kAdjTileA, bb = a0 + 2 * kAdjTileA;
+        // warp-wide loop; one elected lane issues the MMAs and commits
+        const uint32_t d0 = tmem_base, d1 = tmem_base + (uint32_t)Nn;
+        const uint64_t desc0 = sw128_desc(smem_u32(base));
+        for (int c = 0; c < n_chunks; ++c) {
+            const uint32_t s = c % NS, ph = (c / NS) & 1;
+            if (!warp_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) break;
+            tc_fence_after();
+            // descriptors advance by encoded (>> 4) byte offsets
+            const uint64_t a0 = desc0 + (uint64_t)((s * stage_bytes) >> 4);
+            const uint64_t a1 = a0 + (uint64_t)(kAdjTileA >> 4), bb = a0 + (uint64_t)((2 * kAdjTileA) >> 4);
+            if (elect_one()) {
+#pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t bdesc = sw128_desc(bb + kk * 32);
                     const uint32_t acc = (c | kk) != 0;
-                    mma_f16(d0, sw128_desc(a0 + kk * 32), bdesc, P.idesc, acc);
-                    mma_f16(d1, sw128_desc(a1 + kk * 32), bdesc, P.idesc, acc);
+                    mma_f16(d0, a0 + (uint64_t)(2 * kk), bb + (uint64_t)(2 * kk), P.idesc, acc);
+                    mma_f16(d1, a1 + (uint64_t)(2 * kk), bb + (uint64_t)(2 * kk), P.idesc, acc);
                 }
                 mma_commit(smem_u32(&empty[s]));
             }
-            mma_commit(smem_u32(done));
+            __syncwarp();
         }
+        if (elect_one()) mma_commit(smem_u32(done));
         __syncwarp();
     } else {
         // ---------------- generator warps ----------------
@@ -128,28 +154,27 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         const float zj = ((float)j0 - 0.5f * (P.nz - 1)) * vox;
         const bool do_b = 16 * run < P.Nyp;
         for (int c = 0; c < n_chunks; ++c) {
-            const uint32_t s = c % kAdjStages, ph = (c / kAdjStages) & 1;
-            if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutEpilogue)) break;
+            const uint32_t s = c % NS, ph = (c / NS) & 1;
+            if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutEpilogue)) break;
             uint8_t *sA0 = base + s * stage_bytes;
             uint8_t *sA1 = sA0 + kAdjTileA;
             uint8_t *sB = sA0 + 2 * kAdjTileA;
             const long long p = p_begin + (long long)c * kAdjChunk + i;
             float2 g = make_float2(0.f, 0.f);
-            float qxh = 0.f, qxl = 0.f, qyh = 0.f, qyl = 0.f, qzh = 0.f, qzl = 0.f;
+            float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta, tcv = ta;
             if (p < p_end) {
                 const float2 a = P.A[p];
                 const float wp = P.w[p] * inv_g;
                 g = make_float2(a.x * wp, a.y * wp);
-                const double qx = P.q[3 * p], qy = P.q[3 * p + 1], qz = P.q[3 * p + 2];
-                qxh = (float)qx; qxl = (float)(qx - (double)qxh);
-                qyh = (float)qy; qyl = (float)(qy - (double)qyh);
-                qzh = (float)qz; qzl = (float)(qz - (double)qzh);
+                ta = P.tab[3 * p];
+                tb = P.tab[3 * p + 1];
+                tcv = P.tab[3 * p + 2];
             }
             // e^{+i t} = conj(e^{-i t}) = expmi(q, -c)
-            const float2 ez = expmi_fs(qzh, qzl, -zj);
-            const float2 ezs = expmi_fs(qzh, qzl, -vox);
-            const float2 ex = expmi_fs(qxh, qxl, -x0);
-            const float2 exs = expmi_fs(qxh, qxl, -vox);
+            const float2 ez = expmi_fs(tb.x, tb.y, -zj);
+            const float2 ezs = make_float2(tcv.z, tcv.w);
+            const float2 ex = expmi_fs(ta.x, ta.y, -x0);
+            const float2 exs = make_float2(tb.z, tb.w);
             float2 L0 = cmul(cmul(g, ez), ex);       // slice j0, row 16*run
             // rows of the A tiles (both slices)
 #pragma unroll 4
@@ -163,8 +188,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
             }
             // rows of the B tile: (y, re) and (y, im)
             if (do_b) {
-                const float2 eys = expmi_fs(qyh, qyl, -vox);
-                float2 R = expmi_fs(qyh, qyl, -y0);
+                const float2 eys = make_float2(tcv.x, tcv.y);
+                float2 R = expmi_fs(ta.z, ta.w, -y0);
 #pragma unroll 4
                 for (int k = 0; k < 16; ++k) {
                     const int y = 16 * run + k;
@@ -254,13 +279,23 @@ __global__ void adj_sum_kernel(const float2 *__restrict__ partial, int splits, l
     S[v] = s;
 }
 
-static size_t adj_smem_bytes(int Nyp) {
-    return 1024 + (size_t)kAdjStages * (2 * kAdjTileA + (size_t)2 * Nyp * 128) + 128;
+static size_t adj_stage_bytes(int Nyp) { return 2 * (size_t)kAdjTileA + (size_t)2 * Nyp * 128; }
+static size_t adj_fixed_bytes() { return 1024 + 256; }
+// Stages that fit beside the barriers (at most kAdjMaxStages).
+static int adj_stages(int Nyp) {
+    const size_t n = (232448 - adj_fixed_bytes()) / adj_stage_bytes(Nyp);
+    return (int)(n > (size_t)kAdjMaxStages ? kAdjMaxStages : n);
+}
+static size_t adj_smem_bytes(int Nyp) { return adj_fixed_bytes() + (size_t)adj_stages(Nyp) * adj_stage_bytes(Nyp); }
+
+static int adj_nyp(int ny) {
+    const int Nyp = (ny + 7) / 8 * 8;
+    return Nyp % 16 != 0 ? (Nyp + 15) / 16 * 16 : Nyp;   // 16-column epilogue groups
 }
 
 bool adjoint_tc_supported(int nx, int ny) {
-    const int Nyp = (ny + 7) / 8 * 8;
-    return nx <= kAdjRows && Nyp <= 128 && adj_smem_bytes(Nyp) <= 232448;
+    const int Nyp = adj_nyp(ny);
+    return nx <= kAdjRows && Nyp <= 128 && adj_stages(Nyp) >= 2;
 }
 
 // Pixel ranges per slice pair: balance the grid over the SMs (1 CTA per SM).
@@ -282,21 +317,21 @@ int adjoint_tc_splits(long long n_pix, int nz, int sm_count) {
     return best;
 }
 
-cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const double *q, long long n_pix, int nx, int ny, int nz,
-                              double voxel, int splits, float2 *partial, unsigned *gmax_bits, float2 *S, int *err,
-                              cudaStream_t st) {
+cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab, long long n_pix, int nx, int ny,
+                              int nz, double voxel, int splits, float2 *partial, unsigned *gmax_bits, float2 *S,
+                              int *err, cudaStream_t st) {
     AdjParams P;
+    P.tab = tab;
     P.A = A;
     P.w = w;
-    P.q = q;
     P.gmax_bits = gmax_bits;
     P.n_pix = n_pix;
     P.nx = nx;
     P.ny = ny;
     P.nz = nz;
-    P.Nyp = (ny + 7) / 8 * 8;
-    if (P.Nyp % 16 != 0) P.Nyp = (P.Nyp + 15) / 16 * 16;    // 16-column epilogue groups
-    if (!adjoint_tc_supported(nx, ny) || P.Nyp > 128) return cudaErrorInvalidValue;
+    P.Nyp = adj_nyp(ny);
+    if (!adjoint_tc_supported(nx, ny)) return cudaErrorInvalidValue;
+    P.stages = adj_stages(P.Nyp);
     const long long chunks = (n_pix + kAdjChunk - 1) / kAdjChunk;
     P.pix_per_split = (int)((chunks + splits - 1) / splits) * kAdjChunk;
     P.voxel = voxel;

@@ -142,6 +142,7 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_H);
     cudaFree(h->d_adj_part);
     cudaFree(h->d_gmax);
+    cudaFree(h->d_adj_tab);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (dev_prev >= 0) cudaSetDevice(dev_prev);
     delete h;
@@ -520,7 +521,14 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
             h->adj_part_count = cnt;
         }
         if (!h->d_gmax && (rc = alloc_dev(h, (void **)&h->d_gmax, sizeof(unsigned), "adjoint scale"))) return rc;
-        rc = check_cuda(h, launch_adjoint_tc((const float2 *)h->d_A, (const float *)dLdI_dev, h->d_q, h->n_pix, c.nx,
+        if (!h->d_adj_tab) {
+            if ((rc = alloc_dev(h, (void **)&h->d_adj_tab, (size_t)h->n_pix * 3 * sizeof(float4), "adjoint pixel table")))
+                return rc;
+            if ((rc = check_cuda(h, launch_adj_pixel_table(h->d_q, h->n_pix, c.voxel, h->d_adj_tab, h->stream),
+                                 "adjoint pixel table")))
+                return rc;
+        }
+        rc = check_cuda(h, launch_adjoint_tc((const float2 *)h->d_A, (const float *)dLdI_dev, h->d_adj_tab, h->n_pix, c.nx,
                                              c.ny, c.nz, c.voxel, splits, h->d_adj_part, h->d_gmax, (float2 *)h->d_S,
                                              h->d_err, h->stream),
                         "adjoint field (tensor cores)");

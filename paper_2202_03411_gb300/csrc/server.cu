@@ -318,7 +318,7 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     b += round_2mib(npix * (f64 ? 8 : 4));      // intensity scratch
     if (!tc) b += round_2mib(64 * npix * cx);   // partial fields (upper bound on splits)
     b += round_2mib(nvox * cx);                 // adjoint field (backward)
-    if (tc) b += round_2mib(8 * nvox * 8) + round_2mib(4);   // tensor-core adjoint partial fields (<= 8) + scale
+    if (tc) b += round_2mib(8 * nvox * 8) + round_2mib(4) + round_2mib(48 * npix);   // adjoint partial fields (<= 8), scale, pixel table
     b += round_2mib((608LL * ((SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1) + 2) + 256) * 8);
     return b;
 }

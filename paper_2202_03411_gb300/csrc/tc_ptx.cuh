@@ -143,6 +143,18 @@ __device__ __forceinline__ void tmem_ld_wait(float (&a)[16], float (&b)[16]) {
                  :
                  : "memory");
 }
+// No instruction: ties two more load destinations to a preceding
+// tcgen05.wait::ld so the compiler reads them only after that wait.
+__device__ __forceinline__ void tmem_ld_after_wait(float (&a)[16], float (&b)[16]) {
+    asm volatile(""
+                 : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(a[4]), "+f"(a[5]), "+f"(a[6]),
+                   "+f"(a[7]), "+f"(a[8]), "+f"(a[9]), "+f"(a[10]), "+f"(a[11]), "+f"(a[12]), "+f"(a[13]),
+                   "+f"(a[14]), "+f"(a[15]), "+f"(b[0]), "+f"(b[1]), "+f"(b[2]), "+f"(b[3]), "+f"(b[4]),
+                   "+f"(b[5]), "+f"(b[6]), "+f"(b[7]), "+f"(b[8]), "+f"(b[9]), "+f"(b[10]), "+f"(b[11]),
+                   "+f"(b[12]), "+f"(b[13]), "+f"(b[14]), "+f"(b[15])
+                 :
+                 : "memory");
+}
 // Named barrier 1 over `nthreads` threads (a subset of the CTA).
 __device__ __forceinline__ void named_bar_sync(int nthreads) {
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
