@@ -10,9 +10,11 @@
 //   A[x, 2p] = Re L, A[x, 2p+1] = Im L,
 //   B[(y,re), 2p] = Re R, B[(y,re), 2p+1] = -Im R,
 //   B[(y,im), 2p] = Im R, B[(y,im), 2p+1] = Re R.
-// Both operands depend on the pixel chunk, so eight generator warps build them
-// in shared memory (phase recurrences, FP16 with |L|, |R| <= 1) while one MMA
-// warp consumes the previous stages.  Per-pixel constants (q split into FP32
+// Both operands depend on the pixel chunk, so sixteen generator warps build
+// them in shared memory (phase recurrences, FP16 with |L|, |R| <= 1), one
+// 16-row run each (the L runs cover only x < nx: rows beyond feed output rows
+// that are never written back), while one MMA warp consumes the previous
+// stages.  Per-pixel constants (q split into FP32
 // pairs, one-voxel rotations) come from a table built once per handle, so the
 // generators do no FP64 work and one reduced sincos per operand anchor.  A CTA owns two slices (two TMEM
 // accumulators sharing every R tile) and a contiguous range of pixels; the
@@ -22,8 +24,8 @@
 
 namespace scm {
 
-constexpr int kAdjGenWarps = 8;
-constexpr int kAdjMmaWarp = 8;
+constexpr int kAdjGenWarps = 16;            // one 16-row operand run each
+constexpr int kAdjMmaWarp = kAdjGenWarps;
 constexpr int kAdjThreads = (kAdjGenWarps + 1) * 32;
 constexpr int kAdjChunk = 32;                 // pixels per K block (64 real K = 128 bytes)
 constexpr int kAdjMaxStages = 6;
@@ -147,12 +149,16 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         // ---------------- generator warps ----------------
         const float inv_g = 1.0f / fmaxf(__uint_as_float(*P.gmax_bits), 1e-30f);
         const int i = lane;                      // pixel within the chunk
-        const int run = warp;                    // 16-row run: rows 16*run .. 16*run + 15
+        // warp roles: runs 0 .. na-1 of the L tiles (x rows, both slices), then
+        // runs of the R tile; a warp without a run only signals the stage
+        const int na = (P.nx + 15) / 16, nb = P.Nyp / 16;
+        const bool is_a = warp < na, is_b = !is_a && warp - na < nb;
+        const int run = is_a ? warp : warp - na;  // rows 16*run .. 16*run + 15
         const float vox = (float)P.voxel;
         const float x0 = (16 * run - 0.5f * (P.nx - 1)) * vox;
         const float y0 = (16 * run - 0.5f * (P.ny - 1)) * vox;
         const float zj = ((float)j0 - 0.5f * (P.nz - 1)) * vox;
-        const bool do_b = 16 * run < P.Nyp;
+        const int rows_a = min(16, P.nx - 16 * run);
         for (int c = 0; c < n_chunks; ++c) {
             const uint32_t s = c % NS, ph = (c / NS) & 1;
             if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutEpilogue)) break;
@@ -160,43 +166,47 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
             uint8_t *sA1 = sA0 + kAdjTileA;
             uint8_t *sB = sA0 + 2 * kAdjTileA;
             const long long p = p_begin + (long long)c * kAdjChunk + i;
-            float2 g = make_float2(0.f, 0.f);
-            float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta, tcv = ta;
-            if (p < p_end) {
-                const float2 a = P.A[p];
-                const float wp = P.w[p] * inv_g;
-                g = make_float2(a.x * wp, a.y * wp);
-                ta = P.tab[3 * p];
-                tb = P.tab[3 * p + 1];
-                tcv = P.tab[3 * p + 2];
-            }
-            // e^{+i t} = conj(e^{-i t}) = expmi(q, -c)
-            const float2 ez = expmi_fs(tb.x, tb.y, -zj);
-            const float2 ezs = make_float2(tcv.z, tcv.w);
-            const float2 ex = expmi_fs(ta.x, ta.y, -x0);
-            const float2 exs = make_float2(tb.z, tb.w);
-            float2 L0 = cmul(cmul(g, ez), ex);       // slice j0, row 16*run
-            // rows of the A tiles (both slices)
+            const bool in = p < p_end;
+            if (is_a) {
+                float2 g = make_float2(0.f, 0.f);
+                float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta, tcv = ta;
+                if (in) {
+                    const float2 a = P.A[p];
+                    const float wp = P.w[p] * inv_g;
+                    g = make_float2(a.x * wp, a.y * wp);
+                    ta = P.tab[3 * p];
+                    tb = P.tab[3 * p + 1];
+                    tcv = P.tab[3 * p + 2];
+                }
+                // e^{+i t} = conj(e^{-i t}) = expmi(q, -c)
+                const float2 ez = expmi_fs(tb.x, tb.y, -zj);
+                const float2 ezs = make_float2(tcv.z, tcv.w);
+                const float2 ex = expmi_fs(ta.x, ta.y, -x0);
+                const float2 exs = make_float2(tb.z, tb.w);
+                float2 L0 = cmul(cmul(g, ez), ex);       // slice j0, row 16*run
 #pragma unroll 4
-            for (int k = 0; k < 16; ++k) {
-                const int r = 16 * run + k;
-                const float2 L1 = cmul(L0, ezs);
-                const uint32_t off = pair_offset(r, i);
-                *reinterpret_cast<uint32_t *>(sA0 + off) = pack_half2(L0.x, L0.y);
-                *reinterpret_cast<uint32_t *>(sA1 + off) = pack_half2(L1.x, L1.y);
-                L0 = cmul(L0, exs);
-            }
-            // rows of the B tile: (y, re) and (y, im)
-            if (do_b) {
+                for (int k = 0; k < rows_a; ++k) {
+                    const int r = 16 * run + k;
+                    const float2 L1 = cmul(L0, ezs);
+                    const uint32_t off = pair_offset(r, i);
+                    *reinterpret_cast<uint32_t *>(sA0 + off) = pack_half2(L0.x, L0.y);
+                    *reinterpret_cast<uint32_t *>(sA1 + off) = pack_half2(L1.x, L1.y);
+                    L0 = cmul(L0, exs);
+                }
+            } else if (is_b) {
+                // rows of the B tile: (y, re) and (y, im)
+                float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tcv = ta;
+                if (in) {
+                    ta = P.tab[3 * p];
+                    tcv = P.tab[3 * p + 2];
+                }
                 const float2 eys = make_float2(tcv.x, tcv.y);
-                float2 R = expmi_fs(ta.z, ta.w, -y0);
+                float2 R = in ? expmi_fs(ta.z, ta.w, -y0) : make_float2(0.f, 0.f);
 #pragma unroll 4
                 for (int k = 0; k < 16; ++k) {
                     const int y = 16 * run + k;
-                    if (y < P.Nyp) {
-                        *reinterpret_cast<uint32_t *>(sB + pair_offset(y, i)) = pack_half2(R.x, -R.y);
-                        *reinterpret_cast<uint32_t *>(sB + pair_offset(P.Nyp + y, i)) = pack_half2(R.y, R.x);
-                    }
+                    *reinterpret_cast<uint32_t *>(sB + pair_offset(y, i)) = pack_half2(R.x, -R.y);
+                    *reinterpret_cast<uint32_t *>(sB + pair_offset(P.Nyp + y, i)) = pack_half2(R.y, R.x);
                     R = cmul(R, eys);
                 }
             }
@@ -209,7 +219,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         const bool ok = n_chunks == 0 ? false : mbar_wait(smem_u32(done), 0, abort_flag, P.err, kErrTimeoutEpilogue);
         (void)dummy;
         tc_fence_after();
-        const int quarter = warp & 3, half = warp >> 2;
+        const int quarter = warp & 3, part = warp >> 2;   // TMEM lane quarter; column groups part, part + 4, ...
         const int x = quarter * 32 + lane;
         const float gmax = fmaxf(__uint_as_float(*P.gmax_bits), 1e-30f);
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         float2 *out = P.partial + (size_t)blockIdx.y * P.nvox;
         for (int sl = 0; sl < 2; ++sl) {
             const int j = j0 + sl;
-            for (int gq = half; gq < ych; gq += 2) {
+            for (int gq = part; gq < ych; gq += kAdjGenWarps / 4) {
                 float re[16], im[16];
                 tmem_ld16(lane_base + (uint32_t)(sl * Nn + 16 * gq), re);
                 tmem_ld16(lane_base + (uint32_t)(sl * Nn + P.Nyp + 16 * gq), im);
