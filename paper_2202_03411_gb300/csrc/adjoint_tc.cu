@@ -159,7 +159,33 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         const float y0 = (16 * run - 0.5f * (P.ny - 1)) * vox;
         const float zj = ((float)j0 - 0.5f * (P.nz - 1)) * vox;
         const int rows_a = min(16, P.nx - 16 * run);
+        // this lane's pixel data, loaded one chunk ahead so the L2 latency
+        // overlaps the previous chunk's generation
+        float2 a_n = make_float2(0.f, 0.f);
+        float w_n = 0.f;
+        float4 ta_n = make_float4(0.f, 0.f, 0.f, 0.f), tb_n = ta_n, tc_n = ta_n;
+        auto load_pixel = [&](int c) {
+            const long long p = p_begin + (long long)c * kAdjChunk + i;
+            if (c < n_chunks && p < p_end && (is_a || is_b)) {
+                ta_n = P.tab[3 * p];
+                tc_n = P.tab[3 * p + 2];
+                if (is_a) {
+                    a_n = P.A[p];
+                    w_n = P.w[p];
+                    tb_n = P.tab[3 * p + 1];
+                }
+            } else {
+                a_n = make_float2(0.f, 0.f);
+                w_n = 0.f;
+                ta_n = tb_n = tc_n = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        load_pixel(0);
         for (int c = 0; c < n_chunks; ++c) {
+            const float2 a_c = a_n;
+            const float w_c = w_n;
+            const float4 ta = ta_n, tb = tb_n, tcv = tc_n;
+            load_pixel(c + 1);
             const uint32_t s = c % NS, ph = (c / NS) & 1;
             if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutEpilogue)) break;
             uint8_t *sA0 = base + s * stage_bytes;
@@ -168,16 +194,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
             const long long p = p_begin + (long long)c * kAdjChunk + i;
             const bool in = p < p_end;
             if (is_a) {
-                float2 g = make_float2(0.f, 0.f);
-                float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta, tcv = ta;
-                if (in) {
-                    const float2 a = P.A[p];
-                    const float wp = P.w[p] * inv_g;
-                    g = make_float2(a.x * wp, a.y * wp);
-                    ta = P.tab[3 * p];
-                    tb = P.tab[3 * p + 1];
-                    tcv = P.tab[3 * p + 2];
-                }
+                const float wp = w_c * inv_g;
+                const float2 g = make_float2(a_c.x * wp, a_c.y * wp);
                 // e^{+i t} = conj(e^{-i t}) = expmi(q, -c)
                 const float2 ez = expmi_fs(tb.x, tb.y, -zj);
                 const float2 ezs = make_float2(tcv.z, tcv.w);
@@ -195,11 +213,6 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
                 }
             } else if (is_b) {
                 // rows of the B tile: (y, re) and (y, im)
-                float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tcv = ta;
-                if (in) {
-                    ta = P.tab[3 * p];
-                    tcv = P.tab[3 * p + 2];
-                }
                 const float2 eys = make_float2(tcv.x, tcv.y);
                 float2 R = in ? expmi_fs(ta.z, ta.w, -y0) : make_float2(0.f, 0.f);
 #pragma unroll 4
