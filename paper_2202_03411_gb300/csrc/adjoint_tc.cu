@@ -10,23 +10,26 @@
 //   A[x, 2p] = Re L, A[x, 2p+1] = Im L,
 //   B[(y,re), 2p] = Re R, B[(y,re), 2p+1] = -Im R,
 //   B[(y,im), 2p] = Im R, B[(y,im), 2p+1] = Re R.
-// Both operands depend on the pixel chunk, so sixteen generator warps build
-// them in shared memory (phase recurrences, FP16 with |L|, |R| <= 1), one
-// 16-row run each (the L runs cover only x < nx: rows beyond feed output rows
-// that are never written back), while one MMA warp consumes the previous
-// stages.  Per-pixel constants (q split into FP32
-// pairs, one-voxel rotations) come from a table built once per handle, so the
-// generators do no FP64 work and one reduced sincos per operand anchor.  A CTA owns two slices (two TMEM
-// accumulators sharing every R tile) and a contiguous range of pixels; the
-// pixel ranges' partial fields are summed in a fixed order afterwards.
+// The y-phase operand R depends only on the pixels, so it is built once per
+// handle as the tile image the MMA reads (128-byte swizzle, FP16, |R| <= 1) and
+// copied into each stage with one bulk copy; the x-phase operand L depends on
+// the slice and the weights, so eight generator warps build it in shared
+// memory (phase recurrences, FP16 with |L| <= 1), rows x < nx only (padding
+// rows feed output rows that are never written back), while one MMA warp
+// consumes the previous stages.  Per-pixel constants (q split into FP32 pairs,
+// one-voxel rotations) come from a table built once per handle, so the
+// generators do no FP64 work.  A CTA owns two slices (two TMEM accumulators
+// sharing every R tile) and a contiguous range of pixels; the pixel ranges'
+// partial fields are summed in a fixed order afterwards.
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
 namespace scm {
 
-constexpr int kAdjGenWarps = 16;            // one 16-row operand run each
-constexpr int kAdjMmaWarp = kAdjGenWarps;
-constexpr int kAdjThreads = (kAdjGenWarps + 1) * 32;
+constexpr int kAdjGenWarps = 8;             // build the x-phase operand, then the epilogue
+constexpr int kAdjLoadWarp = kAdjGenWarps;  // bulk-copies the y-phase operand
+constexpr int kAdjMmaWarp = kAdjGenWarps + 1;
+constexpr int kAdjThreads = (kAdjGenWarps + 2) * 32;
 constexpr int kAdjChunk = 32;                 // pixels per K block (64 real K = 128 bytes)
 constexpr int kAdjMaxStages = 6;
 constexpr int kAdjRows = 128;                 // M: x rows
@@ -35,6 +38,7 @@ constexpr int kAdjMaxSplits = 8;             // bounds the partial-field memory 
 
 struct AdjParams {
     const float4 *tab;          // per pixel: (qxh, qxl, qyh, qyl), (qzh, qzl, e^{+i qx dv}), (e^{+i qy dv}, e^{+i qz dv})
+    const uint8_t *rtile;       // per 32-pixel chunk: the y-phase operand tile (2 Nyp rows x 128 bytes)
     int stages;
     const float2 *A;            // forward field (FP32)
     const float *w;             // dL/dI
@@ -83,6 +87,40 @@ cudaError_t launch_adj_pixel_table(const double *q, long long n, double voxel, f
     return cudaGetLastError();
 }
 
+// The y-phase operand, per 32-pixel chunk, as the tile image the MMA reads:
+// row y holds (Re R, -Im R) and row Nyp + y holds (Im R, Re R) for each pixel,
+// R = e^{+i q_y y} (zero past the last pixel).
+__global__ void adj_rtile_kernel(const float4 *__restrict__ tab, long long n_pix, int Nyp, int ny, double voxel,
+                                 uint8_t *__restrict__ rt, long long total) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int i = (int)(idx % kAdjChunk);
+    const int y = (int)((idx / kAdjChunk) % Nyp);
+    const long long cg = idx / ((long long)kAdjChunk * Nyp);
+    const long long p = cg * kAdjChunk + i;
+    float2 R = make_float2(0.f, 0.f);
+    if (p < n_pix) {
+        const float4 ta = tab[3 * p];
+        const float yv = ((float)y - 0.5f * (float)(ny - 1)) * (float)voxel;
+        R = expmi_fs(ta.z, ta.w, -yv);           // e^{+i q_y y}
+    }
+    uint8_t *tile = rt + cg * (long long)(2 * Nyp * 128);
+    *reinterpret_cast<uint32_t *>(tile + pair_offset(y, i)) = pack_half2(R.x, -R.y);
+    *reinterpret_cast<uint32_t *>(tile + pair_offset(Nyp + y, i)) = pack_half2(R.y, R.x);
+}
+
+size_t adj_rtile_bytes(long long n_pix, int ny) {
+    const int Nyp = ((ny + 7) / 8 * 8 + 15) / 16 * 16;
+    return (size_t)((n_pix + kAdjChunk - 1) / kAdjChunk) * 2 * Nyp * 128;
+}
+
+cudaError_t launch_adj_rtile(const float4 *tab, long long n_pix, int ny, double voxel, uint8_t *rt, cudaStream_t st) {
+    const int Nyp = ((ny + 7) / 8 * 8 + 15) / 16 * 16;
+    const long long total = (n_pix + kAdjChunk - 1) / kAdjChunk * kAdjChunk * Nyp;
+    adj_rtile_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(tab, n_pix, Nyp, ny, voxel, rt, total);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -91,9 +129,10 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
     const uint32_t stage_bytes = 2 * kAdjTileA + b_bytes;
     const int NS = P.stages;
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + NS * stage_bytes);
-    uint64_t *full = bars;
-    uint64_t *empty = bars + kAdjMaxStages;
-    uint64_t *done = bars + 2 * kAdjMaxStages;
+    uint64_t *full = bars;                          // x-phase operand written (generator warps)
+    uint64_t *bfull = bars + kAdjMaxStages;         // y-phase operand copied (bytes)
+    uint64_t *empty = bars + 2 * kAdjMaxStages;
+    uint64_t *done = bars + 3 * kAdjMaxStages;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -106,6 +145,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&full[s]), kAdjGenWarps);
+            mbar_init(smem_u32(&bfull[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
         mbar_init(smem_u32(done), 1);
@@ -128,6 +168,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         for (int c = 0; c < n_chunks; ++c) {
             const uint32_t s = c % NS, ph = (c / NS) & 1;
             if (!warp_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) break;
+            if (!warp_wait(smem_u32(&bfull[s]), ph, abort_flag, P.err, kErrTimeoutMma)) break;
             tc_fence_after();
             // descriptors advance by encoded (>> 4) byte offsets
             const uint64_t a0 = desc0 + (uint64_t)((s * stage_bytes) >> 4);
@@ -145,20 +186,38 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         }
         if (elect_one()) mma_commit(smem_u32(done));
         __syncwarp();
+    } else if (warp == kAdjLoadWarp) {
+        // ---------------- y-phase operand: one bulk copy per chunk ----------------
+        const uint8_t *src = P.rtile + (size_t)(p_begin / kAdjChunk) * b_bytes;
+        int issued = 0;
+        for (int c = 0; c < n_chunks; ++c) {
+            const uint32_t s = c % NS, ph = (c / NS) & 1;
+            if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutProducer)) break;
+            if (elect_one()) {
+                const uint32_t fb = smem_u32(&bfull[s]);
+                mbar_arrive_expect_tx(fb, b_bytes);
+                bulk_load(smem_u32(base + s * stage_bytes + 2 * kAdjTileA), src + (size_t)c * b_bytes, b_bytes, fb);
+            }
+            __syncwarp();
+            ++issued;
+        }
+        // copies still in flight land before the CTA exits
+        if (*abort_flag && lane == 0) {
+            volatile int dummy = 0;
+            for (int c = issued > NS ? issued - NS : 0; c < issued; ++c)
+                mbar_wait(smem_u32(&bfull[c % NS]), (c / NS) & 1, &dummy, P.err, kErrTimeoutDrain);
+        }
+        __syncwarp();
     } else {
-        // ---------------- generator warps ----------------
+        // ---------------- generator warps: the x-phase operand ----------------
         const float inv_g = 1.0f / fmaxf(__uint_as_float(*P.gmax_bits), 1e-30f);
         const int i = lane;                      // pixel within the chunk
-        // warp roles: runs 0 .. na-1 of the L tiles (x rows, both slices), then
-        // runs of the R tile; a warp without a run only signals the stage
-        const int na = (P.nx + 15) / 16, nb = P.Nyp / 16;
-        const bool is_a = warp < na, is_b = !is_a && warp - na < nb;
-        const int run = is_a ? warp : warp - na;  // rows 16*run .. 16*run + 15
+        // rows r0 .. r1 - 1 of both slices' L tiles (x < nx only)
+        const int ra = (P.nx + kAdjGenWarps - 1) / kAdjGenWarps;
+        const int r0 = warp * ra, r1 = min(P.nx, r0 + ra);
         const float vox = (float)P.voxel;
-        const float x0 = (16 * run - 0.5f * (P.nx - 1)) * vox;
-        const float y0 = (16 * run - 0.5f * (P.ny - 1)) * vox;
+        const float x0 = ((float)r0 - 0.5f * (float)(P.nx - 1)) * vox;
         const float zj = ((float)j0 - 0.5f * (P.nz - 1)) * vox;
-        const int rows_a = min(16, P.nx - 16 * run);
         // this lane's pixel data, loaded one chunk ahead so the L2 latency
         // overlaps the previous chunk's generation
         float2 a_n = make_float2(0.f, 0.f);
@@ -166,14 +225,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         float4 ta_n = make_float4(0.f, 0.f, 0.f, 0.f), tb_n = ta_n, tc_n = ta_n;
         auto load_pixel = [&](int c) {
             const long long p = p_begin + (long long)c * kAdjChunk + i;
-            if (c < n_chunks && p < p_end && (is_a || is_b)) {
+            if (c < n_chunks && p < p_end && r0 < r1) {
+                a_n = P.A[p];
+                w_n = P.w[p];
                 ta_n = P.tab[3 * p];
+                tb_n = P.tab[3 * p + 1];
                 tc_n = P.tab[3 * p + 2];
-                if (is_a) {
-                    a_n = P.A[p];
-                    w_n = P.w[p];
-                    tb_n = P.tab[3 * p + 1];
-                }
             } else {
                 a_n = make_float2(0.f, 0.f);
                 w_n = 0.f;
@@ -190,10 +247,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
             if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutEpilogue)) break;
             uint8_t *sA0 = base + s * stage_bytes;
             uint8_t *sA1 = sA0 + kAdjTileA;
-            uint8_t *sB = sA0 + 2 * kAdjTileA;
-            const long long p = p_begin + (long long)c * kAdjChunk + i;
-            const bool in = p < p_end;
-            if (is_a) {
+            if (r0 < r1) {
                 const float wp = w_c * inv_g;
                 const float2 g = make_float2(a_c.x * wp, a_c.y * wp);
                 // e^{+i t} = conj(e^{-i t}) = expmi(q, -c)
@@ -201,26 +255,14 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
                 const float2 ezs = make_float2(tcv.z, tcv.w);
                 const float2 ex = expmi_fs(ta.x, ta.y, -x0);
                 const float2 exs = make_float2(tb.z, tb.w);
-                float2 L0 = cmul(cmul(g, ez), ex);       // slice j0, row 16*run
+                float2 L0 = cmul(cmul(g, ez), ex);       // slice j0, row r0
 #pragma unroll 4
-                for (int k = 0; k < rows_a; ++k) {
-                    const int r = 16 * run + k;
+                for (int r = r0; r < r1; ++r) {
                     const float2 L1 = cmul(L0, ezs);
                     const uint32_t off = pair_offset(r, i);
                     *reinterpret_cast<uint32_t *>(sA0 + off) = pack_half2(L0.x, L0.y);
                     *reinterpret_cast<uint32_t *>(sA1 + off) = pack_half2(L1.x, L1.y);
                     L0 = cmul(L0, exs);
-                }
-            } else if (is_b) {
-                // rows of the B tile: (y, re) and (y, im)
-                const float2 eys = make_float2(tcv.x, tcv.y);
-                float2 R = in ? expmi_fs(ta.z, ta.w, -y0) : make_float2(0.f, 0.f);
-#pragma unroll 4
-                for (int k = 0; k < 16; ++k) {
-                    const int y = 16 * run + k;
-                    *reinterpret_cast<uint32_t *>(sB + pair_offset(y, i)) = pack_half2(R.x, -R.y);
-                    *reinterpret_cast<uint32_t *>(sB + pair_offset(P.Nyp + y, i)) = pack_half2(R.y, R.x);
-                    R = cmul(R, eys);
                 }
             }
             fence_async_smem();
@@ -303,7 +345,7 @@ __global__ void adj_sum_kernel(const float2 *__restrict__ partial, int splits, l
 }
 
 static size_t adj_stage_bytes(int Nyp) { return 2 * (size_t)kAdjTileA + (size_t)2 * Nyp * 128; }
-static size_t adj_fixed_bytes() { return 1024 + 256; }
+static size_t adj_fixed_bytes() { return 1024 + 256; }   // alignment, barriers
 // Stages that fit beside the barriers (at most kAdjMaxStages).
 static int adj_stages(int Nyp) {
     const size_t n = (232448 - adj_fixed_bytes()) / adj_stage_bytes(Nyp);
@@ -340,11 +382,12 @@ int adjoint_tc_splits(long long n_pix, int nz, int sm_count) {
     return best;
 }
 
-cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab, long long n_pix, int nx, int ny,
-                              int nz, double voxel, int splits, float2 *partial, unsigned *gmax_bits, float2 *S,
-                              int *err, cudaStream_t st) {
+cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab, const uint8_t *rtile, long long n_pix,
+                              int nx, int ny, int nz, double voxel, int splits, float2 *partial, unsigned *gmax_bits,
+                              float2 *S, int *err, cudaStream_t st) {
     AdjParams P;
     P.tab = tab;
+    P.rtile = rtile;
     P.A = A;
     P.w = w;
     P.gmax_bits = gmax_bits;

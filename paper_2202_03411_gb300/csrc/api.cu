@@ -143,6 +143,7 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_adj_part);
     cudaFree(h->d_gmax);
     cudaFree(h->d_adj_tab);
+    cudaFree(h->d_adj_rtile);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (dev_prev >= 0) cudaSetDevice(dev_prev);
     delete h;
@@ -528,7 +529,14 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
                                  "adjoint pixel table")))
                 return rc;
         }
-        rc = check_cuda(h, launch_adjoint_tc((const float2 *)h->d_A, (const float *)dLdI_dev, h->d_adj_tab, h->n_pix, c.nx,
+        if (!h->d_adj_rtile) {
+            if ((rc = alloc_dev(h, (void **)&h->d_adj_rtile, adj_rtile_bytes(h->n_pix, c.ny), "adjoint y-phase tiles")))
+                return rc;
+            if ((rc = check_cuda(h, launch_adj_rtile(h->d_adj_tab, h->n_pix, c.ny, c.voxel, h->d_adj_rtile, h->stream),
+                                 "adjoint y-phase tiles")))
+                return rc;
+        }
+        rc = check_cuda(h, launch_adjoint_tc((const float2 *)h->d_A, (const float *)dLdI_dev, h->d_adj_tab, h->d_adj_rtile, h->n_pix, c.nx,
                                              c.ny, c.nz, c.voxel, splits, h->d_adj_part, h->d_gmax, (float2 *)h->d_S,
                                              h->d_err, h->stream),
                         "adjoint field (tensor cores)");

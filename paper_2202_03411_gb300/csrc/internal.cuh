@@ -133,6 +133,7 @@ struct scatman_handle {
     size_t adj_part_count = 0;
     unsigned *d_gmax = nullptr;     // tensor-core adjoint: max |w A| (float bits)
     float4 *d_adj_tab = nullptr;    // tensor-core adjoint: per-pixel constants (built at the first backward)
+    uint8_t *d_adj_rtile = nullptr; // tensor-core adjoint: y-phase operand tiles (built at the first backward)
     int splits = 1;
     long long device_bytes = 0;
     scm::TcMaps tmap_B;
@@ -191,9 +192,12 @@ int grad_pixel_blocks(long long n_pix);
 // Tensor-core adjoint field (adjoint_tc.cu).
 bool adjoint_tc_supported(int nx, int ny);
 int adjoint_tc_splits(long long n_pix, int nz, int sm_count);
-cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab, long long n_pix, int nx, int ny,
-                              int nz, double voxel, int splits, float2 *partial, unsigned *gmax_bits, float2 *S,
-                              int *err, cudaStream_t st);
+cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab, const uint8_t *rtile, long long n_pix,
+                              int nx, int ny, int nz, double voxel, int splits, float2 *partial, unsigned *gmax_bits,
+                              float2 *S, int *err, cudaStream_t st);
+// The adjoint's y-phase operand tiles (once per handle).
+size_t adj_rtile_bytes(long long n_pix, int ny);
+cudaError_t launch_adj_rtile(const float4 *tab, long long n_pix, int ny, double voxel, uint8_t *rt, cudaStream_t st);
 // Per-pixel constants of the tensor-core adjoint (3 float4 per pixel), once per handle.
 cudaError_t launch_adj_pixel_table(const double *q, long long n, double voxel, float4 *tab, cudaStream_t st);
 // Fit residual 2 (I - target) and partial sums of (I - target)^2 (adjoint.cu).

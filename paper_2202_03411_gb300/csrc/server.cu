@@ -318,7 +318,12 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     b += round_2mib(npix * (f64 ? 8 : 4));      // intensity scratch
     if (!tc) b += round_2mib(64 * npix * cx);   // partial fields (upper bound on splits)
     b += round_2mib(nvox * cx);                 // adjoint field (backward)
-    if (tc) b += round_2mib(8 * nvox * 8) + round_2mib(4) + round_2mib(48 * npix);   // adjoint partial fields (<= 8), scale, pixel table
+    if (tc) {
+        // adjoint partial fields (<= 8), scale, pixel table, y-phase operand tiles
+        const long long Nyp16 = ((c->ny + 7) / 8 * 8 + 15) / 16 * 16;
+        b += round_2mib(8 * nvox * 8) + round_2mib(4) + round_2mib(48 * npix) +
+             round_2mib((npix + 31) / 32 * 2 * Nyp16 * 128);
+    }
     b += round_2mib((608LL * ((SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1) + 2) + 256) * 8);
     return b;
 }
