@@ -15,7 +15,7 @@ from typing import Optional
 
 import numpy as np
 
-from workloads import Geometry, Shape
+from workloads import ELLIPSOID, SPHERE, SPHHARM, Geometry, Shape
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "msft_oracle.c")
@@ -45,6 +45,10 @@ class _OrcShape(ctypes.Structure):
         ("delta", ctypes.c_double), ("beta", ctypes.c_double),
         ("latitude", ctypes.c_double), ("longitude", ctypes.c_double), ("rotation", ctypes.c_double),
         ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("cz", ctypes.c_double),
+        ("radial_map", ctypes.POINTER(ctypes.c_double)), ("map_ntheta", ctypes.c_int), ("map_nphi", ctypes.c_int),
+        ("volume_map", ctypes.POINTER(ctypes.c_ubyte)), ("map_nx", ctypes.c_int), ("map_ny", ctypes.c_int),
+        ("map_nz", ctypes.c_int), ("map_dx", ctypes.c_double),
+        ("map_delta", ctypes.POINTER(ctypes.c_double)), ("map_beta", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -68,6 +72,10 @@ def _load():
         lib.orc_detector_q.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D]
         lib.orc_detector_q_uniform.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D,
                                                ctypes.POINTER(ctypes.c_int)]
+        lib.orc_voxel_index.argtypes = [ctypes.POINTER(_OrcShape), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_double, _D, _D]
+        lib.orc_slices_n.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_double, _D, _D]
         lib.orc_msft.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                  _D, ctypes.c_long, _D, _D]
         lib.orc_intensity.argtypes = [_D, _D, ctypes.c_long, _D]
@@ -94,7 +102,25 @@ def _shape_struct(s: Shape):
     alm = s.alm_array()
     st = _OrcShape(s.kind, s.r, s.a, s.b, s.c, s.R0, s.lmax, _p(alm), s.delta, s.beta,
                    s.latitude, s.longitude, s.rotation, s.cx, s.cy, s.cz)
-    return st, alm  # keep alm alive
+    keep = [alm]
+    if getattr(s, "radial_map", None) is not None:
+        rm = np.ascontiguousarray(s.radial_map, dtype=np.float64)
+        st.radial_map = _p(rm)
+        st.map_ntheta, st.map_nphi = rm.shape
+        keep.append(rm)
+    if getattr(s, "volume_map", None) is not None:
+        vm = np.ascontiguousarray(s.volume_map, dtype=np.uint8)
+        st.volume_map = vm.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        st.map_nx, st.map_ny, st.map_nz = vm.shape
+        st.map_dx = s.map_dx
+        keep.append(vm)
+        for name in ("map_delta", "map_beta"):
+            arr = getattr(s, name, None)
+            if arr is not None:
+                arr = np.ascontiguousarray(arr, dtype=np.float64)
+                setattr(st, name, _p(arr))
+                keep.append(arr)
+    return st, keep  # keep the arrays alive
 
 
 def num_threads() -> int:
@@ -133,6 +159,26 @@ def slices(chi: np.ndarray, g: Geometry, delta: float, beta: float) -> np.ndarra
     re = np.zeros_like(chi)
     im = np.zeros_like(chi)
     _load().orc_slices(_p(chi), g.nx, g.ny, g.nz, g.voxel, g.wavelength, delta, beta, _p(re), _p(im))
+    return re + 1j * im
+
+
+def voxel_index(shape: Shape, g: Geometry):
+    """Per-voxel (delta, beta) [z][x][y] of a volume map with a per-cell index."""
+    d = np.zeros((g.nz, g.nx, g.ny))
+    b = np.zeros((g.nz, g.nx, g.ny))
+    st, keep = _shape_struct(shape)
+    _load().orc_voxel_index(ctypes.byref(st), g.nx, g.ny, g.nz, g.voxel, _p(d), _p(b))
+    return d, b
+
+
+def slices_n(chi: np.ndarray, g: Geometry, delta_v: np.ndarray, beta_v: np.ndarray) -> np.ndarray:
+    """Slice strength with a voxel-resolved index: (n_v^2-1) chi T, T from Eq. 8 with n_v."""
+    chi = np.ascontiguousarray(chi, dtype=np.float64)
+    dv = np.ascontiguousarray(delta_v, dtype=np.float64)
+    bv = np.ascontiguousarray(beta_v, dtype=np.float64)
+    re = np.zeros_like(chi)
+    im = np.zeros_like(chi)
+    _load().orc_slices_n(_p(chi), _p(dv), _p(bv), g.nx, g.ny, g.nz, g.voxel, g.wavelength, _p(re), _p(im))
     return re + 1j * im
 
 
@@ -190,7 +236,10 @@ def forward(shape: Shape, g: Geometry, q: Optional[np.ndarray] = None, soft: boo
     if q is None:
         q = detector_q(g)
     chi, _ = voxelise(shape, g, soft, width)
-    rho = slices(chi, g, shape.delta, shape.beta)
+    if shape.varying_index():
+        rho = slices_n(chi, g, *voxel_index(shape, g))
+    else:
+        rho = slices(chi, g, shape.delta, shape.beta)
     A = msft(rho, q, g.voxel)
     if getattr(g, "detector", 0) == 1 and len(A) == g.n_pix:
         A = np.where(detector_valid(g), A, 0.0)       # no scattering direction: no field
@@ -200,6 +249,8 @@ def forward(shape: Shape, g: Geometry, q: Optional[np.ndarray] = None, soft: boo
 def gradient(shape: Shape, g: Geometry, dLdI: np.ndarray, A: np.ndarray,
              q: Optional[np.ndarray] = None, width: float = 0.5) -> np.ndarray:
     """dL/d(params) for soft occupancy, given dL/dI and the forward field A."""
+    if shape.kind not in (SPHERE, ELLIPSOID, SPHHARM):
+        raise ValueError("the oracle gradient covers sphere, ellipsoid and harmonics shapes")
     if q is None:
         q = detector_q(g)
     st, keep = _shape_struct(shape)

@@ -8,6 +8,9 @@ that agreement between the two pins the C oracle:
 * rotation from an axis-angle (Rodrigues) composition instead of elementary
   matrix products;
 * real spherical harmonics from ``scipy.special.sph_harm_y``;
+* radii maps interpolated with ``scipy.ndimage.map_coordinates`` (linear,
+  periodic grid) instead of an explicit four-point blend; volume-map cells
+  looked up from an integer index grid;
 * transmission as exp(i k0 dz (n-1) * exclusive cumulative sum) instead of the
   running product of Eq. 8;
 * the field as one dense exp(-i q.r) matrix product over all voxels (the 3D
@@ -18,9 +21,10 @@ from __future__ import annotations
 import math
 
 import numpy as np
+from scipy.ndimage import map_coordinates
 from scipy.special import sph_harm_y
 
-from workloads import ELLIPSOID, SPHERE, SPHHARM, Geometry, Shape
+from workloads import ELLIPSOID, RADIALMAP, SPHERE, SPHHARM, VOLUMEMAP, Geometry, Shape
 
 
 def q_pixels(g: Geometry) -> np.ndarray:
@@ -83,6 +87,17 @@ def occupancy(s: Shape, g: Geometry, soft=False, width=0.5):
     elif s.kind == ELLIPSOID:
         rs = 1.0 / np.sqrt((u[..., 0] / s.a) ** 2 + (u[..., 1] / s.b) ** 2 + (u[..., 2] / s.c) ** 2)
         inside = (p[..., 0] / s.a) ** 2 + (p[..., 1] / s.b) ** 2 + (p[..., 2] / s.c) ** 2 <= 1.0
+    elif s.kind == RADIALMAP:
+        rm = np.asarray(s.radial_map, dtype=float)
+        nt, npf = rm.shape
+        lat = np.arcsin(np.clip(u[..., 2], -1, 1))
+        lon = np.mod(np.arctan2(p[..., 1], p[..., 0]), 2 * math.pi)
+        coords = np.stack([((lat + math.pi / 2) / math.pi * nt).ravel(), (lon / (2 * math.pi) * npf).ravel()])
+        rs = map_coordinates(rm, coords, order=1, mode="grid-wrap").reshape(rr.shape)
+        inside = rr <= rs
+    elif s.kind == VOLUMEMAP:
+        inside = _vmap_lookup(s, p, np.asarray(s.volume_map, dtype=bool), False)
+        return inside.astype(float)
     else:
         theta = np.arccos(np.clip(u[..., 2], -1, 1))
         phi = np.arctan2(p[..., 1], p[..., 0])
@@ -97,6 +112,39 @@ def occupancy(s: Shape, g: Geometry, soft=False, width=0.5):
     if soft:
         return 1.0 / (1.0 + np.exp(-(rs - rr) / width))
     return inside.astype(float)
+
+
+def _vmap_lookup(s: Shape, p, values, outside):
+    """values of the volume-map cell holding each body point p (outside: `outside`)."""
+    m = np.array(values.shape)
+    cell = np.floor(p / s.map_dx + m / 2.0).astype(np.int64)
+    ok = ((cell >= 0) & (cell < m)).all(axis=-1)
+    cc = np.where(ok[..., None], cell, 0)
+    return np.where(ok, values[cc[..., 0], cc[..., 1], cc[..., 2]], outside)
+
+
+def body_points(s: Shape, g: Geometry):
+    X, Y, Z = voxel_centres(g)
+    d = np.stack([X - s.cx, Y - s.cy, Z - s.cz], axis=-1)
+    return d @ rotation(s.latitude, s.longitude, s.rotation)
+
+
+def voxel_index(s: Shape, g: Geometry):
+    """Per-voxel delta, beta of a volume map with a per-cell index [z][x][y]."""
+    p = body_points(s, g)
+    dm = s.map_delta if s.map_delta is not None else np.full(s.volume_map.shape, s.delta)
+    bm = s.map_beta if s.map_beta is not None else np.full(s.volume_map.shape, s.beta)
+    return _vmap_lookup(s, p, np.asarray(dm, float), s.delta), _vmap_lookup(s, p, np.asarray(bm, float), s.beta)
+
+
+def slices_n(chi, g: Geometry, delta_v, beta_v):
+    """Slice strength with one index per voxel: exp of the exclusive cumulative
+    sum of chi (n_v - 1) along z, times (n_v^2 - 1) chi."""
+    k0 = 2 * math.pi / g.wavelength
+    n = 1 - delta_v + 1j * beta_v
+    e = chi * (n - 1)
+    E = np.cumsum(e, axis=0) - e
+    return (n * n - 1) * chi * np.exp(1j * k0 * g.voxel * E)
 
 
 def slices(chi, g: Geometry, delta, beta):
@@ -116,6 +164,10 @@ def field(rho, q, g: Geometry):
 def forward(s: Shape, g: Geometry, q=None, soft=False, width=0.5):
     if q is None:
         q = q_pixels(g)
-    rho = slices(occupancy(s, g, soft, width), g, s.delta, s.beta)
+    chi = occupancy(s, g, soft, width)
+    if s.varying_index():
+        rho = slices_n(chi, g, *voxel_index(s, g))
+    else:
+        rho = slices(chi, g, s.delta, s.beta)
     A = field(rho, q, g)
     return np.abs(A) ** 2, A

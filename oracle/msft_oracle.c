@@ -43,6 +43,8 @@
 #define ORC_SPHERE 0
 #define ORC_ELLIPSOID 1
 #define ORC_SPHHARM 2
+#define ORC_RADIALMAP 3
+#define ORC_VOLUMEMAP 4
 
 /* Shape parameters as in the paper's Listings 1-2 (Sec. 5). */
 typedef struct {
@@ -54,6 +56,14 @@ typedef struct {
     double delta, beta;         /* n = 1 - delta + i beta (Eq. 7) */
     double latitude, longitude, rotation;   /* degrees (Fig. 6) */
     double cx, cy, cz;          /* centre offset from the grid centre */
+    /* radii map (Sec. 5.2 "Shape (2/3)"): [n_theta][n_phi], length units */
+    const double *radial_map;
+    int map_ntheta, map_nphi;
+    /* volume map (Sec. 5.2 "Shape (3/3)"): [mx][my][mz], non-zero = inside, cell edge map_dx */
+    const unsigned char *volume_map;
+    int map_nx, map_ny, map_nz;
+    double map_dx;
+    const double *map_delta, *map_beta;   /* optional per-cell index (NULL: the shape's) */
 } orc_shape;
 
 static const double ORC_PI = 3.14159265358979323846;
@@ -185,6 +195,54 @@ static double orc_sh_radius(const orc_shape *sh, double theta, double phi,
 
 static double orc_sigmoid(double t) { return 1.0 / (1.0 + exp(-t)); }
 
+/*
+ * Sec. 5.2 "Shape (2/3)": radius of a radii map along the body direction of p
+ * (|p| = rr).  The map holds radii at latitudes lat_i = -pi/2 + i pi/Nt and
+ * longitudes lon_k = 2 pi k/Np (an N x M map covers latitudes -pi/2 .. pi/2 -
+ * pi/Nt, as the paper's 4x4 example), linearly interpolated in each angle.
+ * Reading: the interpolation is periodic in both angles (after the last
+ * latitude row comes row 0, after the last longitude column comes column 0);
+ * latitude = asin(p_z/|p|) (+pi/2 on the body z axis), longitude =
+ * atan2(p_y, p_x) in [0, 2 pi).
+ */
+static double orc_rmap_radius(const orc_shape *sh, const double p[3], double rr)
+{
+    int nt = sh->map_ntheta, np = sh->map_nphi;
+    double sz = rr > 0.0 ? p[2] / rr : 0.0;
+    if (sz > 1.0) sz = 1.0;
+    if (sz < -1.0) sz = -1.0;
+    double lat = asin(sz);
+    double lon = atan2(p[1], p[0]);
+    if (lon < 0.0) lon += 2.0 * ORC_PI;
+    double ti = (lat + 0.5 * ORC_PI) * ((double)nt / ORC_PI);
+    double tk = lon * ((double)np / (2.0 * ORC_PI));
+    double fi = floor(ti), fk = floor(tk);
+    double f = ti - fi, g = tk - fk;
+    int i0 = (int)fi % nt, k0 = (int)fk % np;
+    if (i0 < 0) i0 += nt;
+    if (k0 < 0) k0 += np;
+    int i1 = (i0 + 1) % nt, k1 = (k0 + 1) % np;
+    const double *R = sh->radial_map;
+    double r00 = R[(size_t)i0 * np + k0], r01 = R[(size_t)i0 * np + k1];
+    double r10 = R[(size_t)i1 * np + k0], r11 = R[(size_t)i1 * np + k1];
+    return (1.0 - f) * (1.0 - g) * r00 + (1.0 - f) * g * r01 + f * (1.0 - g) * r10 + f * g * r11;
+}
+
+/*
+ * Sec. 5.2 "Shape (3/3)": cell of a volume map that contains the body point p.
+ * Cell (i, j, k) covers [(i - Mx/2) dx, (i + 1 - Mx/2) dx) along body x and
+ * likewise along y and z (the map is centred on the shape centre and turns
+ * with the body).  Returns -1 outside the map.
+ */
+static long orc_vmap_cell(const orc_shape *sh, const double p[3])
+{
+    double ci = floor(p[0] / sh->map_dx + 0.5 * sh->map_nx);
+    double cj = floor(p[1] / sh->map_dx + 0.5 * sh->map_ny);
+    double ck = floor(p[2] / sh->map_dx + 0.5 * sh->map_nz);
+    if (ci < 0.0 || cj < 0.0 || ck < 0.0 || ci >= sh->map_nx || cj >= sh->map_ny || ck >= sh->map_nz) return -1;
+    return ((long)ci * sh->map_ny + (long)cj) * sh->map_nz + (long)ck;
+}
+
 /* Body-frame coordinates of voxel centre (ix,iy,iz). */
 static void orc_body_coords(const orc_shape *sh, const double R[9], int ix, int iy, int iz,
                             int nx, int ny, int nz, double voxel, double p[3])
@@ -228,6 +286,11 @@ int orc_voxelise(const orc_shape *sh, int nx, int ny, int nz, double voxel,
                         double qf = (p[0] / sh->a) * (p[0] / sh->a) + (p[1] / sh->b) * (p[1] / sh->b)
                                     + (p[2] / sh->c) * (p[2] / sh->c);
                         v = (qf <= 1.0) ? 1.0 : 0.0;
+                    } else if (sh->kind == ORC_RADIALMAP) {
+                        v = (rr <= orc_rmap_radius(sh, p, rr)) ? 1.0 : 0.0;
+                    } else if (sh->kind == ORC_VOLUMEMAP) {
+                        long cell = orc_vmap_cell(sh, p);
+                        v = (cell >= 0 && sh->volume_map[cell] != 0) ? 1.0 : 0.0;
                     } else {
                         double th = rr > 0.0 ? acos(p[2] / rr) : 0.0;
                         double ph = atan2(p[1], p[0]);
@@ -236,6 +299,10 @@ int orc_voxelise(const orc_shape *sh, int nx, int ny, int nz, double voxel,
                         any_clip |= cl;
                         v = (rr <= rs) ? 1.0 : 0.0;
                     }
+                } else if (sh->kind == ORC_VOLUMEMAP) {
+                    /* a volume map has no surface radius: its occupancy stays binary */
+                    long cell = orc_vmap_cell(sh, p);
+                    v = (cell >= 0 && sh->volume_map[cell] != 0) ? 1.0 : 0.0;
                 } else {
                     double rs;
                     if (sh->kind == ORC_SPHERE) {
@@ -245,6 +312,8 @@ int orc_voxelise(const orc_shape *sh, int nx, int ny, int nz, double voxel,
                         if (rr > 0.0) { u0 = p[0] / rr; u1 = p[1] / rr; u2 = p[2] / rr; }
                         rs = 1.0 / sqrt((u0 / sh->a) * (u0 / sh->a) + (u1 / sh->b) * (u1 / sh->b)
                                         + (u2 / sh->c) * (u2 / sh->c));
+                    } else if (sh->kind == ORC_RADIALMAP) {
+                        rs = orc_rmap_radius(sh, p, rr);
                     } else {
                         double th = rr > 0.0 ? acos(p[2] / rr) : 0.0;
                         double ph = atan2(p[1], p[0]);
@@ -285,6 +354,55 @@ void orc_slices(const double *chi, int nx, int ny, int nz, double dz, double wav
                 rho_re[idx] = creal(rho);
                 rho_im[idx] = cimag(rho);
                 /* Block 9: propagate through slice iz for the next slice */
+                T = T * cexp(I * k0 * dz * chi[idx] * (n - 1.0));
+            }
+        }
+}
+
+/*
+ * Refractive index of every voxel for a volume map with per-cell delta and
+ * beta (the paper's "arbitrary voxel representation of the refractive index",
+ * Sec. 5.2): the cell's values for voxels inside the map, the shape's
+ * elsewhere (where chi = 0 anyway).  [z][x][y].
+ */
+void orc_voxel_index(const orc_shape *sh, int nx, int ny, int nz, double voxel, double *delta_v,
+                     double *beta_v)
+{
+    double R[9];
+    orc_rotation(sh->latitude, sh->longitude, sh->rotation, R);
+#pragma omp parallel for collapse(2)
+    for (int iz = 0; iz < nz; ++iz)
+        for (int ix = 0; ix < nx; ++ix)
+            for (int iy = 0; iy < ny; ++iy) {
+                double p[3];
+                orc_body_coords(sh, R, ix, iy, iz, nx, ny, nz, voxel, p);
+                long cell = orc_vmap_cell(sh, p);
+                size_t idx = ((size_t)iz * nx + ix) * ny + iy;
+                delta_v[idx] = (cell >= 0 && sh->map_delta) ? sh->map_delta[cell] : sh->delta;
+                beta_v[idx] = (cell >= 0 && sh->map_beta) ? sh->map_beta[cell] : sh->beta;
+            }
+}
+
+/*
+ * Eq. 5-9 with a voxel-resolved index: as orc_slices, but every voxel carries
+ * its own n_v = 1 - delta_v + i beta_v, both in the slice strength
+ * (n_v^2 - 1) chi and in the propagation of Eq. 8,
+ *   T_j = prod_{j'<j} e^{i k0 dz chi_{j'} (n_{j'} - 1)}.
+ */
+void orc_slices_n(const double *chi, const double *delta_v, const double *beta_v, int nx, int ny, int nz,
+                  double dz, double wavelength, double *rho_re, double *rho_im)
+{
+    double k0 = 2.0 * ORC_PI / wavelength;
+#pragma omp parallel for collapse(2)
+    for (int ix = 0; ix < nx; ++ix)
+        for (int iy = 0; iy < ny; ++iy) {
+            double complex T = 1.0;
+            for (int iz = 0; iz < nz; ++iz) {
+                size_t idx = ((size_t)iz * nx + ix) * ny + iy;
+                double complex n = 1.0 - delta_v[idx] + I * beta_v[idx];
+                double complex rho = (n * n - 1.0) * chi[idx] * T;
+                rho_re[idx] = creal(rho);
+                rho_im[idx] = cimag(rho);
                 T = T * cexp(I * k0 * dz * chi[idx] * (n - 1.0));
             }
         }

@@ -57,6 +57,9 @@ class scatman_shape(ctypes.Structure):
         ("delta", ctypes.c_double), ("beta", ctypes.c_double),
         ("latitude", ctypes.c_double), ("longitude", ctypes.c_double), ("rotation", ctypes.c_double),
         ("cx", ctypes.c_double), ("cy", ctypes.c_double), ("cz", ctypes.c_double),
+        ("radial_map", _D), ("map_ntheta", ctypes.c_int), ("map_nphi", ctypes.c_int),
+        ("volume_map", ctypes.POINTER(ctypes.c_ubyte)), ("map_nx", ctypes.c_int), ("map_ny", ctypes.c_int),
+        ("map_nz", ctypes.c_int), ("map_dx", ctypes.c_double), ("map_delta", _D), ("map_beta", _D),
     ]
 
 

@@ -90,7 +90,28 @@ def make_shape(shape):
     st.delta, st.beta = shape.delta, shape.beta
     st.latitude, st.longitude, st.rotation = shape.latitude, shape.longitude, shape.rotation
     st.cx, st.cy, st.cz = shape.cx, shape.cy, shape.cz
-    return st, alm
+    keep = [alm]
+    rm = getattr(shape, "radial_map", None)
+    if rm is not None:
+        rm = np.ascontiguousarray(rm, dtype=np.float64)
+        st.radial_map = rm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st.map_ntheta, st.map_nphi = rm.shape
+        keep.append(rm)
+    vm = getattr(shape, "volume_map", None)
+    if vm is not None:
+        vm = np.ascontiguousarray(vm, dtype=np.uint8)
+        st.volume_map = vm.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
+        st.map_nx, st.map_ny, st.map_nz = vm.shape
+        st.map_dx = shape.map_dx
+        keep.append(vm)
+        for name in ("map_delta", "map_beta"):
+            arr = getattr(shape, name, None)
+            if arr is not None:
+                arr = np.ascontiguousarray(arr, dtype=np.float64)
+                assert arr.shape == vm.shape, name + " must match the volume map"
+                setattr(st, name, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                keep.append(arr)
+    return st, keep
 
 
 def scatman_create(geometry, precision, soft: bool = False, soft_width: float = 0.5, scan_fp64: bool = False,

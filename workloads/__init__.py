@@ -34,9 +34,10 @@ from typing import List, Optional
 
 import numpy as np
 
-SPHERE, ELLIPSOID, SPHHARM = 0, 1, 2
+SPHERE, ELLIPSOID, SPHHARM, RADIALMAP, VOLUMEMAP = 0, 1, 2, 3, 4
 DETECTOR_FLAT, DETECTOR_UNIFORM_Q = 0, 1
-KIND_NAMES = {SPHERE: "sphere", ELLIPSOID: "ellipsoid", SPHHARM: "sphharm"}
+KIND_NAMES = {SPHERE: "sphere", ELLIPSOID: "ellipsoid", SPHHARM: "sphharm", RADIALMAP: "radialmap",
+              VOLUMEMAP: "volumemap"}
 
 
 @dataclasses.dataclass
@@ -59,13 +60,27 @@ class Shape:
     cx: float = 0.0                     # centre offset from the grid centre (length units)
     cy: float = 0.0
     cz: float = 0.0
+    # radii map (Sec. 5.2 "Shape (2/3)"): [n_theta][n_phi] radii in length units at
+    # latitudes -pi/2 + i pi/n_theta and longitudes 2 pi k/n_phi
+    radial_map: Optional[np.ndarray] = None
+    # volume map (Sec. 5.2 "Shape (3/3)"): [mx][my][mz] booleans, cell edge map_dx,
+    # optional per-cell delta and beta (same shape) for a voxel-resolved index
+    volume_map: Optional[np.ndarray] = None
+    map_dx: float = 1.0
+    map_delta: Optional[np.ndarray] = None
+    map_beta: Optional[np.ndarray] = None
 
     def n_params(self) -> int:
         if self.kind == SPHERE:
             return 3
         if self.kind == ELLIPSOID:
             return 5
+        if self.kind in (RADIALMAP, VOLUMEMAP):
+            return 0                    # no gradient for map shapes
         return (self.lmax + 1) ** 2 - 1 + 3
+
+    def varying_index(self) -> bool:
+        return self.kind == VOLUMEMAP and (self.map_delta is not None or self.map_beta is not None)
 
     def alm_array(self) -> np.ndarray:
         if self.alm is None:
@@ -74,8 +89,10 @@ class Shape:
 
     def copy(self) -> "Shape":
         s = dataclasses.replace(self)
-        if self.alm is not None:
-            s.alm = np.array(self.alm, dtype=np.float64, copy=True)
+        for f in ("alm", "radial_map", "volume_map", "map_delta", "map_beta"):
+            v = getattr(self, f)
+            if v is not None:
+                setattr(s, f, np.array(v, copy=True))
         return s
 
 
@@ -257,3 +274,79 @@ def random_slices(rng: np.random.Generator, nz: int, nx: int, ny: int) -> np.nda
     mag = rng.uniform(0.0, 1.0, size=(nz, nx, ny))
     ph = rng.uniform(-math.pi, math.pi, size=(nz, nx, ny))
     return mag * np.cos(ph) + 1j * mag * np.sin(ph)
+
+
+# ---------------------------------------------------------------------------
+# Map shapes (Sec. 5.2, "Shape (2/3)" and "Shape (3/3)")
+# ---------------------------------------------------------------------------
+
+def random_radial_map(rng: np.random.Generator, n_theta: int, n_phi: int, R0: float, amp: float = 0.15,
+                      terms: int = 6) -> np.ndarray:
+    """A smooth random radii map: R0 times one plus a few random low-order
+    cosine/sine products in latitude and longitude (periodic in both)."""
+    lat = -math.pi / 2 + math.pi * np.arange(n_theta) / n_theta
+    lon = 2 * math.pi * np.arange(n_phi) / n_phi
+    L, P = np.meshgrid(lat, lon, indexing="ij")
+    f = np.zeros((n_theta, n_phi))
+    for _ in range(terms):
+        a, b = int(rng.integers(1, 4)), int(rng.integers(0, 4))
+        ph1, ph2 = rng.uniform(0, 2 * math.pi, size=2)
+        f += rng.normal(0.0, 1.0) * np.cos(2 * a * L + ph1) * np.cos(b * P + ph2)
+    f *= amp / max(1e-12, np.abs(f).max())
+    return R0 * (1.0 + f)
+
+
+def random_volume_map(rng: np.random.Generator, m: int, blobs: int = 6, fill: float = 0.35) -> np.ndarray:
+    """A random solid in an m^3 box: the union of a few random axis-aligned
+    boxes and a core block, as booleans [mx][my][mz]."""
+    v = np.zeros((m, m, m), dtype=bool)
+    c0, c1 = int(m * (0.5 - fill / 2)), int(m * (0.5 + fill / 2))
+    v[c0:c1, c0:c1, c0:c1] = True
+    for _ in range(blobs):
+        lo = rng.integers(0, m - 2, size=3)
+        size = rng.integers(2, max(3, m // 3), size=3)
+        hi = np.minimum(lo + size, m)
+        v[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]] = True
+    return v
+
+
+def core_shell_index(volume_map: np.ndarray, core_delta: float, core_beta: float, shell_delta: float,
+                     shell_beta: float, core_frac: float = 0.5):
+    """Per-cell delta and beta for a two-material sample: cells in the central
+    core_frac of the map's box take the core values, the rest the shell's."""
+    m = np.array(volume_map.shape)
+    idx = np.indices(volume_map.shape).reshape(3, -1).T
+    centre = (m - 1) / 2.0
+    core = (np.abs(idx - centre) <= core_frac * m / 2.0).all(axis=1).reshape(volume_map.shape)
+    delta = np.where(core, core_delta, shell_delta)
+    beta = np.where(core, core_beta, shell_beta)
+    return delta.astype(np.float64), beta.astype(np.float64)
+
+
+def radialmap_96(n_shapes: int = 4, seed0: int = 0, n_theta: int = 96, n_phi: int = 192):
+    """Radii-map shapes on the 96^3 grid of the ellipsoid workload."""
+    g = Geometry(96, 96, 96, 1.0, 10.0, 45.0, 256, 256)
+    shapes = []
+    for k in range(n_shapes):
+        rng = np.random.default_rng(3000 + seed0 + k)
+        lat, lon, rot = random_orientation(rng)
+        shapes.append(Shape(RADIALMAP, radial_map=random_radial_map(rng, n_theta, n_phi, 30.0), delta=0.01,
+                            beta=0.001, latitude=lat, longitude=lon, rotation=rot))
+    return g, shapes
+
+
+def volumemap_96(n_shapes: int = 4, seed0: int = 0, m: int = 40, dx: float = 1.7, core_shell: bool = True):
+    """Volume-map shapes on the 96^3 grid, with a two-material index when asked."""
+    g = Geometry(96, 96, 96, 1.0, 10.0, 45.0, 256, 256)
+    shapes = []
+    for k in range(n_shapes):
+        rng = np.random.default_rng(4000 + seed0 + k)
+        lat, lon, rot = random_orientation(rng)
+        v = random_volume_map(rng, m)
+        s = Shape(VOLUMEMAP, volume_map=v, map_dx=dx, delta=0.01, beta=0.001, latitude=lat, longitude=lon,
+                  rotation=rot)
+        if core_shell:
+            s.map_delta, s.map_beta = core_shell_index(v, 0.02, 0.004, 0.006, 0.0005)
+        shapes.append(s)
+    return g, shapes
+
