@@ -90,7 +90,7 @@ def occupancy(s: Shape, g: Geometry, soft=False, width=0.5):
     elif s.kind == RADIALMAP:
         rm = np.asarray(s.radial_map, dtype=float)
         nt, npf = rm.shape
-        lat = np.arcsin(np.clip(u[..., 2], -1, 1))
+        lat = np.arcsin(np.clip(u[..., 2], -1, 1))            # the same angle as atan2(p_z, |p_xy|)
         lon = np.mod(np.arctan2(p[..., 1], p[..., 0]), 2 * math.pi)
         coords = np.stack([((lat + math.pi / 2) / math.pi * nt).ravel(), (lon / (2 * math.pi) * npf).ravel()])
         rs = map_coordinates(rm, coords, order=1, mode="grid-wrap").reshape(rr.shape)

@@ -202,16 +202,15 @@ static double orc_sigmoid(double t) { return 1.0 / (1.0 + exp(-t)); }
  * pi/Nt, as the paper's 4x4 example), linearly interpolated in each angle.
  * Reading: the interpolation is periodic in both angles (after the last
  * latitude row comes row 0, after the last longitude column comes column 0);
- * latitude = asin(p_z/|p|) (+pi/2 on the body z axis), longitude =
+ * latitude = atan2(p_z, sqrt(p_x^2 + p_y^2)) (+pi/2 on the body z axis; the
+ * same angle as asin(p_z/|p|), better conditioned at the poles), longitude =
  * atan2(p_y, p_x) in [0, 2 pi).
  */
 static double orc_rmap_radius(const orc_shape *sh, const double p[3], double rr)
 {
     int nt = sh->map_ntheta, np = sh->map_nphi;
-    double sz = rr > 0.0 ? p[2] / rr : 0.0;
-    if (sz > 1.0) sz = 1.0;
-    if (sz < -1.0) sz = -1.0;
-    double lat = asin(sz);
+    (void)rr;
+    double lat = atan2(p[2], sqrt(p[0] * p[0] + p[1] * p[1]));
     double lon = atan2(p[1], p[0]);
     if (lon < 0.0) lon += 2.0 * ORC_PI;
     double ti = (lat + 0.5 * ORC_PI) * ((double)nt / ORC_PI);
