@@ -62,7 +62,7 @@ typedef enum {
     SCATMAN_TC_BF16 = 5        /* tcgen05, bf16 operands, single phase product */
 } scatman_precision;
 
-enum { SCATMAN_SPHERE = 0, SCATMAN_ELLIPSOID = 1, SCATMAN_SPHHARM = 2 };
+enum { SCATMAN_SPHERE = 0, SCATMAN_ELLIPSOID = 1, SCATMAN_SPHHARM = 2, SCATMAN_RADIALMAP = 3, SCATMAN_VOLUMEMAP = 4 };
 
 /* Detector geometry. */
 enum {
@@ -126,6 +126,28 @@ typedef struct {
  *                  (lat, lon) with +90 deg towards the source (-z); the body
  *                  then spins by `rotation` about that axis
  *  cx, cy, cz      centre offset from the grid centre, length units
+ *  radial_map      SCATMAN_RADIALMAP (Sec. 5.2 "Shape (2/3)"): radii in length
+ *                  units, row-major [map_ntheta][map_nphi], at latitudes
+ *                  -pi/2 + i pi/map_ntheta and longitudes 2 pi k/map_nphi of
+ *                  the body frame (latitude +pi/2 on the main axis, longitude
+ *                  from body x towards body y); linear interpolation in both
+ *                  angles, periodic in both; a voxel is inside when its
+ *                  distance from the centre is at most the interpolated radius
+ *                  (soft occupancy: the logistic of the difference)
+ *  volume_map      SCATMAN_VOLUMEMAP (Sec. 5.2 "Shape (3/3)"): occupancy of
+ *                  map_nx x map_ny x map_nz cells, row-major [i][j][k] along
+ *                  body x, y, z, non-zero = inside; cells of edge map_dx
+ *                  (length units) centred on the shape centre, turning with the
+ *                  body; cell (i,j,k) covers [(i - map_nx/2) map_dx,
+ *                  (i + 1 - map_nx/2) map_dx) along x and likewise; occupancy
+ *                  stays binary in soft mode
+ *  map_delta, map_beta  optional per-cell index of a volume map (same layout;
+ *                  NULL takes the shape's delta or beta): a voxel-resolved
+ *                  n = 1 - delta + i beta enters both the slice strength
+ *                  (n^2 - 1) chi and the transmission scan of Eq. 8
+ * Map arrays are borrowed for the scatman_voxelise call only (copied to the
+ * device).  Map shapes have no gradient: scatman_backward returns
+ * ERR_UNSUPPORTED for them and scatman_param_count returns 0.
  */
 typedef struct {
     int kind;
@@ -136,6 +158,12 @@ typedef struct {
     double delta, beta;
     double latitude, longitude, rotation;
     double cx, cy, cz;
+    const double *radial_map;
+    int map_ntheta, map_nphi;
+    const unsigned char *volume_map;
+    int map_nx, map_ny, map_nz;
+    double map_dx;
+    const double *map_delta, *map_beta;
 } scatman_shape;
 
 typedef struct scatman_handle scatman_handle;
@@ -282,7 +310,8 @@ SCATMAN_API int scatman_server_create(const scatman_server_config *cfg, scatman_
 
 /* Queues a request; *ticket identifies it.  Returns ERR_ADMISSION if the
  * request alone needs more than the budget, ERR_ARG for invalid geometry or
- * shape (the request is not queued then). */
+ * shape, including map shapes (fit requests take sphere, ellipsoid and
+ * harmonics shapes); the request is not queued then. */
 SCATMAN_API int scatman_server_submit(scatman_server *srv, const scatman_request *req, long long *ticket);
 
 /* Waits up to timeout_s seconds (< 0: forever) for a request.  Returns

@@ -107,8 +107,11 @@ int scatman_elem_size(const scatman_handle *h) { return h && h->precision == SCA
 
 long long scatman_device_bytes(const scatman_handle *h) { return h ? h->device_bytes : 0; }
 
+static bool is_map_kind(int kind) { return kind == SCATMAN_RADIALMAP || kind == SCATMAN_VOLUMEMAP; }
+
 int scatman_param_count(const scatman_handle *h) {
     if (!h || !h->have_shape) return 0;
+    if (is_map_kind(h->sp.kind)) return 0;      // map shapes have no gradient
     return grad_param_count(h->sp) + 2;
 }
 
@@ -144,6 +147,11 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_gmax);
     cudaFree(h->d_adj_tab);
     cudaFree(h->d_adj_rtile);
+    cudaFree(h->d_rmap);
+    cudaFree(h->d_rmapf);
+    cudaFree(h->d_vmap);
+    cudaFree(h->d_mdelta);
+    cudaFree(h->d_mbeta);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     if (dev_prev >= 0) cudaSetDevice(dev_prev);
     delete h;
@@ -276,11 +284,130 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     return SCATMAN_OK;
 }
 
+// Copies a map shape's arrays to the device (grown buffers owned by the handle)
+// and fills the map fields of the shape parameters.
+static int upload_maps(scatman_handle *h, const scatman_shape *s, ShapeParams *sp) {
+    int rc;
+    sp->varn = 0;
+    sp->nscale = 1.0;
+    h->map_index_max = 0.0;
+    if (s->kind == SCATMAN_RADIALMAP) {
+        const int nt = s->map_ntheta, np = s->map_nphi;
+        const size_t n = (size_t)nt * np;
+        if (h->rmap_cap < n) {
+            cudaFree(h->d_rmap);
+            cudaFree(h->d_rmapf);
+            h->d_rmap = nullptr;
+            h->d_rmapf = nullptr;
+            h->rmap_cap = 0;
+            if ((rc = alloc_dev(h, (void **)&h->d_rmap, n * sizeof(double), "radial map"))) return rc;
+            if ((rc = alloc_dev(h, (void **)&h->d_rmapf, n * sizeof(float), "radial map"))) return rc;
+            h->rmap_cap = n;
+        }
+        std::vector<float> f(n);
+        double slope_t = 0.0, slope_p = 0.0;
+        for (int i = 0; i < nt; ++i)
+            for (int k = 0; k < np; ++k) {
+                const double r = s->radial_map[(size_t)i * np + k];
+                f[(size_t)i * np + k] = (float)r;
+                slope_t = std::fmax(slope_t, std::fabs(s->radial_map[(size_t)((i + 1) % nt) * np + k] - r));
+                slope_p = std::fmax(slope_p, std::fabs(s->radial_map[(size_t)i * np + (k + 1) % np] - r));
+            }
+        if ((rc = check_cuda(h, cudaMemcpyAsync(h->d_rmap, s->radial_map, n * sizeof(double), cudaMemcpyHostToDevice,
+                                                 h->stream), "radial map upload")))
+            return rc;
+        if ((rc = check_cuda(h, cudaMemcpyAsync(h->d_rmapf, f.data(), n * sizeof(float), cudaMemcpyHostToDevice,
+                                                 h->stream), "radial map upload")))
+            return rc;
+        // the staging vector must outlive the copy
+        if ((rc = check_cuda(h, cudaStreamSynchronize(h->stream), "radial map upload"))) return rc;
+        sp->rmap = h->d_rmap;
+        sp->rmapf = h->d_rmapf;
+        sp->ntheta = nt;
+        sp->nphi = np;
+        sp->rm_tscale = (double)nt / kPi;
+        sp->rm_pscale = (double)np / (2.0 * kPi);
+        sp->rm_tscalef = (float)sp->rm_tscale;
+        sp->rm_pscalef = (float)sp->rm_pscale;
+        sp->rm_slope = (float)std::fmax(slope_t * sp->rm_tscale, slope_p * sp->rm_pscale);
+    }
+    if (s->kind == SCATMAN_VOLUMEMAP) {
+        const size_t n = (size_t)s->map_nx * s->map_ny * s->map_nz;
+        if (h->vmap_cap < n) {
+            cudaFree(h->d_vmap);
+            h->d_vmap = nullptr;
+            h->vmap_cap = 0;
+            if ((rc = alloc_dev(h, (void **)&h->d_vmap, n, "volume map"))) return rc;
+            h->vmap_cap = n;
+        }
+        if ((rc = check_cuda(h, cudaMemcpyAsync(h->d_vmap, s->volume_map, n, cudaMemcpyHostToDevice, h->stream),
+                             "volume map upload")))
+            return rc;
+        sp->vmap = h->d_vmap;
+        sp->mx = s->map_nx;
+        sp->my = s->map_ny;
+        sp->mz = s->map_nz;
+        sp->mdx = s->map_dx;
+        sp->mdxf = (float)s->map_dx;
+        if (s->map_delta || s->map_beta) {
+            if (h->mindex_cap < n) {
+                cudaFree(h->d_mdelta);
+                cudaFree(h->d_mbeta);
+                h->d_mdelta = h->d_mbeta = nullptr;
+                h->mindex_cap = 0;
+                if ((rc = alloc_dev(h, (void **)&h->d_mdelta, n * sizeof(double), "map index"))) return rc;
+                if ((rc = alloc_dev(h, (void **)&h->d_mbeta, n * sizeof(double), "map index"))) return rc;
+                h->mindex_cap = n;
+            }
+            // per-cell values, the shape's where an array is absent; the scale
+            // is the largest |n^2 - 1| over the cells
+            std::vector<double> dl(n), bt(n);
+            double scale = 0.0, imax = 0.0;
+            for (size_t k = 0; k < n; ++k) {
+                dl[k] = s->map_delta ? s->map_delta[k] : s->delta;
+                bt[k] = s->map_beta ? s->map_beta[k] : s->beta;
+                const double re = -2.0 * dl[k] + dl[k] * dl[k] - bt[k] * bt[k];
+                const double im = 2.0 * bt[k] - 2.0 * dl[k] * bt[k];
+                scale = std::fmax(scale, std::sqrt(re * re + im * im));
+                imax = std::fmax(imax, std::fmax(std::fabs(dl[k]), std::fabs(bt[k])));
+            }
+            if ((rc = check_cuda(h, cudaMemcpyAsync(h->d_mdelta, dl.data(), n * sizeof(double), cudaMemcpyHostToDevice,
+                                                     h->stream), "map index upload")))
+                return rc;
+            if ((rc = check_cuda(h, cudaMemcpyAsync(h->d_mbeta, bt.data(), n * sizeof(double), cudaMemcpyHostToDevice,
+                                                     h->stream), "map index upload")))
+                return rc;
+            if ((rc = check_cuda(h, cudaStreamSynchronize(h->stream), "map index upload"))) return rc;
+            sp->mdelta = h->d_mdelta;
+            sp->mbeta = h->d_mbeta;
+            sp->varn = 1;
+            sp->nscale = scale > 0.0 ? scale : 1.0;
+            h->map_index_max = imax;
+        }
+    }
+    return SCATMAN_OK;
+}
+
 int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     if (!h || !s) return SCATMAN_ERR_ARG;
     const scatman_config &c = h->cfg;
-    if (s->kind < SCATMAN_SPHERE || s->kind > SCATMAN_SPHHARM)
+    if (s->kind < SCATMAN_SPHERE || s->kind > SCATMAN_VOLUMEMAP)
         return set_error(h, SCATMAN_ERR_ARG, "unknown shape kind");
+    if (s->kind == SCATMAN_RADIALMAP) {
+        if (!s->radial_map || s->map_ntheta < 1 || s->map_nphi < 1)
+            return set_error(h, SCATMAN_ERR_ARG, "radial map needs data and map_ntheta, map_nphi >= 1");
+        for (long long k = 0; k < (long long)s->map_ntheta * s->map_nphi; ++k)
+            if (!std::isfinite(s->radial_map[k])) return set_error(h, SCATMAN_ERR_ARG, "radial map values must be finite");
+    }
+    if (s->kind == SCATMAN_VOLUMEMAP) {
+        if (!s->volume_map || s->map_nx < 1 || s->map_ny < 1 || s->map_nz < 1 || !(s->map_dx > 0))
+            return set_error(h, SCATMAN_ERR_ARG, "volume map needs data, map_nx/ny/nz >= 1 and map_dx > 0");
+        const long long ncell = (long long)s->map_nx * s->map_ny * s->map_nz;
+        for (const double *arr : {s->map_delta, s->map_beta})
+            if (arr)
+                for (long long k = 0; k < ncell; ++k)
+                    if (!std::isfinite(arr[k])) return set_error(h, SCATMAN_ERR_ARG, "map index values must be finite");
+    }
     if (s->kind == SCATMAN_SPHERE && !(s->r > 0)) return set_error(h, SCATMAN_ERR_ARG, "sphere radius must be > 0");
     if (s->kind == SCATMAN_ELLIPSOID && !(s->a > 0 && s->b > 0 && s->c > 0))
         return set_error(h, SCATMAN_ERR_ARG, "ellipsoid semi-axes must be > 0");
@@ -293,6 +420,10 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
         return set_error(h, SCATMAN_ERR_ARG, "delta and beta must be finite");
 
     h->shape = *s;
+    // the map arrays are borrowed for this call only
+    h->shape.radial_map = nullptr;
+    h->shape.volume_map = nullptr;
+    h->shape.map_delta = h->shape.map_beta = nullptr;
     h->alm.assign((size_t)(s->kind == SCATMAN_SPHHARM ? (s->lmax + 1) * (s->lmax + 1) : 0), 0.0);
     if (s->kind == SCATMAN_SPHHARM && s->lmax > 0)
         std::memcpy(h->alm.data(), s->alm, sizeof(double) * h->alm.size());
@@ -320,6 +451,8 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     sp.cz = s->cz;
     for (size_t k = 0; k < h->alm.size(); ++k) sp.alm[k] = h->alm[k];
     finish_shape_params(&sp);
+    int rc = upload_maps(h, s, &sp);
+    if (rc) return rc;
 
     GridParams gp{c.nx, c.ny, c.nz, c.voxel, h->k0, s->delta, s->beta};
     SliceOut so;
@@ -333,9 +466,19 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     so.chi = h->d_chi;
     so.bounds = h->d_bounds;
     double strength = std::fmax(std::fabs(s->delta), std::fabs(s->beta));
+    if (sp.varn) strength = std::fmax(strength, h->map_index_max);
     h->scan_fp64 = c.scan_fp64 || (h->k0 * c.voxel * c.nz * strength > 5.0);
-    int rc = check_cuda(h, launch_voxelise(sp, gp, so, h->scan_fp64, h->precision == SCATMAN_FP64, h->stream),
-                        "voxelise");
+    // global strength factor of the stored slices: n^2 - 1 with n = 1 - delta + i beta,
+    // or the index scale when every cell carries its own n
+    if (sp.varn) {
+        h->str_re = sp.nscale;
+        h->str_im = 0.0;
+    } else {
+        h->str_re = -2.0 * s->delta + s->delta * s->delta - s->beta * s->beta;
+        h->str_im = 2.0 * s->beta - 2.0 * s->delta * s->beta;
+    }
+    rc = check_cuda(h, launch_voxelise(sp, gp, so, h->scan_fp64, h->precision == SCATMAN_FP64, h->stream),
+                    "voxelise");
     if (rc) return rc;
     h->have_shape = true;
     h->have_forward = false;
@@ -346,10 +489,7 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
     if (!h || !I_dev) return set_error(h, SCATMAN_ERR_ARG, "I_dev is NULL");
     if (!h->have_shape) return set_error(h, SCATMAN_ERR_STATE, "forward before voxelise");
     const scatman_config &c = h->cfg;
-    const double d = h->shape.delta, b = h->shape.beta;
-    // n^2 - 1 with n = 1 - delta + i beta
-    const double str_re = -2.0 * d + d * d - b * b;
-    const double str_im = 2.0 * b - 2.0 * d * b;
+    const double str_re = h->str_re, str_im = h->str_im;     // set by voxelise
     cudaError_t e;
     if (h->uniform_q) {
         e = launch_msft_uniform(h->precision == SCATMAN_FP64, h->d_s, c.nx, c.ny, c.nz, c.det_nx, c.det_ny,
@@ -492,6 +632,8 @@ int scatman_get_q(scatman_handle *h, double *q_host) {
 int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams) {
     if (!h || !dLdI_dev || !dLdparams) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
     if (!h->have_forward) return set_error(h, SCATMAN_ERR_STATE, "backward before forward");
+    if (is_map_kind(h->sp.kind))
+        return set_error(h, SCATMAN_ERR_UNSUPPORTED, "map shapes have no gradient (forward only)");
     const scatman_config &c = h->cfg;
     const bool f64 = h->precision == SCATMAN_FP64;
     const size_t nvox = (size_t)c.nx * c.ny * c.nz;

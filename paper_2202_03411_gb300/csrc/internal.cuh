@@ -53,6 +53,21 @@ struct ShapeParams {
     float sh_bf[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 2) / 2];
     float sh_df[SCATMAN_MAX_LMAX + 1];
     float sh_ef[SCATMAN_MAX_LMAX + 1];
+    // radii map (device copies, [ntheta][nphi])
+    const double *rmap;
+    const float *rmapf;
+    int ntheta, nphi;
+    double rm_tscale, rm_pscale;    // ntheta / pi, nphi / (2 pi)
+    float rm_tscalef, rm_pscalef;
+    float rm_slope;                 // max |dr/d angle| between neighbouring samples (FP32 decision margin)
+    // volume map (device copies, [mx][my][mz])
+    const unsigned char *vmap;
+    int mx, my, mz;
+    double mdx;
+    float mdxf;
+    const double *mdelta, *mbeta;   // per-cell index, or null
+    int varn;                       // 1: voxel-resolved index (s carries (n_v^2 - 1) / nscale)
+    double nscale;                  // max |n_v^2 - 1| over the map's cells
 };
 
 // Fills the FP32 copies and the harmonic recurrence tables of a ShapeParams
@@ -67,6 +82,7 @@ __host__ __device__
 inline int n_geom_params(int kind, int lmax) {
     if (kind == SCATMAN_SPHERE) return 1;
     if (kind == SCATMAN_ELLIPSOID) return 3;
+    if (kind == SCATMAN_RADIALMAP || kind == SCATMAN_VOLUMEMAP) return 0;
     return (lmax + 1) * (lmax + 1);
 }
 
@@ -134,6 +150,16 @@ struct scatman_handle {
     unsigned *d_gmax = nullptr;     // tensor-core adjoint: max |w A| (float bits)
     float4 *d_adj_tab = nullptr;    // tensor-core adjoint: per-pixel constants (built at the first backward)
     uint8_t *d_adj_rtile = nullptr; // tensor-core adjoint: y-phase operand tiles (built at the first backward)
+    // map shapes: device copies of the last voxelised map (grown as needed)
+    double *d_rmap = nullptr;
+    float *d_rmapf = nullptr;
+    size_t rmap_cap = 0;
+    unsigned char *d_vmap = nullptr;
+    size_t vmap_cap = 0;
+    double *d_mdelta = nullptr, *d_mbeta = nullptr;
+    size_t mindex_cap = 0;
+    double str_re = 0, str_im = 0;  // global strength factor of s: n^2 - 1, or the map's index scale
+    double map_index_max = 0;       // max |delta|, |beta| over a volume map's cells
     int splits = 1;
     long long device_bytes = 0;
     scm::TcMaps tmap_B;

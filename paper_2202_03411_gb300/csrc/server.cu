@@ -366,6 +366,9 @@ int scatman_server_submit(scatman_server *srv, const scatman_request *req, long 
         return SCATMAN_ERR_ARG;
     if (req->want_gradient && !req->grad_out) return SCATMAN_ERR_ARG;
     const scatman_shape &sh = req->shape;
+    // fit requests take parametric shapes (sphere, ellipsoid, harmonics): map
+    // shapes have no gradient, and their arrays are only borrowed for a call
+    if (sh.kind < SCATMAN_SPHERE || sh.kind > SCATMAN_SPHHARM) return SCATMAN_ERR_ARG;
     if (sh.kind == SCATMAN_SPHHARM && (sh.lmax < 0 || sh.lmax > SCATMAN_MAX_LMAX || (sh.lmax > 0 && !sh.alm)))
         return SCATMAN_ERR_ARG;
     auto r = std::make_shared<Req>();

@@ -114,6 +114,65 @@ __device__ __forceinline__ void body_coords(const ShapeParams &sp, const GridPar
     pz = __dadd_rn(__dadd_rn(__dmul_rn(sp.R[2], dx), __dmul_rn(sp.R[5], dy)), __dmul_rn(sp.R[8], dz));
 }
 
+// Radius of a radii map (Sec. 5.2 "Shape (2/3)") along the body direction of
+// p: latitude atan2(p_z, |p_xy|), longitude atan2(p_y, p_x) in [0, 2 pi);
+// samples at latitudes -pi/2 + i pi/ntheta and longitudes 2 pi k/nphi,
+// linear in each angle, periodic in both.  The FP64 form keeps the oracle's
+// operation order (no contraction into fused multiply-adds).
+__device__ __forceinline__ double rmap_radius_d(const ShapeParams &sp, double px, double py, double pz) {
+    const double rxy = sqrt(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)));
+    const double lat = atan2(pz, rxy);
+    double lon = atan2(py, px);
+    if (lon < 0.0) lon = __dadd_rn(lon, 2.0 * kPi);
+    const double ti = __dmul_rn(__dadd_rn(lat, 0.5 * kPi), sp.rm_tscale);
+    const double tk = __dmul_rn(lon, sp.rm_pscale);
+    const double fi = floor(ti), fk = floor(tk);
+    const double f = __dadd_rn(ti, -fi), g = __dadd_rn(tk, -fk);
+    const int nt = sp.ntheta, np = sp.nphi;
+    int i0 = (int)fi % nt, k0 = (int)fk % np;
+    if (i0 < 0) i0 += nt;
+    if (k0 < 0) k0 += np;
+    const int i1 = (i0 + 1) % nt, k1 = (k0 + 1) % np;
+    const double r00 = sp.rmap[(size_t)i0 * np + k0], r01 = sp.rmap[(size_t)i0 * np + k1];
+    const double r10 = sp.rmap[(size_t)i1 * np + k0], r11 = sp.rmap[(size_t)i1 * np + k1];
+    const double omf = __dadd_rn(1.0, -f), omg = __dadd_rn(1.0, -g);
+    const double t1 = __dmul_rn(__dmul_rn(omf, omg), r00);
+    const double t2 = __dmul_rn(__dmul_rn(omf, g), r01);
+    const double t3 = __dmul_rn(__dmul_rn(f, omg), r10);
+    const double t4 = __dmul_rn(__dmul_rn(f, g), r11);
+    return __dadd_rn(__dadd_rn(__dadd_rn(t1, t2), t3), t4);
+}
+__device__ __forceinline__ float rmap_radius_f(const ShapeParams &sp, float px, float py, float pz) {
+    const float lat = atan2f(pz, sqrtf(px * px + py * py));
+    float lon = atan2f(py, px);
+    if (lon < 0.f) lon += 2.f * (float)kPi;
+    const float ti = (lat + 0.5f * (float)kPi) * sp.rm_tscalef;
+    const float tk = lon * sp.rm_pscalef;
+    const float fi = floorf(ti), fk = floorf(tk);
+    const float f = ti - fi, g = tk - fk;
+    const int nt = sp.ntheta, np = sp.nphi;
+    int i0 = (int)fi % nt, k0 = (int)fk % np;
+    if (i0 < 0) i0 += nt;
+    if (k0 < 0) k0 += np;
+    const int i1 = (i0 + 1) % nt, k1 = (k0 + 1) % np;
+    const float r00 = sp.rmapf[(size_t)i0 * np + k0], r01 = sp.rmapf[(size_t)i0 * np + k1];
+    const float r10 = sp.rmapf[(size_t)i1 * np + k0], r11 = sp.rmapf[(size_t)i1 * np + k1];
+    return (1.f - f) * (1.f - g) * r00 + (1.f - f) * g * r01 + f * (1.f - g) * r10 + f * g * r11;
+}
+
+// Volume-map cell (Sec. 5.2 "Shape (3/3)") holding the centre of voxel
+// (ix, iy, iz): cell (i, j, k) covers [(i - mx/2) dx, (i + 1 - mx/2) dx) along
+// body x and likewise; -1 outside the map.  The FP32 form decides unless a
+// cell coordinate lies within its error bound of a cell face; then the FP64
+// form (the oracle's operation order) decides.
+__device__ __forceinline__ int vmap_cell_fp64(const ShapeParams &sp, double px, double py, double pz) {
+    const double ci = floor(__dadd_rn(__ddiv_rn(px, sp.mdx), 0.5 * sp.mx));
+    const double cj = floor(__dadd_rn(__ddiv_rn(py, sp.mdx), 0.5 * sp.my));
+    const double ck = floor(__dadd_rn(__ddiv_rn(pz, sp.mdx), 0.5 * sp.mz));
+    if (ci < 0.0 || cj < 0.0 || ck < 0.0 || ci >= sp.mx || cj >= sp.my || ck >= sp.mz) return -1;
+    return ((int)ci * sp.my + (int)cj) * sp.mz + (int)ck;
+}
+
 // The FP64 binary decision: sphere |d|^2 <= r^2, ellipsoid
 // (x/a)^2+(y/b)^2+(z/c)^2 <= 1, harmonics |p| <= r(theta,phi); ties inside.
 static __device__ __noinline__ double occupancy_binary_fp64(const ShapeParams &sp, const GridParams &gp, int ix, int iy,
@@ -134,8 +193,44 @@ static __device__ __noinline__ double occupancy_binary_fp64(const ShapeParams &s
         return qf <= 1.0 ? 1.0 : 0.0;
     }
     double rr = sqrt(p2);
+    if (sp.kind == SCATMAN_RADIALMAP) return rr <= rmap_radius_d(sp, px, py, pz) ? 1.0 : 0.0;
+    if (sp.kind == SCATMAN_VOLUMEMAP) {
+        const int cell = vmap_cell_fp64(sp, px, py, pz);
+        return (cell >= 0 && sp.vmap[cell] != 0) ? 1.0 : 0.0;
+    }
     double rs = sh_radius<double>(sp, px, py, pz, rr);
     return rr <= rs ? 1.0 : 0.0;
+}
+
+// Volume-map cell of voxel (ix, iy, iz) in either precision (see vmap_cell_fp64).
+template <bool kFp64>
+__device__ __forceinline__ int vmap_cell(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz) {
+    if (!kFp64) {
+        const float vox = (float)gp.voxel;
+        const float dx = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
+        const float dy = ((float)iy - 0.5f * (float)(gp.ny - 1)) * vox - sp.cyf;
+        const float dz = ((float)iz - 0.5f * (float)(gp.nz - 1)) * vox - sp.czf;
+        const float px = sp.Rf[0] * dx + sp.Rf[3] * dy + sp.Rf[6] * dz;
+        const float py = sp.Rf[1] * dx + sp.Rf[4] * dy + sp.Rf[7] * dz;
+        const float pz = sp.Rf[2] * dx + sp.Rf[5] * dy + sp.Rf[8] * dz;
+        const float ci = px / sp.mdxf + 0.5f * (float)sp.mx;
+        const float cj = py / sp.mdxf + 0.5f * (float)sp.my;
+        const float ck = pz / sp.mdxf + 0.5f * (float)sp.mz;
+        // error bound of a cell coordinate: the rotated position to ~1e-6 of
+        // its size plus the division and the offset
+        const float d = fabsf(dx) + fabsf(dy) + fabsf(dz) + vox;
+        const float tol = 1e-4f + 4e-6f * d / sp.mdxf + 4e-7f * (float)(sp.mx + sp.my + sp.mz);
+        const float fi = ci - floorf(ci), fj = cj - floorf(cj), fk = ck - floorf(ck);
+        const bool clear = fi > tol && fi < 1.f - tol && fj > tol && fj < 1.f - tol && fk > tol && fk < 1.f - tol;
+        if (clear) {
+            const int i = (int)floorf(ci), j = (int)floorf(cj), k = (int)floorf(ck);
+            if (i < 0 || j < 0 || k < 0 || i >= sp.mx || j >= sp.my || k >= sp.mz) return -1;
+            return (i * sp.my + j) * sp.mz + k;
+        }
+    }
+    double px, py, pz;
+    body_coords(sp, gp, ix, iy, iz, px, py, pz);
+    return vmap_cell_fp64(sp, px, py, pz);
 }
 
 // Occupancy of one voxel.  Binary decisions are the FP64 ones above; the
@@ -146,6 +241,11 @@ static __device__ __noinline__ double occupancy_binary_fp64(const ShapeParams &s
 // the signed distance to the surface along the ray from the centre.
 template <bool kFp64>
 __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz) {
+    if (sp.kind == SCATMAN_VOLUMEMAP) {
+        // binary in both modes: a volume map has no surface radius
+        const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
+        return (cell >= 0 && sp.vmap[cell] != 0) ? 1.0 : 0.0;
+    }
     if (!sp.soft) {
         if (!kFp64) {
             const float vox = (float)gp.voxel;
@@ -164,6 +264,15 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
                     const float u = px * sp.inv_af, v = py * sp.inv_bf, w = pz * sp.inv_cf;
                     const float m = 1.f - (u * u + v * v + w * w);
                     if (fabsf(m) > 1e-4f) return m > 0.f ? 1.0 : 0.0;
+                } else if (sp.kind == SCATMAN_RADIALMAP) {
+                    const float rr = sqrtf(px * px + py * py + pz * pz);
+                    const float rs = rmap_radius_f(sp, px, py, pz);
+                    const float m = rs - rr;
+                    // FP32 error bound: angles to ~2e-6 rad (worse near the
+                    // centre) times the map's steepest slope, plus rounding
+                    const float margin = 4e-3f * vox + 1e-6f * (fabsf(rs) + rr) +
+                                         sp.rm_slope * (2e-6f + 2e-5f / fmaxf(rr, vox));
+                    if (fabsf(m) > margin) return m > 0.f ? 1.0 : 0.0;
                 } else {
                     const float rr = sqrtf(px * px + py * py + pz * pz);
                     const float rs = sh_radius<float>(sp, px, py, pz, rr);
@@ -192,6 +301,8 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
             double u0 = 0, u1 = 0, u2 = 1;
             if (rr > 0) { u0 = px / rr; u1 = py / rr; u2 = pz / rr; }
             rs = 1.0 / sqrt((u0 / sp.a) * (u0 / sp.a) + (u1 / sp.b) * (u1 / sp.b) + (u2 / sp.c) * (u2 / sp.c));
+        } else if (sp.kind == SCATMAN_RADIALMAP) {
+            rs = rmap_radius_d(sp, px, py, pz);
         } else {
             rs = sh_radius<double>(sp, px, py, pz, rr);
         }
@@ -205,6 +316,8 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
         if (rf > 0.f) { u0 = (float)px / rf; u1 = (float)py / rf; u2 = (float)pz / rf; }
         const float ia = sp.inv_af, ib = sp.inv_bf, ic = sp.inv_cf;
         rs = rsqrtf(u0 * u0 * ia * ia + u1 * u1 * ib * ib + u2 * u2 * ic * ic);
+    } else if (sp.kind == SCATMAN_RADIALMAP) {
+        rs = rmap_radius_f(sp, (float)px, (float)py, (float)pz);
     } else {
         rs = sh_radius<float>(sp, (float)px, (float)py, (float)pz, rf);
     }

@@ -68,18 +68,70 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
     const ScanT a_att = (ScanT)(gp.k0 * gp.voxel * gp.beta);     // attenuation per unit C
     const ScanT a_ph = (ScanT)(gp.k0 * gp.voxel * gp.delta);     // phase per unit C
 
+    const bool varn = sp.varn != 0;                               // per-cell index of a volume map
+    const ScanT kdz = (ScanT)(gp.k0 * gp.voxel);
+    const Re inv_scale = (Re)(1.0 / sp.nscale);
     for (int yl = warp; yl < kLinesPerCta; yl += kVoxThreads / 32) {
         const int iy = y0 + yl;
         if (iy >= gp.ny) break;
         const int z0 = lane * run;
         const int z1 = min(nz, z0 + run);
         ScanT local = (ScanT)0;
+        ScanT ld = (ScanT)0, lb = (ScanT)0;                        // sums of chi delta_v, chi beta_v
 #pragma unroll 1
         for (int iz = z0; iz < z1; ++iz) {
-            const double c = occupancy<kFp64>(sp, gp, ix, iy, iz);
+            double c;
+            if (varn) {
+                const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
+                c = (cell >= 0 && sp.vmap[cell] != 0) ? 1.0 : 0.0;
+                if (c != 0.0) {
+                    ld += (ScanT)sp.mdelta[cell];
+                    lb += (ScanT)sp.mbeta[cell];
+                }
+            } else {
+                c = occupancy<kFp64>(sp, gp, ix, iy, iz);
+            }
             if (kFp64) s_tile[iz * kLinesPerCta + yl].x = c;         // exact copy until pass 2
             chi_tile[iz * kLinesPerCta + yl] = (float)c;
             local += (ScanT)c;
+        }
+        if (varn) {
+            // voxel-resolved index: T_j = exp(i k0 dz sum_{j'<j} chi (n_v - 1)),
+            // s = chi (n_v^2 - 1) T / nscale (Eq. 8-9 with one n per voxel)
+            ScanT id = ld, ib = lb;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const ScanT a = __shfl_up_sync(0xffffffffu, id, o);
+                const ScanT b = __shfl_up_sync(0xffffffffu, ib, o);
+                if (lane >= o) {
+                    id += a;
+                    ib += b;
+                }
+            }
+            ScanT Cd = id - ld, Cb = ib - lb;
+#pragma unroll 1
+            for (int iz = z0; iz < z1; ++iz) {
+                const Re chi = kFp64 ? (Re)s_tile[iz * kLinesPerCta + yl].x : (Re)chi_tile[iz * kLinesPerCta + yl];
+                double dl = 0.0, bt = 0.0;
+                if (chi != (Re)0) {
+                    const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
+                    dl = sp.mdelta[cell];
+                    bt = sp.mbeta[cell];
+                }
+                const ScanT mag = exp(-kdz * Cb);
+                ScanT sn, cs;
+                sincos(kdz * Cd, &sn, &cs);
+                const Re sr = (Re)((-2.0 * dl + dl * dl - bt * bt)) * inv_scale;
+                const Re si = (Re)((2.0 * bt - 2.0 * dl * bt)) * inv_scale;
+                const Re tr = (Re)(mag * cs), ti = -(Re)(mag * sn);
+                Cx v;
+                v.x = chi * (sr * tr - si * ti);
+                v.y = chi * (sr * ti + si * tr);
+                s_tile[iz * kLinesPerCta + yl] = v;
+                Cd += (ScanT)(chi * (Re)dl);
+                Cb += (ScanT)(chi * (Re)bt);
+            }
+            continue;
         }
         // warp exclusive scan of the lanes' run totals
         ScanT incl = local;
