@@ -217,6 +217,38 @@ def plain_config_errors(c1, c2, n_sample=1024):
             "ellipsoid_sample_pixels": n_sample}
 
 
+def map_configs(precision):
+    """Map shapes of Sec. 5.2 on the 96^3 / 256^2 / 45 deg geometry: radii maps
+    (96 x 192 samples) and two-material volume maps (40^3 cells of 1.7 voxels,
+    per-cell delta and beta).  Errors against the oracle are added by the CPU leg."""
+    from workloads import radialmap_96, volumemap_96
+    out, refs = {}, {}
+    for name, maker in (("radialmap_96", radialmap_96), ("volumemap_index_96", volumemap_96)):
+        g, shapes = maker(n_shapes=4)
+        ms, I0 = time_mode(g, shapes, precision, reps=2)
+        out[name] = {"precision": precision, "patterns_per_s": 1e3 / ms, "ms_per_pattern": ms,
+                     "shapes_timed": len(shapes)}
+        refs[name] = (g, shapes[0], I0)
+    return out, refs
+
+
+def map_config_errors(refs, n_sample=1024):
+    """CPU leg: the oracle on a pixel sample of each map workload's first shape."""
+    import numpy as np
+
+    import oracle
+    errs = {}
+    for name, (g, s, I) in refs.items():
+        sample = np.sort(np.random.default_rng(1).choice(g.n_pix, size=n_sample, replace=False))
+        chi, _ = oracle.voxelise(s, g)
+        rho = oracle.slices_n(chi, g, *oracle.voxel_index(s, g)) if s.varying_index() else \
+            oracle.slices(chi, g, s.delta, s.beta)
+        Iref = np.abs(oracle.msft(rho, oracle.detector_q(g)[sample], g.voxel)) ** 2
+        errs[name + "_rel_l2"] = oracle.relative_l2(I[sample], Iref)
+    errs["sample_pixels"] = n_sample
+    return errs
+
+
 def fig8b_run(radii=(3.0, 5.0, 10.0, 20.0), dets=(256, 512, 1024, 2048), precision="fp32", reps=5):
     """Sec. 6 timing study (Fig. 8b): the Listing-2 harmonics shape scaled to a mean
     radius of 3/5/10/20 wavelengths on the paper's uniform-q virtual detector of
@@ -563,6 +595,7 @@ def main():
     fit = fit_step_run(32, args.precision) if extras else None
     plain, c1, c2 = plain_configs() if extras else (None, None, None)
     fig8b = fig8b_run() if extras else None
+    maps, map_refs = map_configs(args.precision) if extras else (None, None)
     cpu = None
     err = None
     err_fp32 = None
@@ -571,6 +604,8 @@ def main():
         _, err_fp32 = cpu_baseline(shapes, g, I0_fp32, 512)
         if plain is not None:
             plain["errors_vs_fp64_oracle"] = plain_config_errors(c1, c2)
+        if maps is not None:
+            maps["errors_vs_fp64_oracle"] = map_config_errors(map_refs)
     if fp32 is not None:
         fp32["rel_l2_I_vs_fp64_oracle"] = err_fp32
     serving = None
@@ -598,6 +633,7 @@ def main():
         "fit_step_96": fit,
         "plain_configs": plain,
         "fig8b_uniform_q": fig8b,
+        "map_shapes_96": maps,
         "serving_short": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,

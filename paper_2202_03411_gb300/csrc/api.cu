@@ -319,8 +319,7 @@ static int upload_maps(scatman_handle *h, const scatman_shape *s, ShapeParams *s
         if ((rc = check_cuda(h, cudaMemcpyAsync(h->d_rmapf, f.data(), n * sizeof(float), cudaMemcpyHostToDevice,
                                                  h->stream), "radial map upload")))
             return rc;
-        // the staging vector must outlive the copy
-        if ((rc = check_cuda(h, cudaStreamSynchronize(h->stream), "radial map upload"))) return rc;
+        // a copy from pageable host memory has left the staging vector when the call returns
         sp->rmap = h->d_rmap;
         sp->rmapf = h->d_rmapf;
         sp->ntheta = nt;
@@ -377,7 +376,6 @@ static int upload_maps(scatman_handle *h, const scatman_shape *s, ShapeParams *s
             if ((rc = check_cuda(h, cudaMemcpyAsync(h->d_mbeta, bt.data(), n * sizeof(double), cudaMemcpyHostToDevice,
                                                      h->stream), "map index upload")))
                 return rc;
-            if ((rc = check_cuda(h, cudaStreamSynchronize(h->stream), "map index upload"))) return rc;
             sp->mdelta = h->d_mdelta;
             sp->mbeta = h->d_mbeta;
             sp->varn = 1;

@@ -239,9 +239,11 @@ __device__ __forceinline__ int vmap_cell(const ShapeParams &sp, const GridParams
 // (1e-4 relative for sphere and ellipsoid, 4e-3 voxel for harmonics), so the
 // decision always equals the FP64 one.  Soft occupancy is the logistic of
 // the signed distance to the surface along the ray from the centre.
-template <bool kFp64>
+// kMaps: compiled for the map kinds (radii and volume maps); the parametric
+// kinds' instantiation carries none of their code.
+template <bool kFp64, bool kMaps = false>
 __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz) {
-    if (sp.kind == SCATMAN_VOLUMEMAP) {
+    if (kMaps && sp.kind == SCATMAN_VOLUMEMAP) {
         // binary in both modes: a volume map has no surface radius
         const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
         return (cell >= 0 && sp.vmap[cell] != 0) ? 1.0 : 0.0;
@@ -264,7 +266,7 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
                     const float u = px * sp.inv_af, v = py * sp.inv_bf, w = pz * sp.inv_cf;
                     const float m = 1.f - (u * u + v * v + w * w);
                     if (fabsf(m) > 1e-4f) return m > 0.f ? 1.0 : 0.0;
-                } else if (sp.kind == SCATMAN_RADIALMAP) {
+                } else if (kMaps && sp.kind == SCATMAN_RADIALMAP) {
                     const float rr = sqrtf(px * px + py * py + pz * pz);
                     const float rs = rmap_radius_f(sp, px, py, pz);
                     const float m = rs - rr;
@@ -301,7 +303,7 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
             double u0 = 0, u1 = 0, u2 = 1;
             if (rr > 0) { u0 = px / rr; u1 = py / rr; u2 = pz / rr; }
             rs = 1.0 / sqrt((u0 / sp.a) * (u0 / sp.a) + (u1 / sp.b) * (u1 / sp.b) + (u2 / sp.c) * (u2 / sp.c));
-        } else if (sp.kind == SCATMAN_RADIALMAP) {
+        } else if (kMaps && sp.kind == SCATMAN_RADIALMAP) {
             rs = rmap_radius_d(sp, px, py, pz);
         } else {
             rs = sh_radius<double>(sp, px, py, pz, rr);
@@ -316,7 +318,7 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
         if (rf > 0.f) { u0 = (float)px / rf; u1 = (float)py / rf; u2 = (float)pz / rf; }
         const float ia = sp.inv_af, ib = sp.inv_bf, ic = sp.inv_cf;
         rs = rsqrtf(u0 * u0 * ia * ia + u1 * u1 * ib * ib + u2 * u2 * ic * ic);
-    } else if (sp.kind == SCATMAN_RADIALMAP) {
+    } else if (kMaps && sp.kind == SCATMAN_RADIALMAP) {
         rs = rmap_radius_f(sp, (float)px, (float)py, (float)pz);
     } else {
         rs = sh_radius<float>(sp, (float)px, (float)py, (float)pz, rf);

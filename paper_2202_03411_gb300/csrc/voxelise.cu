@@ -51,7 +51,7 @@ constexpr int kMaxRun = 8;          // z values per lane: nz <= 256
 // Pass 1 renders chi into shared memory and sums each lane's run of z;
 // a warp-shuffle scan turns the run totals into exclusive prefixes; pass 2
 // walks the run again to form C_j, T_j and s_j.
-template <bool kFp64, typename ScanT>
+template <bool kFp64, typename ScanT, bool kMaps>
 __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams sp, GridParams gp,
                                                                     SliceOut out) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
     const ScanT a_att = (ScanT)(gp.k0 * gp.voxel * gp.beta);     // attenuation per unit C
     const ScanT a_ph = (ScanT)(gp.k0 * gp.voxel * gp.delta);     // phase per unit C
 
-    const bool varn = sp.varn != 0;                               // per-cell index of a volume map
+    const bool varn = kMaps && sp.varn != 0;                      // per-cell index of a volume map
     const ScanT kdz = (ScanT)(gp.k0 * gp.voxel);
     const Re inv_scale = (Re)(1.0 / sp.nscale);
     for (int yl = warp; yl < kLinesPerCta; yl += kVoxThreads / 32) {
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
                     lb += (ScanT)sp.mbeta[cell];
                 }
             } else {
-                c = occupancy<kFp64>(sp, gp, ix, iy, iz);
+                c = occupancy<kFp64, kMaps>(sp, gp, ix, iy, iz);
             }
             if (kFp64) s_tile[iz * kLinesPerCta + yl].x = c;         // exact copy until pass 2
             chi_tile[iz * kLinesPerCta + yl] = (float)c;
@@ -227,23 +227,13 @@ cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const S
     // per-function attribute shared by all threads: set it to the largest size
     // (nz = 256) so a concurrent launch from another thread is never rejected
     const int smem_max = (int)((cx + sizeof(float)) * 32 * kMaxRun * kLinesPerCta);
-    cudaError_t e;
-    if (fp64_mode) {
-        auto k = voxelise_scan_kernel<true, double>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-        if (e != cudaSuccess) return e;
-        k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
-    } else if (scan_fp64) {
-        auto k = voxelise_scan_kernel<false, double>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-        if (e != cudaSuccess) return e;
-        k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
-    } else {
-        auto k = voxelise_scan_kernel<false, float>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
-        if (e != cudaSuccess) return e;
-        k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
-    }
+    const bool maps = sp.kind == SCATMAN_RADIALMAP || sp.kind == SCATMAN_VOLUMEMAP;
+    auto k = fp64_mode   ? (maps ? voxelise_scan_kernel<true, double, true> : voxelise_scan_kernel<true, double, false>)
+             : scan_fp64 ? (maps ? voxelise_scan_kernel<false, double, true> : voxelise_scan_kernel<false, double, false>)
+                         : (maps ? voxelise_scan_kernel<false, float, true> : voxelise_scan_kernel<false, float, false>);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
     return cudaGetLastError();
 }
 
