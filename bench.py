@@ -169,17 +169,21 @@ def time_mode(g, shapes, precision, reps=1):
     sm.scatman_sync(h)
     I0 = I.double().cpu().numpy()
     stream = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    n = reps * len(shapes)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    ev[0].record(stream)
+    k = 0
     for _ in range(reps):
         for s_ in shapes:
             sm.scatman_voxelise(h, s_)
             sm.scatman_forward(h, I)
-    e1.record(stream)
+            k += 1
+            ev[k].record(stream)
     sm.scatman_sync(h)
     h.close()
-    ms = e0.elapsed_time(e1) / (reps * len(shapes))
+    per = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(n))
+    ms = ev[0].elapsed_time(ev[n]) / n
+    time_mode.last_p50_p99 = (per[len(per) // 2], per[min(len(per) - 1, int(math.ceil(0.99 * len(per))) - 1)])
     return ms, I0
 
 
@@ -189,12 +193,17 @@ def plain_configs():
     from workloads import ellipsoid_96, sphere_32
     g1, s1 = sphere_32()
     ms1, I1 = time_mode(g1, s1, "fp64", reps=20)
+    lat1 = time_mode.last_p50_p99
     g2, s2 = ellipsoid_96(n_shapes=64)
     ms32, I2_32 = time_mode(g2, s2[:16], "fp32")
+    lat32 = time_mode.last_p50_p99
     ms64, I2_64 = time_mode(g2, s2[:4], "fp64")
-    out = {"sphere_32_fp64": {"patterns_per_s": 1e3 / ms1, "ms_per_pattern": ms1},
-           "ellipsoid_96": {"fp32": {"patterns_per_s": 1e3 / ms32, "ms_per_pattern": ms32, "shapes_timed": 16},
-                            "fp64": {"patterns_per_s": 1e3 / ms64, "ms_per_pattern": ms64, "shapes_timed": 4}}}
+    lat64 = time_mode.last_p50_p99
+    out = {"sphere_32_fp64": {"patterns_per_s": 1e3 / ms1, "ms_per_pattern": ms1, "p50_p99_ms": lat1},
+           "ellipsoid_96": {"fp32": {"patterns_per_s": 1e3 / ms32, "ms_per_pattern": ms32, "shapes_timed": 16,
+                                     "p50_p99_ms": lat32},
+                            "fp64": {"patterns_per_s": 1e3 / ms64, "ms_per_pattern": ms64, "shapes_timed": 4,
+                                     "p50_p99_ms": lat64}}}
     return out, (g1, s1[0], I1), (g2, s2[0], I2_32, I2_64)
 
 
@@ -227,7 +236,7 @@ def map_configs(precision):
         g, shapes = maker(n_shapes=4)
         ms, I0 = time_mode(g, shapes, precision, reps=2)
         out[name] = {"precision": precision, "patterns_per_s": 1e3 / ms, "ms_per_pattern": ms,
-                     "shapes_timed": len(shapes)}
+                     "shapes_timed": len(shapes), "p50_p99_ms": time_mode.last_p50_p99}
         refs[name] = (g, shapes[0], I0)
     return out, refs
 
@@ -383,14 +392,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(shapes, g, I_gpu, n_sample, seed=0):
+def cpu_baseline(shapes, g, I_gpu, n_sample, seed=0, threads=None):
     """The oracle, as it stands, on a bounded sample of the same workload: one
     pattern's full voxelisation and transmission plus the field at n_sample
     pixels, scaled to patterns/s.  Also returns the GPU result's relative L2
-    error against the oracle on that sample."""
+    error against the oracle on that sample.  threads: OpenMP threads (None:
+    all host cores)."""
     import numpy as np
 
     import oracle
+    all_threads = oracle.num_threads()
+    if threads is not None:
+        oracle.set_threads(threads)
     shape = shapes[0]
     rng = np.random.default_rng(seed)
     sample = np.sort(rng.choice(g.n_pix, size=min(n_sample, g.n_pix), replace=False))
@@ -404,7 +417,9 @@ def cpu_baseline(shapes, g, I_gpu, n_sample, seed=0):
     per_pattern = (t1 - t0) + (t2 - t1) * g.n_pix / len(sample)
     Iref = np.abs(A) ** 2
     err = oracle.relative_l2(I_gpu[sample], Iref) if I_gpu is not None else None
-    return {"value": 1.0 / per_pattern, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    oracle.set_threads(all_threads)
+    return {"value": 1.0 / per_pattern, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"1 pattern: full 128^3 voxelisation + transmission, field at {len(sample)} of "
                       f"{g.n_pix} pixels, time scaled to the whole detector ({t2 - t0:.1f} s of CPU work)"}, err
 
@@ -572,6 +587,18 @@ def main():
                 "frac_of_burst_peak": achieved / float(peaks.get("bf16_tflops", peak)),
                 "useful_single_product_tflops": achieved / products}
 
+    # the voxeliser + scan: ALU-bound (the harmonic radius per voxel); its HBM
+    # writes are the slice operand and the occupancy
+    tc = args.precision.startswith("tc_")
+    nxp, nyp = (g.nx + 15) // 16 * 16, (g.ny + 15) // 16 * 16
+    s_bytes = g.nz * 3 * nxp * nyp * 2 if tc else n_vox * (16 if args.precision == "fp64" else 8)
+    vox_bytes = s_bytes + n_vox * 4
+    vox_s = statistics.mean(vox_ms) / 1e3
+    voxelise = {"bound": "alu", "bytes_written_per_launch": vox_bytes, "achieved_gbs": vox_bytes / vox_s / 1e9,
+                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 0.0)),
+                "frac_of_hbm": vox_bytes / vox_s / 1e9 / float(peaks.get("hbm_gbs", 1.0)),
+                "note": "one spherical-harmonics radius (l <= 8) per voxel; the writes are far below HBM speed"}
+
     # end to end through the C ABI with host memory: voxelise + forward + D2H per pattern
     I_host = torch.empty((B, g.n_pix), dtype=torch.float32, pin_memory=True)
     for s_i, s in enumerate(shapes[:2]):
@@ -601,6 +628,7 @@ def main():
     err_fp32 = None
     if rank == 0 and extras and not args.no_cpu_baseline:
         cpu, err = cpu_baseline(shapes, g, I0, args.cpu_sample_pixels)
+        cpu["one_core"], _ = cpu_baseline(shapes, g, None, max(256, args.cpu_sample_pixels // 32), threads=1)
         _, err_fp32 = cpu_baseline(shapes, g, I0_fp32, 512)
         if plain is not None:
             plain["errors_vs_fp64_oracle"] = plain_config_errors(c1, c2)
@@ -629,6 +657,7 @@ def main():
         "stage_ms": {"voxelise_scan": statistics.mean(vox_ms), "contraction": statistics.mean(fwd_ms)},
         "error_vs_fp64_oracle": {"rel_l2_I": err, "on": "cpu_baseline sample of pattern 0"},
         "roofline": roofline,
+        "voxelise_scan": voxelise,
         "fp32_cuda_core_comparator": fp32,
         "fit_step_96": fit,
         "plain_configs": plain,

@@ -284,6 +284,40 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     return SCATMAN_OK;
 }
 
+// Radius band of a binary harmonics or radii-map shape: every direction's
+// surface radius lies in [band_lo, band_hi], so voxels clearly inside or
+// outside skip the radius evaluation.  Harmonics: per degree l,
+// |sum_m a_lm Y_lm| <= |a_l| sqrt((2l+1)/(4 pi)) (Cauchy-Schwarz with the
+// addition theorem sum_m Y_lm^2 = (2l+1)/(4 pi)), then the clip; radii map:
+// the interpolation stays within the samples' range.
+static void set_radius_band(const scatman_shape *s, ShapeParams *sp) {
+    sp->band_lo = sp->band_hi = 0.f;
+    if (sp->soft) return;
+    double lo = 0.0, hi = 0.0;
+    if (s->kind == SCATMAN_SPHHARM) {
+        double b = 0.0;
+        for (int l = 1; l <= s->lmax; ++l) {
+            double n2 = 0.0;
+            for (int m = -l; m <= l; ++m) n2 += sp->alm[l * l + l + m] * sp->alm[l * l + l + m];
+            b += std::sqrt(n2) * std::sqrt((2.0 * l + 1.0) / (4.0 * kPi));
+        }
+        lo = std::fmin(std::fmax(s->R0 * (1.0 - b), sp->rmin), sp->rmax);
+        hi = std::fmin(std::fmax(s->R0 * (1.0 + b), sp->rmin), sp->rmax);
+    } else if (s->kind == SCATMAN_RADIALMAP) {
+        lo = hi = s->radial_map[0];
+        for (long long k = 1; k < (long long)s->map_ntheta * s->map_nphi; ++k) {
+            lo = std::fmin(lo, s->radial_map[k]);
+            hi = std::fmax(hi, s->radial_map[k]);
+        }
+    } else {
+        return;
+    }
+    // widen by a relative 1e-6 so the FP64 rounding of the radius stays inside
+    sp->band_lo = (float)(lo * (1.0 - 1e-6) - 1e-9);
+    sp->band_hi = (float)(hi * (1.0 + 1e-6) + 1e-9);
+    if (!(sp->band_hi > 0.f)) sp->band_lo = sp->band_hi = 0.f;
+}
+
 // Copies a map shape's arrays to the device (grown buffers owned by the handle)
 // and fills the map fields of the shape parameters.
 static int upload_maps(scatman_handle *h, const scatman_shape *s, ShapeParams *sp) {
@@ -451,6 +485,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     finish_shape_params(&sp);
     int rc = upload_maps(h, s, &sp);
     if (rc) return rc;
+    set_radius_band(s, &sp);
 
     GridParams gp{c.nx, c.ny, c.nz, c.voxel, h->k0, s->delta, s->beta};
     SliceOut so;

@@ -68,6 +68,9 @@ struct ShapeParams {
     const double *mdelta, *mbeta;   // per-cell index, or null
     int varn;                       // 1: voxel-resolved index (s carries (n_v^2 - 1) / nscale)
     double nscale;                  // max |n_v^2 - 1| over the map's cells
+    // binary harmonics / radii map: the surface radius lies in [band_lo, band_hi]
+    // for every direction (band_hi = 0: no band)
+    float band_lo, band_hi;
 };
 
 // Fills the FP32 copies and the harmonic recurrence tables of a ShapeParams

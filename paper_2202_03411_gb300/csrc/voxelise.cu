@@ -2,12 +2,12 @@
 // scan (Block 5 + Block 9, Eq. 8 of arXiv 2202.03411).
 //
 // One CTA owns one x column-plane strip: a fixed x and 32 consecutive y lines.
-// Each warp takes whole lines along z; lane l renders the occupancy of a
-// contiguous run of z values, and the exclusive prefix C_j = sum_{j'<j} chi
-// is formed with a warp-shuffle scan of the lanes' run totals.  The slice
-// strength s_j = chi_j exp(i k0 dz (n-1) C_j) is staged in shared memory as
-// [z][y] and then written out so that consecutive threads store consecutive
-// y -- the contraction's operand rows are y-contiguous.
+// Each warp takes whole lines along z, 32 consecutive z per step (one per
+// lane), and the exclusive prefix C_j = sum_{j'<j} chi is a warp-shuffle scan
+// per step plus the running total of the earlier steps.  The slice strength
+// s_j = chi_j exp(i k0 dz (n-1) C_j) is staged in shared memory and then
+// written out so that consecutive threads store consecutive y -- the
+// contraction's operand rows are y-contiguous.
 #include "internal.cuh"
 #include "shape_device.cuh"
 
@@ -48,110 +48,137 @@ constexpr int kVoxThreads = 256;
 constexpr int kMaxRun = 8;          // z values per lane: nz <= 256
 
 // s_j = chi_j T_j with T_j = exp(i k0 dz (n-1) C_j) = e^{-k0 dz beta C} e^{-i k0 dz delta C}.
-// Pass 1 renders chi into shared memory and sums each lane's run of z;
-// a warp-shuffle scan turns the run totals into exclusive prefixes; pass 2
-// walks the run again to form C_j, T_j and s_j.
+// A warp takes one (x, y) line at a time; its lanes take 32 consecutive z per
+// step, so neighbouring lanes hold neighbouring voxels (and binary shapes can
+// skip the surface radius where the whole step is clearly inside or outside).
+// Pass 1 renders chi into shared memory; pass 2 forms the exclusive prefix
+// C_j with a warp scan per step plus the running total of earlier steps, then
+// T_j and s_j.  Tiles are [line][z] with a padded row, so both the z-walk and
+// the line-fastest output loop are free of bank conflicts.
 template <bool kFp64, typename ScanT, bool kMaps>
-__global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams sp, GridParams gp,
+__global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapeParams sp, GridParams gp,
                                                                     SliceOut out) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int nz = gp.nz;
+    const int zs = nz + 1;                                                    // padded row
     using Cx = typename std::conditional<kFp64, double2, float2>::type;
     using Re = typename std::conditional<kFp64, double, float>::type;
-    Cx *s_tile = reinterpret_cast<Cx *>(smem);                                // [nz][32]
-    float *chi_tile = reinterpret_cast<float *>(smem + sizeof(Cx) * nz * kLinesPerCta);
+    Cx *s_tile = reinterpret_cast<Cx *>(smem);                                // [32][zs]
+    float *chi_tile = reinterpret_cast<float *>(smem + sizeof(Cx) * zs * kLinesPerCta);
 
     const int ix = blockIdx.x;
     const int y0 = blockIdx.y * kLinesPerCta;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int run = (nz + 31) / 32;
+    const int steps = (nz + 31) / 32;
     const ScanT a_att = (ScanT)(gp.k0 * gp.voxel * gp.beta);     // attenuation per unit C
     const ScanT a_ph = (ScanT)(gp.k0 * gp.voxel * gp.delta);     // phase per unit C
-
     const bool varn = kMaps && sp.varn != 0;                      // per-cell index of a volume map
     const ScanT kdz = (ScanT)(gp.k0 * gp.voxel);
     const Re inv_scale = (Re)(1.0 / sp.nscale);
+    // radius band of a binary harmonics or radii-map shape: inside below lo, outside above hi
+    const bool band = !sp.soft && sp.band_hi > 0.f;
+    const float vox = (float)gp.voxel;
+    const float xo = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
+
     for (int yl = warp; yl < kLinesPerCta; yl += kVoxThreads / 32) {
         const int iy = y0 + yl;
         if (iy >= gp.ny) break;
-        const int z0 = lane * run;
-        const int z1 = min(nz, z0 + run);
-        ScanT local = (ScanT)0;
-        ScanT ld = (ScanT)0, lb = (ScanT)0;                        // sums of chi delta_v, chi beta_v
+        const float yo = ((float)iy - 0.5f * (float)(gp.ny - 1)) * vox - sp.cyf;
+        const float r2xy = xo * xo + yo * yo;
+        Cx *srow = s_tile + (size_t)yl * zs;
+        float *crow = chi_tile + (size_t)yl * zs;
+        // pass 1: occupancy (and, with a per-cell index, the cells' delta and beta)
 #pragma unroll 1
-        for (int iz = z0; iz < z1; ++iz) {
-            double c;
-            if (varn) {
-                const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
-                c = (cell >= 0 && sp.vmap[cell] != 0) ? 1.0 : 0.0;
-                if (c != 0.0) {
-                    ld += (ScanT)sp.mdelta[cell];
-                    lb += (ScanT)sp.mbeta[cell];
+        for (int st = 0; st < steps; ++st) {
+            const int iz = 32 * st + lane;
+            double c = 0.0;
+            if (iz < nz) {
+                bool decided = false;
+                if (band) {
+                    // |p| = |d|: the rotation keeps lengths; margins cover FP32 rounding
+                    const float zo = ((float)iz - 0.5f * (float)(nz - 1)) * vox - sp.czf;
+                    const float d = sqrtf(r2xy + zo * zo);
+                    const float m = 1e-3f * vox + 1e-5f * d;
+                    if (d + m < sp.band_lo) {
+                        c = 1.0;
+                        decided = true;
+                    } else if (d - m > sp.band_hi) {
+                        decided = true;
+                    }
                 }
-            } else {
-                c = occupancy<kFp64, kMaps>(sp, gp, ix, iy, iz);
+                if (!decided) {
+                    if (varn) {
+                        const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
+                        c = (cell >= 0 && sp.vmap[cell] != 0) ? 1.0 : 0.0;
+                    } else {
+                        c = occupancy<kFp64, kMaps>(sp, gp, ix, iy, iz);
+                    }
+                }
+                if (kFp64) srow[iz].x = c;                                // exact copy until pass 2
+                crow[iz] = (float)c;
             }
-            if (kFp64) s_tile[iz * kLinesPerCta + yl].x = c;         // exact copy until pass 2
-            chi_tile[iz * kLinesPerCta + yl] = (float)c;
-            local += (ScanT)c;
         }
-        if (varn) {
-            // voxel-resolved index: T_j = exp(i k0 dz sum_{j'<j} chi (n_v - 1)),
-            // s = chi (n_v^2 - 1) T / nscale (Eq. 8-9 with one n per voxel)
-            ScanT id = ld, ib = lb;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const ScanT a = __shfl_up_sync(0xffffffffu, id, o);
-                const ScanT b = __shfl_up_sync(0xffffffffu, ib, o);
-                if (lane >= o) {
-                    id += a;
-                    ib += b;
-                }
-            }
-            ScanT Cd = id - ld, Cb = ib - lb;
+        __syncwarp();
+        // pass 2: exclusive prefix along z, transmission, slice value
+        ScanT carry = (ScanT)0, carry_d = (ScanT)0, carry_b = (ScanT)0;
 #pragma unroll 1
-            for (int iz = z0; iz < z1; ++iz) {
-                const Re chi = kFp64 ? (Re)s_tile[iz * kLinesPerCta + yl].x : (Re)chi_tile[iz * kLinesPerCta + yl];
+        for (int st = 0; st < steps; ++st) {
+            const int iz = 32 * st + lane;
+            const Re chi = iz < nz ? (kFp64 ? (Re)srow[iz].x : (Re)crow[iz]) : (Re)0;
+            if (varn) {
+                // voxel-resolved index: T_j = exp(i k0 dz sum_{j'<j} chi (n_v - 1)),
+                // s = chi (n_v^2 - 1) T / nscale (Eq. 8-9 with one n per voxel)
                 double dl = 0.0, bt = 0.0;
                 if (chi != (Re)0) {
                     const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
                     dl = sp.mdelta[cell];
                     bt = sp.mbeta[cell];
                 }
-                const ScanT mag = exp(-kdz * Cb);
-                ScanT sn, cs;
-                sincos(kdz * Cd, &sn, &cs);
-                const Re sr = (Re)((-2.0 * dl + dl * dl - bt * bt)) * inv_scale;
-                const Re si = (Re)((2.0 * bt - 2.0 * dl * bt)) * inv_scale;
-                const Re tr = (Re)(mag * cs), ti = -(Re)(mag * sn);
-                Cx v;
-                v.x = chi * (sr * tr - si * ti);
-                v.y = chi * (sr * ti + si * tr);
-                s_tile[iz * kLinesPerCta + yl] = v;
-                Cd += (ScanT)(chi * (Re)dl);
-                Cb += (ScanT)(chi * (Re)bt);
-            }
-            continue;
-        }
-        // warp exclusive scan of the lanes' run totals
-        ScanT incl = local;
+                const ScanT ed = (ScanT)(chi * (Re)dl), eb = (ScanT)(chi * (Re)bt);
+                ScanT id = ed, ib = eb;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            ScanT nb = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += nb;
-        }
-        ScanT C = incl - local;
-#pragma unroll 1
-        for (int iz = z0; iz < z1; ++iz) {
-            const Re chi = kFp64 ? (Re)s_tile[iz * kLinesPerCta + yl].x : (Re)chi_tile[iz * kLinesPerCta + yl];
-            const ScanT mag = exp(-a_att * C);
-            ScanT sn, cs;
-            sincos(a_ph * C, &sn, &cs);
-            Cx v;
-            v.x = chi * (Re)(mag * cs);
-            v.y = -chi * (Re)(mag * sn);
-            s_tile[iz * kLinesPerCta + yl] = v;
-            C += (ScanT)chi;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const ScanT a = __shfl_up_sync(0xffffffffu, id, o);
+                    const ScanT b = __shfl_up_sync(0xffffffffu, ib, o);
+                    if (lane >= o) {
+                        id += a;
+                        ib += b;
+                    }
+                }
+                const ScanT Cd = carry_d + id - ed, Cb = carry_b + ib - eb;
+                carry_d += __shfl_sync(0xffffffffu, id, 31);
+                carry_b += __shfl_sync(0xffffffffu, ib, 31);
+                if (iz < nz) {
+                    const ScanT mag = exp(-kdz * Cb);
+                    ScanT sn, cs;
+                    sincos(kdz * Cd, &sn, &cs);
+                    const Re sr = (Re)((-2.0 * dl + dl * dl - bt * bt)) * inv_scale;
+                    const Re si = (Re)((2.0 * bt - 2.0 * dl * bt)) * inv_scale;
+                    const Re tr = (Re)(mag * cs), ti = -(Re)(mag * sn);
+                    Cx v;
+                    v.x = chi * (sr * tr - si * ti);
+                    v.y = chi * (sr * ti + si * tr);
+                    srow[iz] = v;
+                }
+                continue;
+            }
+            ScanT incl = (ScanT)chi;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const ScanT nb = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += nb;
+            }
+            const ScanT C = carry + incl - (ScanT)chi;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+            if (iz < nz) {
+                const ScanT mag = exp(-a_att * C);
+                ScanT sn, cs;
+                sincos(a_ph * C, &sn, &cs);
+                Cx v;
+                v.x = chi * (Re)(mag * cs);
+                v.y = -chi * (Re)(mag * sn);
+                srow[iz] = v;
+            }
         }
     }
     __syncthreads();
@@ -163,7 +190,7 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
         for (int iz = threadIdx.x; iz < nz; iz += kVoxThreads) {
             int lo = kLinesPerCta, hi = -1;
             for (int yl = 0; yl < ny_here; ++yl)
-                if (chi_tile[iz * kLinesPerCta + yl] != 0.f) {
+                if (chi_tile[(size_t)yl * (nz + 1) + iz] != 0.f) {
                     lo = min(lo, yl);
                     hi = yl;
                 }
@@ -179,9 +206,9 @@ __global__ void __launch_bounds__(kVoxThreads) voxelise_scan_kernel(ShapeParams 
         const int iz = it / kLinesPerCta, yl = it % kLinesPerCta;
         if (yl >= ny_here) continue;
         const int iy = y0 + yl;
-        const Cx v = s_tile[iz * kLinesPerCta + yl];
+        const Cx v = s_tile[(size_t)yl * (nz + 1) + iz];
         const long long vidx = iz * nxy + (long long)ix * gp.ny + iy;
-        out.chi[vidx] = chi_tile[iz * kLinesPerCta + yl];
+        out.chi[vidx] = chi_tile[(size_t)yl * (nz + 1) + iz];
         if (out.layout == kLayoutC64) {
             reinterpret_cast<double2 *>(out.s)[vidx] = make_double2((double)v.x, (double)v.y);
         } else if (out.layout == kLayoutC32) {
@@ -223,10 +250,10 @@ cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const S
     if (out.bounds) bounds_init_kernel<<<(4 * gp.nz + 255) / 256, 256, 0, st>>>(out.bounds, gp.nz);
     dim3 grid(gp.nx, (gp.ny + kLinesPerCta - 1) / kLinesPerCta);
     size_t cx = fp64_mode ? sizeof(double2) : sizeof(float2);
-    size_t smem = (cx + sizeof(float)) * (size_t)gp.nz * kLinesPerCta;
+    size_t smem = (cx + sizeof(float)) * (size_t)(gp.nz + 1) * kLinesPerCta;
     // per-function attribute shared by all threads: set it to the largest size
     // (nz = 256) so a concurrent launch from another thread is never rejected
-    const int smem_max = (int)((cx + sizeof(float)) * 32 * kMaxRun * kLinesPerCta);
+    const int smem_max = (int)((cx + sizeof(float)) * (32 * kMaxRun + 1) * kLinesPerCta);
     const bool maps = sp.kind == SCATMAN_RADIALMAP || sp.kind == SCATMAN_VOLUMEMAP;
     auto k = fp64_mode   ? (maps ? voxelise_scan_kernel<true, double, true> : voxelise_scan_kernel<true, double, false>)
              : scan_fp64 ? (maps ? voxelise_scan_kernel<false, double, true> : voxelise_scan_kernel<false, double, false>)
