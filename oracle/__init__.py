@@ -76,6 +76,11 @@ def _load():
                                         ctypes.c_double, _D, _D]
         lib.orc_slices_n.argtypes = [_D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, _D, _D]
+        lib.orc_pixel_solid_angle.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, _D]
+        lib.orc_philox.argtypes = [ctypes.c_uint] * 6 + [ctypes.POINTER(ctypes.c_uint)]
+        lib.orc_photon_counts.argtypes = [_D, _D, ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_ulonglong, _D, ctypes.POINTER(ctypes.c_longlong)]
         lib.orc_msft.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                  _D, ctypes.c_long, _D, _D]
         lib.orc_intensity.argtypes = [_D, _D, ctypes.c_long, _D]
@@ -264,6 +269,33 @@ def gradient(shape: Shape, g: Geometry, dLdI: np.ndarray, A: np.ndarray,
     lib.orc_gradient(ctypes.byref(st), g.nx, g.ny, g.nz, g.voxel, g.wavelength, width, _p(q),
                      q.shape[0], _p(dl), _p(ar), _p(ai), _p(out))
     return out
+
+
+def pixel_solid_angle(g: Geometry) -> np.ndarray:
+    """Solid angle of every pixel: the flat detector or the uniform-q one."""
+    out = np.zeros(g.n_pix)
+    _load().orc_pixel_solid_angle(g.det_nx, g.det_ny, g.theta_max_deg, g.wavelength,
+                                  int(getattr(g, "detector", 0) == 1), _p(out))
+    return out
+
+
+def philox(counter, key) -> np.ndarray:
+    """Philox-4x32-10 block for a 4-word counter and a 2-word key."""
+    out = (ctypes.c_uint * 4)()
+    _load().orc_philox(*[int(c) & 0xFFFFFFFF for c in counter], *[int(k) & 0xFFFFFFFF for k in key], out)
+    return np.array(list(out), dtype=np.uint64)
+
+
+def photon_counts(I: np.ndarray, g: Geometry, photon_density: float, seed: int, counts: bool = True):
+    """Ideal detector: expected photons per pixel and Poisson counts."""
+    I = np.ascontiguousarray(I, dtype=np.float64)
+    dom = pixel_solid_angle(g)
+    lam = np.zeros(I.shape[0])
+    cnt = np.zeros(I.shape[0], dtype=np.int64) if counts else None
+    _load().orc_photon_counts(_p(I), _p(dom), I.shape[0], photon_density, g.wavelength, g.voxel,
+                              int(seed) & 0xFFFFFFFFFFFFFFFF, _p(lam),
+                              cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)) if counts else None)
+    return lam, cnt
 
 
 def relative_l2(x: np.ndarray, ref: np.ndarray) -> float:

@@ -716,3 +716,140 @@ int orc_gradient(const orc_shape *sh, int nx, int ny, int nz, double voxel, doub
     free(S_im);
     return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * The Ideal detector (Sec. 5.2, Listing 2 and its description): a perfect
+ * detector still counts photons, so the simulated pattern is turned into an
+ * expected number of scattered photons per pixel and then into Poisson
+ * counts.  The paper's normalisation is in its (unavailable) supplement;
+ * reading:
+ *   lambda_p = F (k0^2 v / (4 pi))^2 I_p dOmega_p,
+ * F the incident photon density (photons per length^2), v = voxel^3 (the
+ * volume element of Eq. 1's integral, which the prefactor-1 field omits),
+ * I_p = |A_p|^2, dOmega_p the pixel's solid angle: a flat pixel of area
+ * a = (2 tan(theta_max))^2 / (Nx Ny) at distance 1 subtends a / r^3 with
+ * r^2 = 1 + X^2 + Y^2; a uniform-q pixel of d2q = (2 q_max)^2 / (Nx Ny)
+ * subtends d2q / (k0^2 cos(theta)) (d2q_perp = k0^2 cos(theta) dOmega), zero
+ * where the pixel has no scattering direction.
+ * ------------------------------------------------------------------------ */
+
+/* Solid angle of every detector pixel (flat: uniform_q = 0). */
+void orc_pixel_solid_angle(int det_nx, int det_ny, double theta_max_deg, double wavelength, int uniform_q,
+                           double *domega)
+{
+    double k0 = 2.0 * ORC_PI / wavelength;
+    double th = theta_max_deg * ORC_PI / 180.0;
+    for (int v = 0; v < det_ny; ++v)
+        for (int u = 0; u < det_nx; ++u) {
+            size_t p = (size_t)v * det_nx + u;
+            if (!uniform_q) {
+                double h = tan(th);
+                double X = h * (2.0 * u + 1.0 - det_nx) / det_nx;
+                double Y = h * (2.0 * v + 1.0 - det_ny) / det_ny;
+                double area = (2.0 * h / det_nx) * (2.0 * h / det_ny);
+                double r = sqrt(1.0 + X * X + Y * Y);
+                domega[p] = area / (r * r * r);
+            } else {
+                double qmax = k0 * sin(th);
+                double qx = qmax * (2.0 * u + 1.0 - det_nx) / det_nx;
+                double qy = qmax * (2.0 * v + 1.0 - det_ny) / det_ny;
+                double s2 = (qx * qx + qy * qy) / (k0 * k0);
+                double d2q = (2.0 * qmax / det_nx) * (2.0 * qmax / det_ny);
+                domega[p] = s2 < 1.0 ? d2q / (k0 * k0 * sqrt(1.0 - s2)) : 0.0;
+            }
+        }
+}
+
+/*
+ * Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+ * easy as 1, 2, 3", SC'11): ten rounds of two 32x32 -> 64-bit multiplications
+ * (multipliers 0xD2511F53, 0xCD9E8D57) on a 4-word counter with a 2-word key
+ * bumped by the Weyl constants 0x9E3779B9, 0xBB67AE85 between rounds.
+ */
+static void orc_philox4x32_10(const unsigned ctr[4], const unsigned key[2], unsigned out[4])
+{
+    unsigned x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    unsigned k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        unsigned long long p0 = (unsigned long long)0xD2511F53u * x0;
+        unsigned long long p1 = (unsigned long long)0xCD9E8D57u * x2;
+        unsigned y0 = (unsigned)(p1 >> 32) ^ x1 ^ k0;
+        unsigned y1 = (unsigned)p1;
+        unsigned y2 = (unsigned)(p0 >> 32) ^ x3 ^ k1;
+        unsigned y3 = (unsigned)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+void orc_philox(unsigned c0, unsigned c1, unsigned c2, unsigned c3, unsigned k0, unsigned k1, unsigned *out)
+{
+    unsigned ctr[4] = {c0, c1, c2, c3}, key[2] = {k0, k1};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* Draw d (0, 1, 2, ...) of pixel p: a double in (0, 1) from 53 bits of one
+ * half of Philox block (p, d / 2) under the seed's key. */
+static double orc_uniform(unsigned long long seed, unsigned long long p, unsigned d)
+{
+    unsigned ctr[4] = {(unsigned)p, (unsigned)(p >> 32), d >> 1, 0u};
+    unsigned key[2] = {(unsigned)seed, (unsigned)(seed >> 32)};
+    unsigned o[4];
+    orc_philox4x32_10(ctr, key, o);
+    unsigned hi = (d & 1u) ? o[2] : o[0], lo = (d & 1u) ? o[3] : o[1];
+    unsigned long long bits = ((unsigned long long)hi << 21) ^ (unsigned long long)(lo >> 11);
+    bits &= (1ull << 53) - 1ull;
+    return ((double)bits + 0.5) * (1.0 / 9007199254740992.0);   /* (bits + 1/2) 2^-53 */
+}
+
+/*
+ * One Poisson(lambda) count from pixel p's stream.  lambda < 12: Knuth's
+ * multiplication method (count uniforms until their product drops to
+ * e^-lambda).  lambda >= 12: Hormann's transformed rejection with squeeze
+ * (PTRS; W. Hormann, "The transformed rejection method for generating Poisson
+ * random variables", Insurance: Mathematics and Economics 12 (1993)).
+ */
+static long long orc_poisson(double lambda, unsigned long long seed, unsigned long long p)
+{
+    if (!(lambda > 0.0)) return 0;
+    unsigned d = 0;
+    if (lambda < 12.0) {
+        double L = exp(-lambda), prod = 1.0;
+        long long k = 0;
+        for (;;) {
+            prod *= orc_uniform(seed, p, d++);
+            if (prod <= L) return k;
+            ++k;
+        }
+    }
+    double slam = sqrt(lambda), loglam = log(lambda);
+    double b = 0.931 + 2.53 * slam;
+    double a = -0.059 + 0.02483 * b;
+    double invalpha = 1.1239 + 1.1328 / (b - 3.4);
+    double vr = 0.9277 - 3.6224 / (b - 2.0);
+    for (;;) {
+        double U = orc_uniform(seed, p, d++) - 0.5;
+        double V = orc_uniform(seed, p, d++);
+        double us = 0.5 - fabs(U);
+        long long k = (long long)floor((2.0 * a / us + b) * U + lambda + 0.43);
+        if (us >= 0.07 && V <= vr) return k;
+        if (k < 0 || (us < 0.013 && V > us)) continue;
+        if (log(V) + log(invalpha) - log(a / (us * us) + b) <= -lambda + k * loglam - lgamma(k + 1.0)) return k;
+    }
+}
+
+/* Expected counts and Poisson counts of every pixel (counts may be NULL). */
+void orc_photon_counts(const double *intensity, const double *domega, long n, double photon_density, double wavelength,
+                       double voxel, unsigned long long seed, double *lambda, long long *counts)
+{
+    double k0 = 2.0 * ORC_PI / wavelength;
+    double amp = k0 * k0 * voxel * voxel * voxel / (4.0 * ORC_PI);
+    double scale = photon_density * amp * amp;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long p = 0; p < n; ++p) {
+        lambda[p] = scale * intensity[p] * domega[p];
+        if (counts) counts[p] = orc_poisson(lambda[p], seed, (unsigned long long)p);
+    }
+}
