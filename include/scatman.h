@@ -209,6 +209,27 @@ SCATMAN_API int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev);
 SCATMAN_API int scatman_acquire(scatman_handle *h, const scatman_shape *shape, void *I_host);
 
 /*
+ * The Ideal detector (Sec. 5.2, Listing 2: "photon statistics"): turns an
+ * intensity I (device array from scatman_forward on this handle, n_pix
+ * elements of its element type) into the expected number of scattered photons
+ * per pixel and a Poisson count.  The paper leaves the normalisation to a
+ * supplement; this library reads it as
+ *   lambda_p = photon_density * (k0^2 voxel^3 / (4 pi))^2 * I_p * dOmega_p,
+ * photon_density in photons per squared length unit (the wavelength's),
+ * dOmega_p the pixel's solid angle (flat pixel of area a at distance 1:
+ * a / r^3 with r^2 = 1 + X^2 + Y^2; uniform-q pixel: d2q / (k0^2 cos theta),
+ * 0 without a scattering direction).  Counts are Poisson(lambda_p) draws
+ * from the counter-based generator Philox-4x32-10 keyed by `seed` and counted
+ * by (pixel, draw): the same seed gives the same counts on any launch.
+ *  lambda_dev  optional device array of n_pix doubles (NULL skips it)
+ *  counts_dev  optional device array of n_pix 64-bit counts (NULL skips it)
+ * Asynchronous.  Errors: ERR_ARG (NULL I, both outputs NULL, negative or
+ * non-finite density, a handle built with q_list), ERR_CUDA.
+ */
+SCATMAN_API int scatman_photon_counts(scatman_handle *h, double photon_density, unsigned long long seed,
+                                      const void *I_dev, double *lambda_dev, long long *counts_dev);
+
+/*
  * Gradient of a real loss L(I) with respect to the shape parameters, given
  * dL/dI on every pixel (device array, n_pix elements, same element type as
  * I), for the shape of the last scatman_voxelise and the field of the last

@@ -88,6 +88,8 @@ SIGNATURES = {
     "scatman_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "scatman_acquire": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(scatman_shape), ctypes.c_void_p]),
     "scatman_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _D]),
+    "scatman_photon_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_ulonglong, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
     "scatman_param_count": (ctypes.c_int, [ctypes.c_void_p]),
     "scatman_n_pix": (ctypes.c_longlong, [ctypes.c_void_p]),
     "scatman_elem_size": (ctypes.c_int, [ctypes.c_void_p]),

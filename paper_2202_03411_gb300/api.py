@@ -160,6 +160,21 @@ def scatman_backward(h: Handle, dLdI) -> np.ndarray:
     return out
 
 
+def scatman_photon_counts(h: Handle, photon_density: float, seed: int, I, want_lambda: bool = True,
+                          want_counts: bool = True):
+    """Ideal detector: (expected photons, Poisson counts) as CUDA tensors
+    (float64 and int64); either may be skipped (None)."""
+    import torch
+    n = scatman_n_pix(h)
+    lam = torch.empty(n, dtype=torch.float64, device=I.device) if want_lambda else None
+    cnt = torch.empty(n, dtype=torch.int64, device=I.device) if want_counts else None
+    _check(_lib.load().scatman_photon_counts(
+        h.ptr, float(photon_density), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(I.data_ptr()),
+        ctypes.c_void_p(lam.data_ptr() if lam is not None else None),
+        ctypes.c_void_p(cnt.data_ptr() if cnt is not None else None)), h, "photon counts")
+    return lam, cnt
+
+
 def scatman_param_count(h: Handle) -> int:
     return _lib.load().scatman_param_count(h.ptr)
 

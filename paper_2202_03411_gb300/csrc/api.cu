@@ -164,6 +164,7 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     scatman_handle *h = new (std::nothrow) scatman_handle();
     if (!h) return SCATMAN_ERR_OOM;
     h->cfg = *cfg;
+    h->from_q_list = cfg->q_list != nullptr;
     h->cfg.q_list = nullptr;
     g_create_error.clear();
     auto fail = [&](int code) {
@@ -660,6 +661,19 @@ int scatman_get_q(scatman_handle *h, double *q_host) {
                         "q download");
     if (rc) return rc;
     return scatman_sync(h);
+}
+
+int scatman_photon_counts(scatman_handle *h, double photon_density, unsigned long long seed, const void *I_dev,
+                          double *lambda_dev, long long *counts_dev) {
+    if (!h || !I_dev || (!lambda_dev && !counts_dev)) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
+    if (!(photon_density >= 0.0) || !std::isfinite(photon_density))
+        return set_error(h, SCATMAN_ERR_ARG, "photon density must be finite and >= 0");
+    const scatman_config &c = h->cfg;
+    if (h->from_q_list) return set_error(h, SCATMAN_ERR_ARG, "photon counts need the detector's pixels (no q_list)");
+    return check_cuda(h, launch_photon_counts(I_dev, h->precision == SCATMAN_FP64, h->n_pix, c.det_nx, c.det_ny,
+                                              h->uniform_q, c.theta_max_deg, c.wavelength, c.voxel, photon_density,
+                                              seed, lambda_dev, counts_dev, h->stream),
+                      "photon counts");
 }
 
 int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams) {

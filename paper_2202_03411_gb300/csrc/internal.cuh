@@ -148,6 +148,7 @@ struct scatman_handle {
     void *d_partial = nullptr;      // CUDA-core contraction: per-split partial fields
     void *d_H = nullptr;            // uniform-q detector: y-contracted slices [v][z][x]
     bool uniform_q = false;
+    bool from_q_list = false;       // q given by the caller: no pixel geometry
     float2 *d_adj_part = nullptr;   // tensor-core adjoint: per-pixel-range partial fields
     size_t adj_part_count = 0;
     unsigned *d_gmax = nullptr;     // tensor-core adjoint: max |w A| (float bits)
@@ -208,6 +209,10 @@ cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix,
 // Real flops one contraction launch issues for the given per-slice boxes.
 double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
 bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why);
+// Ideal detector (detector.cu): expected photons and Poisson counts per pixel.
+cudaError_t launch_photon_counts(const void *I, bool fp64, long long n, int det_nx, int det_ny, bool uniform,
+                                 double theta_max_deg, double wavelength, double voxel, double photon_density,
+                                 uint64_t seed, double *lambda, long long *counts, cudaStream_t st);
 // Backward (adjoint.cu).
 cudaError_t launch_adjoint_field(bool fp64, const void *A, const void *dLdI, const double *q, long long n_pix,
                                  int nx, int ny, int nz, double voxel, void *S, cudaStream_t st);

@@ -1,0 +1,85 @@
+"""The Ideal detector on the GPU against the FP64 oracle: expected photons to
+rounding, Poisson counts bit for bit (both sides implement Philox-4x32-10 and
+the same Poisson method in FP64 with the same operation order)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import SPHHARM, Geometry, Shape, random_alm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _pattern(g, prec):
+    import torch
+    import paper_2202_03411_gb300 as sm
+    rng = np.random.default_rng(8)
+    shape = Shape(SPHHARM, R0=7.0, lmax=4, alm=random_alm(rng, 4), delta=0.02, beta=0.004, latitude=20,
+                  longitude=10, rotation=30)
+    h = sm.scatman_create(g, prec)
+    I = torch.empty(g.n_pix, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+    sm.scatman_voxelise(h, shape)
+    sm.scatman_forward(h, I)
+    return h, I
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tc_bf16_split"])
+@pytest.mark.parametrize("detector", [0, 1])
+@pytest.mark.parametrize("density", [1e-2, 50.0, 1e5])
+def test_photon_counts_match_oracle(prec, detector, density):
+    import paper_2202_03411_gb300 as sm
+    if detector == 1 and prec.startswith("tc"):
+        pytest.skip("the uniform-q detector runs in the CUDA-core modes")
+    g = Geometry(24, 24, 24, 1.0, 8.0, 40.0, 96, 80, detector)
+    h, I = _pattern(g, prec)
+    lam, cnt = sm.scatman_photon_counts(h, density, 12345, I)
+    sm.scatman_sync(h)
+    I_host = I.double().cpu().numpy()
+    lam_ref, cnt_ref = oracle.photon_counts(I_host, g, density, 12345)
+    np.testing.assert_array_equal(lam.cpu().numpy(), lam_ref)
+    np.testing.assert_array_equal(cnt.cpu().numpy(), cnt_ref)
+    assert cnt_ref.sum() > 0 or density < 1
+    h.close()
+
+
+def test_counts_are_reproducible_and_seeded():
+    import paper_2202_03411_gb300 as sm
+    g = Geometry(24, 24, 24, 1.0, 8.0, 40.0, 64, 64)
+    h, I = _pattern(g, "fp32")
+    _, c1 = sm.scatman_photon_counts(h, 1e4, 1, I, want_lambda=False)
+    _, c2 = sm.scatman_photon_counts(h, 1e4, 1, I, want_lambda=False)
+    _, c3 = sm.scatman_photon_counts(h, 1e4, 2, I, want_lambda=False)
+    sm.scatman_sync(h)
+    assert np.array_equal(c1.cpu().numpy(), c2.cpu().numpy())
+    assert not np.array_equal(c1.cpu().numpy(), c3.cpu().numpy())
+    h.close()
+
+
+def test_photon_counts_argument_checks():
+    import torch
+    import paper_2202_03411_gb300 as sm
+    from paper_2202_03411_gb300.api import ScatmanError
+    g = Geometry(16, 16, 16, 1.0, 8.0, 40.0, 32, 32)
+    h, I = _pattern(g, "fp32")
+    with pytest.raises(ScatmanError):
+        sm.scatman_photon_counts(h, -1.0, 0, I)
+    with pytest.raises(ScatmanError):
+        sm.scatman_photon_counts(h, math.inf, 0, I)
+    h.close()
+    q = np.zeros((10, 3))
+    hq = sm.scatman_create(g, "fp32", q_list=q)
+    Iq = torch.zeros(10, dtype=torch.float32, device="cuda")
+    with pytest.raises(ScatmanError):
+        sm.scatman_photon_counts(hq, 1.0, 0, Iq)
+    hq.close()
