@@ -258,6 +258,30 @@ def map_config_errors(refs, n_sample=1024):
     return errs
 
 
+def detector_run(g, I, reps=20, photon_density=1e3):
+    """Ideal detector (Sec. 5.2, photon statistics) on the bench pattern: the
+    launch that turns I into expected photons and Poisson counts."""
+    import torch
+    import paper_2202_03411_gb300 as sm
+    h = sm.scatman_create(g, "tc_bf16_split")
+    lam, cnt = sm.scatman_photon_counts(h, photon_density, 0, I)
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(reps):
+        sm.scatman_photon_counts(h, photon_density, k, I)
+    e1.record(stream)
+    sm.scatman_sync(h)
+    ms = e0.elapsed_time(e1) / reps
+    out = {"photon_density_per_length2": photon_density, "us_per_pattern": 1e3 * ms,
+           "expected_photons": float(lam.sum().item()), "counted_photons": int(cnt.sum().item()),
+           "note": "expected photons per pixel from the pixel solid angle and the cross-section; Poisson counts "
+                   "from Philox-4x32-10 (FP64)"}
+    h.close()
+    return out
+
+
 def fig8b_run(radii=(3.0, 5.0, 10.0, 20.0), dets=(256, 512, 1024, 2048), precision="fp32", reps=5):
     """Sec. 6 timing study (Fig. 8b): the Listing-2 harmonics shape scaled to a mean
     radius of 3/5/10/20 wavelengths on the paper's uniform-q virtual detector of
@@ -623,6 +647,7 @@ def main():
     plain, c1, c2 = plain_configs() if extras else (None, None, None)
     fig8b = fig8b_run() if extras else None
     maps, map_refs = map_configs(args.precision) if extras else (None, None)
+    detector = detector_run(g, I_all[0]) if extras else None
     cpu = None
     err = None
     err_fp32 = None
@@ -663,6 +688,7 @@ def main():
         "plain_configs": plain,
         "fig8b_uniform_q": fig8b,
         "map_shapes_96": maps,
+        "ideal_detector": detector,
         "serving_short": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
