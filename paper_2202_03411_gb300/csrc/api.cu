@@ -143,6 +143,7 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_S);
     cudaFree(h->d_partial);
     cudaFree(h->d_H);
+    cudaFree(h->d_uq_qz);
     cudaFree(h->d_adj_part);
     cudaFree(h->d_gmax);
     cudaFree(h->d_adj_tab);
@@ -193,12 +194,18 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if (c.detector != SCATMAN_DETECTOR_FLAT && c.detector != SCATMAN_DETECTOR_UNIFORM_Q)
         return fail(set_error(h, SCATMAN_ERR_ARG, "unknown detector"));
     h->uniform_q = c.detector == SCATMAN_DETECTOR_UNIFORM_Q && !cfg->q_list;
-    if (h->uniform_q && (c.precision != SCATMAN_FP32 && c.precision != SCATMAN_FP64))
-        return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector runs in SCATMAN_FP32 or SCATMAN_FP64"));
     if (h->uniform_q && c.nz > 128)
         return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector supports nz <= 128"));
     h->precision = c.precision;
-    h->tensor_core = is_tc(c.precision);
+    // The uniform-q detector keeps FP32 slices (its y sum runs on the CUDA
+    // cores); in the tensor-core modes its x/z sum runs on the tensor cores.
+    h->uniform_tc = h->uniform_q && is_tc(c.precision);
+    h->tensor_core = is_tc(c.precision) && !h->uniform_q;
+    if (h->uniform_tc) {
+        uq_tc_geometry(c.nx, c.nz, &h->uq_Kx, &h->uq_Jp, &h->uq_Rg);
+        if (c.nx > 128)
+            return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector's tensor-core modes support nx <= 128"));
+    }
     h->split = (c.precision == SCATMAN_TC_F16_SPLIT || c.precision == SCATMAN_TC_BF16_SPLIT);
     h->bf16 = (c.precision == SCATMAN_TC_BF16_SPLIT || c.precision == SCATMAN_TC_BF16);
     h->k0 = 2.0 * kPi / c.wavelength;
@@ -252,7 +259,13 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if ((rc = alloc_dev(h, &h->d_A, npix * cx, "field buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, &h->d_I, npix * (f64 ? 8 : 4), "intensity buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, (void **)&h->d_err, sizeof(int), "error word"))) return fail(rc);
-    if (h->uniform_q) {
+    if (h->uniform_tc) {
+        const size_t hb = uq_tc_h_bytes(c.nx, c.nz, c.det_ny);
+        if ((rc = alloc_dev(h, &h->d_H, hb, "y-contracted slices"))) return fail(rc);
+        if ((rc = alloc_dev(h, (void **)&h->d_uq_qz, npix * sizeof(float2), "q_z table"))) return fail(rc);
+        // padding rows (z >= nz) and columns (x >= nx) stay zero for good
+        if ((rc = check_cuda(h, cudaMemsetAsync(h->d_H, 0, hb, h->stream), "memset"))) return fail(rc);
+    } else if (h->uniform_q) {
         if ((rc = alloc_dev(h, &h->d_H, (size_t)c.det_ny * nvox / c.ny * cx, "y-contracted slices"))) return fail(rc);
     } else if (!h->tensor_core) {
         h->splits = simt_splits(h->n_pix, c.nx, c.nz, h->sm_count);
@@ -280,6 +293,13 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
         if (!encode_tmap_B(&h->tmap_B, h->d_s, h->Kp, h->Nxp, c.nz, h->bf16, &why))
             return fail(set_error(h, SCATMAN_ERR_CUDA, why));
         h->have_tmap = true;
+    }
+    if (h->uniform_tc) {
+        std::string why;
+        if (!encode_tmap_uq(&h->tmap_H, h->d_H, c.nx, c.nz, c.det_ny, h->bf16, &why))
+            return fail(set_error(h, SCATMAN_ERR_CUDA, why));
+        if ((rc = check_cuda(h, launch_uq_qz_table(h->d_q, h->n_pix, h->k0, h->d_uq_qz, h->stream), "q_z table")))
+            return fail(rc);
     }
     *out = h;
     return SCATMAN_OK;
@@ -491,7 +511,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     GridParams gp{c.nx, c.ny, c.nz, c.voxel, h->k0, s->delta, s->beta};
     SliceOut so;
     so.layout = h->precision == SCATMAN_FP64 ? kLayoutC64
-                : h->precision == SCATMAN_FP32 ? kLayoutC32
+                : !h->tensor_core ? kLayoutC32
                 : h->bf16 ? kLayoutTcBF16 : kLayoutTcF16;
     so.Nxp = h->Nxp;
     so.Nyp = h->Nyp;
@@ -525,7 +545,14 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
     const scatman_config &c = h->cfg;
     const double str_re = h->str_re, str_im = h->str_im;     // set by voxelise
     cudaError_t e;
-    if (h->uniform_q) {
+    if (h->uniform_tc) {
+        e = launch_uq_y_tc((const float2 *)h->d_s, c.nx, c.ny, c.nz, c.det_ny, c.theta_max_deg, h->k0, c.voxel,
+                           h->bf16, h->uq_Jp, h->uq_Rg, h->uq_Kx, (uint16_t *)h->d_H, h->stream);
+        if (e == cudaSuccess)
+            e = launch_uq_tc(h->tmap_H, h->d_uq_qz, c.nx, c.nz, c.det_nx, c.det_ny, c.theta_max_deg, h->k0, c.voxel,
+                             str_re, str_im, h->split, h->bf16, (float2 *)h->d_A, (float *)I_dev, h->d_err,
+                             h->sm_count, h->stream);
+    } else if (h->uniform_q) {
         e = launch_msft_uniform(h->precision == SCATMAN_FP64, h->d_s, c.nx, c.ny, c.nz, c.det_nx, c.det_ny,
                                 c.theta_max_deg, h->k0, c.voxel, str_re, str_im, h->d_H, h->d_A, I_dev, h->stream);
     } else if (h->tensor_core) {
@@ -616,7 +643,7 @@ int scatman_get_slices(scatman_handle *h, double *s_host) {
     if ((rc = scatman_sync(h))) return rc;
     if (h->precision == SCATMAN_FP64) {
         std::memcpy(s_host, tmp.data(), nvox * sizeof(double2));
-    } else if (h->precision == SCATMAN_FP32) {
+    } else if (!h->tensor_core) {
         const float *f = (const float *)tmp.data();
         for (size_t i = 0; i < 2 * nvox; ++i) s_host[i] = f[i];
     } else {
@@ -638,6 +665,12 @@ int scatman_contraction_flops(scatman_handle *h, double *issued, double *dense) 
     if (!h->have_shape) return set_error(h, SCATMAN_ERR_STATE, "no voxelised shape");
     const scatman_config &c = h->cfg;
     const double dense_pairs = (double)h->n_pix * c.nx * c.ny * c.nz;
+    if (h->uniform_tc) {
+        // the x/z launch only: 8 real flops per (pixel, x, z) term, twice with split phases
+        *dense = 8.0 * (double)h->n_pix * c.nx * c.nz * (h->split ? 2.0 : 1.0);
+        *issued = uq_tc_issued_flops(c.nx, c.nz, c.det_nx, c.det_ny, h->split);
+        return SCATMAN_OK;
+    }
     if (!h->tensor_core) {
         *dense = 8.0 * dense_pairs;
         *issued = *dense;

@@ -146,8 +146,14 @@ struct scatman_handle {
     size_t part_count = 0;
     void *d_S = nullptr;            // backward adjoint field (complex, nvox)
     void *d_partial = nullptr;      // CUDA-core contraction: per-split partial fields
-    void *d_H = nullptr;            // uniform-q detector: y-contracted slices [v][z][x]
+    void *d_H = nullptr;            // uniform-q detector: y-contracted slices [v][z][x], or in the
+                                    // tensor-core modes 16-bit planes [row group][-Im | Re | Im][Rg Jp][Kx]
     bool uniform_q = false;
+    bool uniform_tc = false;        // uniform-q detector with the x/z sum on the tensor cores
+    int uq_Jp = 0, uq_Kx = 0, uq_Rg = 1;   // its operand geometry: nz padded to 16, nx padded to 64,
+                                           // detector rows per GEMM column group
+    float2 *d_uq_qz = nullptr;      // its per-pixel q_z (float pair; marker off the Ewald sphere)
+    CUtensorMap tmap_H;
     bool from_q_list = false;       // q given by the caller: no pixel geometry
     float2 *d_adj_part = nullptr;   // tensor-core adjoint: per-pixel-range partial fields
     size_t adj_part_count = 0;
@@ -195,6 +201,21 @@ cudaError_t launch_detector_q_uniform(int det_nx, int det_ny, double theta_max_d
 cudaError_t launch_msft_uniform(bool fp64, const void *s, int nx, int ny, int nz, int det_nx, int det_ny,
                                 double theta_max_deg, double k0, double voxel, double str_re, double str_im,
                                 void *H, void *A, void *I, cudaStream_t st);
+// Uniform-q detector on the tensor cores (msft_uniform.cu, msft_uniform_tc.cu): U1 with a
+// 16-bit three-plane output, then the x/z contraction by tcgen05.
+// Operand geometry: Kx = nx padded to 64, Jp = nz padded to 16, Rg rows per group.
+void uq_tc_geometry(int nx, int nz, int *Kx, int *Jp, int *Rg);
+size_t uq_tc_h_bytes(int nx, int nz, int det_ny);
+cudaError_t launch_uq_y_tc(const float2 *s, int nx, int ny, int nz, int det_ny, double theta_max_deg, double k0,
+                           double voxel, bool bf16, int Jp, int Rg, int Kx, uint16_t *Ht, cudaStream_t st);
+int uq_tc_slots(int nx, int nz, bool split);
+bool encode_tmap_uq(CUtensorMap *map, void *H, int nx, int nz, int det_ny, bool bf16, std::string *why);
+double uq_tc_issued_flops(int nx, int nz, int det_nx, int det_ny, bool split);
+// q_z per pixel as a float pair with a marker off the Ewald sphere (once per handle).
+cudaError_t launch_uq_qz_table(const double *q, long long n, double k0, float2 *tab, cudaStream_t st);
+cudaError_t launch_uq_tc(const CUtensorMap &map, const float2 *qz, int nx, int nz, int det_nx, int det_ny,
+                         double theta_max_deg, double k0, double voxel, double str_re, double str_im, bool split,
+                         bool bf16, float2 *A, float *I, int *err, int sm_count, cudaStream_t st);
 // CUDA-core contraction (msft_simt.cu).
 int simt_splits(long long n_pix, int nx, int nz, int sm_count);
 cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long long n_pix, int nx, int ny,

@@ -30,6 +30,7 @@
 // releases its tensor memory and returns.
 #include "internal.cuh"
 #include "tc_ptx.cuh"
+#include "tc_tiles.cuh"
 
 #include <cstring>
 
@@ -137,36 +138,6 @@ __global__ void pack_spans_kernel(const int *bounds, int nz, int Nxp, int Nyp, u
 // starts over at offset 0 when it does not fit before the end.
 __device__ __forceinline__ uint32_t ring_start(uint32_t head_off, uint32_t sz, uint32_t ring) {
     return head_off + sz > ring ? 0u : head_off;
-}
-
-// Two values as a packed 16-bit pair (first value in the low half) and the
-// packed pair of their remainders: v = hi + lo to about twice the format's
-// precision.  One packed conversion per pair and part.
-__device__ __forceinline__ void split_pair(float a, float b, int bf16, uint32_t *hi, uint32_t *lo) {
-    if (bf16) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        const float2 back = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(a - back.x, b - back.y);
-        *hi = *reinterpret_cast<const uint32_t *>(&h);
-        *lo = *reinterpret_cast<const uint32_t *>(&l);
-    } else {
-        const __half2 h = __floats2half2_rn(a, b);
-        const float2 back = __half22float2(h);
-        const __half2 l = __floats2half2_rn(a - back.x, b - back.y);
-        *hi = *reinterpret_cast<const uint32_t *>(&h);
-        *lo = *reinterpret_cast<const uint32_t *>(&l);
-    }
-}
-
-// Byte offset of K element k (a multiple of 16) from the start of a 128-row
-// operand made of 64-element K blocks: the descriptor start of that K step.
-__device__ __forceinline__ uint32_t a_k_offset(int k) { return (uint32_t)((k >> 6) * kKBlockBytes + (k & 63) * 2); }
-
-// Byte offset of 16-byte chunk `c` (8 elements) of row `m` in K-block `kb`
-// of a 128-row operand laid out for the 128-byte swizzle.
-__device__ __forceinline__ uint32_t a_chunk_offset(int m, int k) {
-    const int kb = k >> 6, c = (k & 63) >> 3;
-    return (uint32_t)(kb * kKBlockBytes + m * 128 + ((c ^ (m & 7)) << 4));
 }
 
 // Phase operand P[m, k] of one pixel tile (and its low part when split),

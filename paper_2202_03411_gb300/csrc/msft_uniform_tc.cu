@@ -1,0 +1,470 @@
+// msft_uniform_tc.cu -- tensor-core form of the uniform-q detector's x/z sum
+// (the paper's virtual detector, Block 1 and Block 6: q_x depends on the
+// pixel column u only and q_y on the row v only):
+//   G[u, (v, j)] = sum_x e^{-i q_x(u) x} H_v[j, x]          (one complex GEMM over all rows v)
+//   A(u, v)      = (n^2-1) sum_j e^{-i q_z(u,v) z_j} G[u, (v, j)]
+// H_v[j, x] = sum_y e^{-i q_y(v) y} s_j(x, y) comes from the y-contraction
+// (msft_uniform.cu) as 16-bit planes [-Im | Re | Im].  Rows v are grouped
+// Rg at a time (Rg Jp = Jg <= 128 GEMM columns per plane, Jp = nz padded to
+// 16), so each K step of 16 x is two MMAs with N = 2 Jg:
+//   [Re G | Im G] += Er [Hr | Hi] + Ei [-Hi | Hr],
+// with the phase operand [Er | Ei] split hi + lo.  A work unit is a tile of
+// 128 pixel columns u and a run of row groups: its phase operand is built
+// once and serves every group of the run.  Warp roles (320 threads): warps
+// 0-7 build the phase tile and sum the z-phases, warps 0-3 on even groups
+// and 4-7 on odd ones (each warp reads its TMEM lane quarter), warp 8 loads
+// H tiles by TMA, warp 9 issues the MMAs and owns the tensor memory, whose
+// two accumulators alternate between the groups.  Every wait is bounded: on
+// time-out the kernel sets a bit in the error word, drains its own work,
+// releases its tensor memory and returns.
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+#include "tc_tiles.cuh"
+
+#include <cstring>
+
+namespace scm {
+
+constexpr int kUqThreads = 320;
+constexpr int kUqEpiWarps = 8;
+constexpr int kUqEpiThreads = kUqEpiWarps * 32;
+constexpr int kUqProdWarp = 8;
+constexpr int kUqMmaWarp = 9;
+constexpr int kUqMaxSlots = 8;
+constexpr int kUqMaxSmem = 232448;
+constexpr uint32_t kUqOffSphere = 0x7fc00000u;   // q_z table marker of a pixel off the Ewald sphere
+
+struct UqParams {
+    const float2 *qz;           // per pixel (q_z hi, lo); hi = NaN marker off the Ewald sphere
+    int det_nx, det_ny;
+    int nx, nz;
+    int Kx, Jp, Jg;             // x padded to 64, z padded to 16, Rg Jp
+    int n_groups;               // ceil(det_ny / Rg)
+    int nkb;                    // Kx / 64
+    int n_ut, gc, n_units;      // u tiles, groups per unit, units
+    int slots;
+    uint32_t stage_bytes;       // one 64-x block of a group: 3 Jg rows of 128 bytes
+    int split, bf16;
+    uint32_t idesc;             // N = 2 Jg
+    uint32_t tmem_cols;
+    double qmax, voxel;
+    float str_re, str_im;
+    float2 *A;
+    float *I;
+    int *err;
+};
+
+__device__ __forceinline__ double uq_coord(int i, int n, double qmax) {
+    return qmax * (double)(2 * i + 1 - n) / (double)n;
+}
+
+// q_z of every pixel as a float pair, or the off-sphere marker: decided from
+// the detector's stored q with the same FP64 operations that set q_z.
+__global__ void uq_qz_table_kernel(const double *q, long long n, double k0, float2 *tab) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+    const double s2 = __ddiv_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(k0, k0));
+    const float h = (float)qz;
+    tab[p] = s2 <= 1.0 ? make_float2(h, (float)(qz - (double)h)) : make_float2(__uint_as_float(kUqOffSphere), 0.f);
+}
+
+cudaError_t launch_uq_qz_table(const double *q, long long n, double k0, float2 *tab, cudaStream_t st) {
+    uq_qz_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q, n, k0, tab);
+    return cudaGetLastError();
+}
+
+// Phase operand E[m, k] = [cos(q_x x_k) | -sin(q_x x_k)] of pixel column
+// u = u0 + m (zero beyond nx and beyond the detector), hi and lo parts: one
+// reduced sincos per 8 x and FP32 rotations by 1..4 voxels.
+__device__ __forceinline__ void build_uq_phase(const UqParams &P, int u0, uint8_t *sA_hi, uint8_t *sA_lo, int tid) {
+    const int m = tid % kTileRows;
+    const int u = u0 + m;
+    const bool valid = u < P.det_nx;
+    const double qx = valid ? uq_coord(u, P.det_nx, P.qmax) : 0.0;
+    const float qh = (float)qx, ql = (float)(qx - (double)qh);
+    const float xoff = 0.5f * (float)(P.nx - 1), vox = (float)P.voxel;
+    const float2 s1 = expmi_fs(qh, ql, vox);
+    const float2 s2 = cmul(s1, s1), s3 = cmul(s2, s1), s4 = cmul(s2, s2);
+    const int nx8 = P.Kx >> 3;
+#pragma unroll 2
+    for (int x8 = tid / kTileRows; x8 < nx8; x8 += kUqEpiThreads / kTileRows) {
+        const float2 p0 = expmi_fs(qh, ql, ((float)(8 * x8) - xoff) * vox);
+        const float2 p4 = cmul(p0, s4);
+        const float2 phs[8] = {p0, cmul(p0, s1), cmul(p0, s2), cmul(p0, s3),
+                               p4, cmul(p4, s1), cmul(p4, s2), cmul(p4, s3)};
+        uint32_t re_hi[4], im_hi[4], re_lo[4], im_lo[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const int x = 8 * x8 + e;
+            const bool in0 = valid && x < P.nx, in1 = valid && x + 1 < P.nx;
+            split_pair(in0 ? phs[e].x : 0.f, in1 ? phs[e + 1].x : 0.f, P.bf16, &re_hi[e >> 1], &re_lo[e >> 1]);
+            split_pair(in0 ? phs[e].y : 0.f, in1 ? phs[e + 1].y : 0.f, P.bf16, &im_hi[e >> 1], &im_lo[e >> 1]);
+        }
+        const uint32_t o_re = a_chunk_offset(m, 8 * x8);
+        const uint32_t o_im = a_chunk_offset(m, P.Kx + 8 * x8);
+        *reinterpret_cast<uint4 *>(sA_hi + o_re) = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+        *reinterpret_cast<uint4 *>(sA_hi + o_im) = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+        if (P.split) {
+            *reinterpret_cast<uint4 *>(sA_lo + o_re) = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+            *reinterpret_cast<uint4 *>(sA_lo + o_im) = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
+        }
+    }
+}
+
+template <int kR>
+__global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_constant__ CUtensorMap map, const UqParams P) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t a_bytes = (uint32_t)(2 * P.nkb) * kTileKBlockBytes;         // [Er | Ei] over K = 2 Kx
+    uint8_t *sA_hi = base;
+    uint8_t *sA_lo = base + a_bytes;
+    uint8_t *stages = base + (P.split ? 2 : 1) * a_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stages + (size_t)P.slots * P.stage_bytes);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + kUqMaxSlots;
+    uint64_t *tfull = bars + 2 * kUqMaxSlots;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint64_t *a_full = drain + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_full + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.slots; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull[b]), 1);
+            mbar_init(smem_u32(&tempty[b]), kUqEpiWarps / 2);
+        }
+        mbar_init(smem_u32(drain), 1);
+        mbar_init(smem_u32(a_full), kUqEpiThreads);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == kUqMmaWarp) {
+        tmem_alloc(smem_u32(tmem_slot), P.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    uint32_t prod_it = 0;
+
+    if (warp == kUqProdWarp) {
+        // ---------------- TMA producer: every group of every unit, every 64-x block ----------------
+        for (int unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
+            const int gb = (unit / P.n_ut) * P.gc, ge = min(P.n_groups, gb + P.gc);
+            bool ok = true;
+            for (int g = gb; g < ge && ok; ++g)
+                for (int kb = 0; kb < P.nkb; ++kb) {
+                    const uint32_t s = prod_it % P.slots, ph = (prod_it / P.slots) & 1;
+                    if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutProducer)) {
+                        ok = false;
+                        break;
+                    }
+                    if (elect_one()) {
+                        const uint32_t fb = smem_u32(&full[s]);
+                        mbar_arrive_expect_tx(fb, P.stage_bytes);
+                        tma_load_3d(smem_u32(stages + (size_t)s * P.stage_bytes), &map, fb, kb * kTileKBlock, 0, 3 * g);
+                    }
+                    __syncwarp();
+                    ++prod_it;
+                }
+            if (!ok) break;
+        }
+    } else if (warp == kUqMmaWarp) {
+        // ---------------- MMA issuer (warp-wide loop, one elected lane issues) ----------------
+        const uint64_t ahi0 = sw128_desc(smem_u32(sA_hi)), alo0 = sw128_desc(smem_u32(sA_lo));
+        const uint64_t st0 = sw128_desc(smem_u32(stages));
+        uint32_t it = 0, acc_it = 0, tl = 0;
+        bool ok = true;
+        for (int unit = blockIdx.x; unit < P.n_units && ok; unit += gridDim.x, ++tl) {
+            const int gb = (unit / P.n_ut) * P.gc, ge = min(P.n_groups, gb + P.gc);
+            if (!warp_wait(smem_u32(a_full), tl & 1, abort_flag, P.err, kErrTimeoutMma)) break;
+            tc_fence_after();
+            for (int g = gb; g < ge && ok; ++g) {
+                const uint32_t b = acc_it & 1, aph = (acc_it >> 1) & 1;
+                if (!warp_wait(smem_u32(&tempty[b]), aph ^ 1, abort_flag, P.err, kErrTimeoutMma)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem_base + b * (uint32_t)(2 * P.Jg);
+                bool first = true;
+                for (int kb = 0; kb < P.nkb; ++kb) {
+                    const uint32_t s = it % P.slots, ph = (it / P.slots) & 1;
+                    if (!warp_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t w2 = st0 + (uint64_t)(((size_t)s * P.stage_bytes) >> 4);    // rows [0, 2 Jg): [-Hi | Hr]
+                    const uint64_t w1 = w2 + (uint64_t)(((uint32_t)P.Jg * 128u) >> 4);         // rows [Jg, 3 Jg): [Hr | Hi]
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int x0 = kTileKBlock * kb + 16 * kk;
+                        const uint64_t off_r = a_k_offset(x0) >> 4, off_i = a_k_offset(P.Kx + x0) >> 4;
+                        const uint64_t b1 = w1 + (uint64_t)(kk * 2), b2 = w2 + (uint64_t)(kk * 2);
+                        const uint32_t acc0 = first ? 0u : 1u;
+                        if (elect_one()) {
+                            mma_f16(d, ahi0 + off_r, b1, P.idesc, acc0);
+                            mma_f16(d, ahi0 + off_i, b2, P.idesc, 1u);
+                            if (P.split) {
+                                mma_f16(d, alo0 + off_r, b1, P.idesc, 1u);
+                                mma_f16(d, alo0 + off_i, b2, P.idesc, 1u);
+                            }
+                        }
+                        __syncwarp();
+                        first = false;
+                    }
+                    if (elect_one()) mma_commit(smem_u32(&empty[s]));
+                    __syncwarp();
+                    ++it;
+                }
+                if (!ok) break;
+                if (elect_one()) mma_commit(smem_u32(&tfull[b]));
+                __syncwarp();
+                ++acc_it;
+            }
+        }
+    } else {
+        // ---------------- phase tile; z-phase sums, halves on alternate groups ----------------
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = quarter * 32 + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        const float vf = (float)P.voxel;
+        const float zoff = 0.5f * (float)(P.nz - 1);
+        const int cpr = P.Jp >> 4;                     // 16-column chunks per row
+        const float2 str = make_float2(P.str_re, P.str_im);
+        uint32_t git = 0;                              // groups seen by this CTA (both halves count all)
+        for (int unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
+            const int u0 = (unit % P.n_ut) * kTileRows;
+            const int gb = (unit / P.n_ut) * P.gc, ge = min(P.n_groups, gb + P.gc);
+            // Each half has seen the completion of its own last group; after
+            // this barrier every MMA that read the previous phase tile is done.
+            named_bar_sync(kUqEpiThreads);
+            if (!*abort_flag) build_uq_phase(P, u0, sA_hi, sA_lo, threadIdx.x);
+            fence_async_smem();
+            mbar_arrive(smem_u32(a_full));
+            const int u = u0 + m;
+            const bool valid_u = u < P.det_nx;
+            for (int g = gb; g < ge; ++g, ++git) {
+                if ((int)(git & 1) != half) continue;
+                // the rows' q_z before the accumulator wait, so the loads overlap it
+                float2 tq[kR];
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const int v = g * kR + r;
+                    tq[r] = (valid_u && v < P.det_ny) ? P.qz[(long long)v * P.det_nx + u]
+                                                      : make_float2(__uint_as_float(kUqOffSphere), 0.f);
+                }
+                const uint32_t b = git & 1, ph = (git >> 1) & 1;
+                const bool got = mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue);
+                if (!__all_sync(0xffffffffu, got)) continue;
+                tc_fence_after();
+                float2 out[kR];
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const float2 zs = expmi_fs(tq[r].x, tq[r].y, vf);
+                    float2 acc = make_float2(0.f, 0.f);
+                    for (int cc = 0; cc < cpr; ++cc) {
+                        float gr[16], gi[16];
+                        const uint32_t col = b * (uint32_t)(2 * P.Jg) + (uint32_t)(r * P.Jp + 16 * cc);
+                        tmem_ld16(lane_base + col, gr);
+                        tmem_ld16(lane_base + col + (uint32_t)P.Jg, gi);
+                        tmem_ld_wait(gr, gi);
+                        float2 z = expmi_fs(tq[r].x, tq[r].y, ((float)(16 * cc) - zoff) * vf);   // e^{-i q_z z_j}
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            acc.x = fmaf(z.x, gr[k], fmaf(-z.y, gi[k], acc.x));
+                            acc.y = fmaf(z.x, gi[k], fmaf(z.y, gr[k], acc.y));
+                            z = cmul(z, zs);
+                        }
+                    }
+                    out[r] = acc;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+                if (valid_u) {
+#pragma unroll
+                    for (int r = 0; r < kR; ++r) {
+                        const int v = g * kR + r;
+                        if (v >= P.det_ny) break;
+                        // a pixel with no scattering direction has no field
+                        const bool on = __float_as_uint(tq[r].x) != kUqOffSphere;
+                        const float2 a = on ? cmul(str, out[r]) : make_float2(0.f, 0.f);
+                        const long long p = (long long)v * P.det_nx + u;
+                        P.A[p] = a;
+                        P.I[p] = a.x * a.x + a.y * a.y;
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- teardown: no tensor-core or TMA work may be in flight ----
+    __syncthreads();
+    if (*abort_flag) {
+        if (warp == kUqMmaWarp && lane == 0) {
+            mma_commit(smem_u32(drain));
+            volatile int dummy = 0;
+            mbar_wait(smem_u32(drain), 0, &dummy, P.err, kErrTimeoutDrain);
+        }
+        if (warp == kUqProdWarp && lane == 0) {
+            volatile int dummy = 0;
+            const uint32_t first = prod_it > (uint32_t)P.slots ? prod_it - P.slots : 0;
+            for (uint32_t i = first; i < prod_it; ++i)
+                mbar_wait(smem_u32(&full[i % P.slots]), (i / P.slots) & 1, &dummy, P.err, kErrTimeoutDrain);
+        }
+    }
+    __syncthreads();
+    if (warp == kUqMmaWarp) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, P.tmem_cols);
+    }
+}
+
+// ---- host side ----------------------------------------------------------------------
+static size_t uq_a_bytes(int Kx, bool split) { return (size_t)(split ? 2 : 1) * 2 * (Kx / 64) * kTileKBlockBytes; }
+static size_t uq_fixed_bytes() { return 1024 + 256; }
+
+void uq_tc_geometry(int nx, int nz, int *Kx, int *Jp, int *Rg) {
+    *Kx = (nx + 63) / 64 * 64;
+    *Jp = (nz + 15) / 16 * 16;
+    int r = 1;
+    while (r < 8 && 2 * r * *Jp <= 128) r <<= 1;
+    *Rg = r;
+}
+
+// Stage slots beside the phase operand (0 when fewer than two fit).
+int uq_tc_slots(int nx, int nz, bool split) {
+    int Kx, Jp, Rg;
+    uq_tc_geometry(nx, nz, &Kx, &Jp, &Rg);
+    if (Kx > 128 || Jp > 128) return 0;
+    const size_t stage = (size_t)3 * Rg * Jp * 128;
+    const size_t used = uq_a_bytes(Kx, split) + uq_fixed_bytes();
+    if (used + 2 * stage > (size_t)kUqMaxSmem) return 0;
+    const size_t n = ((size_t)kUqMaxSmem - used) / stage;
+    return (int)(n > (size_t)kUqMaxSlots ? kUqMaxSlots : n);
+}
+
+typedef CUresult (*UqEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_tmap_uq(CUtensorMap *map, void *H, int nx, int nz, int det_ny, bool bf16, std::string *why) {
+    static UqEncodeFn fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult qr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &qr);
+        if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !ptr) {
+            *why = "cuTensorMapEncodeTiled is not available from the driver";
+            return false;
+        }
+        fn = reinterpret_cast<UqEncodeFn>(ptr);
+    }
+    int Kx, Jp, Rg;
+    uq_tc_geometry(nx, nz, &Kx, &Jp, &Rg);
+    const int Jg = Rg * Jp, n_groups = (det_ny + Rg - 1) / Rg;
+    std::memset(map, 0, sizeof(CUtensorMap));
+    cuuint64_t dims[3] = {(cuuint64_t)Kx, (cuuint64_t)Jg, (cuuint64_t)3 * n_groups};
+    cuuint64_t strides[2] = {(cuuint64_t)Kx * 2, (cuuint64_t)Jg * Kx * 2};
+    cuuint32_t box[3] = {(cuuint32_t)kTileKBlock, (cuuint32_t)Jg, 3u};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, H, dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
+// Bytes of the y-contracted 16-bit operand: every row group, three planes.
+size_t uq_tc_h_bytes(int nx, int nz, int det_ny) {
+    int Kx, Jp, Rg;
+    uq_tc_geometry(nx, nz, &Kx, &Jp, &Rg);
+    return (size_t)((det_ny + Rg - 1) / Rg) * 3 * Rg * Jp * Kx * 2;
+}
+
+// Real flops the x/z launch issues: per row group and pixel tile, 4 MMAs of
+// 128 x 2 Jg x 16 per K step of 16 x (2 with unsplit phases).
+double uq_tc_issued_flops(int nx, int nz, int det_nx, int det_ny, bool split) {
+    int Kx, Jp, Rg;
+    uq_tc_geometry(nx, nz, &Kx, &Jp, &Rg);
+    const double n_ut = (double)((det_nx + kTileRows - 1) / kTileRows);
+    const double n_groups = (double)((det_ny + Rg - 1) / Rg);
+    return n_ut * n_groups * (Kx / 16) * 2.0 * (split ? 2.0 : 1.0) * 2.0 * kTileRows * (2.0 * Rg * Jp) * 16.0;
+}
+
+cudaError_t launch_uq_tc(const CUtensorMap &map, const float2 *qz, int nx, int nz, int det_nx, int det_ny,
+                         double theta_max_deg, double k0, double voxel, double str_re, double str_im, bool split,
+                         bool bf16, float2 *A, float *I, int *err, int sm_count, cudaStream_t st) {
+    UqParams P;
+    int Rg;
+    uq_tc_geometry(nx, nz, &P.Kx, &P.Jp, &Rg);
+    P.qz = qz;
+    P.det_nx = det_nx;
+    P.det_ny = det_ny;
+    P.nx = nx;
+    P.nz = nz;
+    P.Jg = Rg * P.Jp;
+    P.n_groups = (det_ny + Rg - 1) / Rg;
+    P.nkb = P.Kx / 64;
+    P.slots = uq_tc_slots(nx, nz, split);
+    if (P.slots < 2) return cudaErrorInvalidValue;
+    P.stage_bytes = (uint32_t)(3 * P.Jg * 128);
+    P.n_ut = (det_nx + kTileRows - 1) / kTileRows;
+    // groups per unit: about two units per SM, at most 32 groups per phase tile
+    long long want = ((long long)P.n_ut * P.n_groups + 2LL * sm_count - 1) / (2LL * sm_count);
+    P.gc = (int)(want < 1 ? 1 : want > 32 ? 32 : want);
+    P.n_units = P.n_ut * ((P.n_groups + P.gc - 1) / P.gc);
+    P.split = split ? 1 : 0;
+    P.bf16 = bf16 ? 1 : 0;
+    const uint32_t N = (uint32_t)(2 * P.Jg), M = kTileRows;
+    P.idesc = (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+    uint32_t cols = 32;
+    while (cols < 2 * N) cols <<= 1;
+    P.tmem_cols = cols;
+    P.qmax = k0 * sin(theta_max_deg * kPi / 180.0);
+    P.voxel = voxel;
+    P.str_re = (float)str_re;
+    P.str_im = (float)str_im;
+    P.A = A;
+    P.I = I;
+    P.err = err;
+    const size_t smem = uq_a_bytes(P.Kx, split) + (size_t)P.slots * P.stage_bytes + uq_fixed_bytes();
+    const int grid = P.n_units < sm_count ? P.n_units : sm_count;
+    // per-function attribute shared by every thread of the process: always the maximum
+    cudaError_t e;
+    switch (Rg) {
+    case 8:
+        e = cudaFuncSetAttribute(uq_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUqMaxSmem);
+        if (e == cudaSuccess) uq_tc_kernel<8><<<grid, kUqThreads, smem, st>>>(map, P);
+        break;
+    case 4:
+        e = cudaFuncSetAttribute(uq_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUqMaxSmem);
+        if (e == cudaSuccess) uq_tc_kernel<4><<<grid, kUqThreads, smem, st>>>(map, P);
+        break;
+    case 2:
+        e = cudaFuncSetAttribute(uq_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUqMaxSmem);
+        if (e == cudaSuccess) uq_tc_kernel<2><<<grid, kUqThreads, smem, st>>>(map, P);
+        break;
+    default:
+        e = cudaFuncSetAttribute(uq_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kUqMaxSmem);
+        if (e == cudaSuccess) uq_tc_kernel<1><<<grid, kUqThreads, smem, st>>>(map, P);
+        break;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace scm

@@ -300,7 +300,9 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     const long long npix = c->q_list ? c->n_q : (long long)c->det_nx * c->det_ny;
     if (npix < 1) return -1;
     const bool f64 = c->precision == SCATMAN_FP64;
-    const bool tc = c->precision >= SCATMAN_TC_F16_SPLIT;
+    const bool uniform = !c->q_list && c->detector == SCATMAN_DETECTOR_UNIFORM_Q;
+    // the uniform-q detector keeps FP32 slices and runs its own x/z operand
+    const bool tc = c->precision >= SCATMAN_TC_F16_SPLIT && !uniform;
     const long long cx = f64 ? 16 : 8;
     long long s_bytes;
     if (tc) {
@@ -316,7 +318,14 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     b += round_2mib(s_bytes);                   // slices
     b += round_2mib(npix * cx);                 // field cache
     b += round_2mib(npix * (f64 ? 8 : 4));      // intensity scratch
-    if (!tc) b += round_2mib(64 * npix * cx);   // partial fields (upper bound on splits)
+    if (uniform && c->precision >= SCATMAN_TC_F16_SPLIT) {
+        b += round_2mib((long long)scm::uq_tc_h_bytes(c->nx, c->nz, c->det_ny));   // y-contracted 16-bit planes
+        b += round_2mib(npix * 8);                                                 // q_z table
+    } else if (uniform) {
+        b += round_2mib((long long)c->det_ny * c->nx * c->nz * cx);   // y-contracted slices
+    } else if (!tc) {
+        b += round_2mib(64 * npix * cx);        // partial fields (upper bound on splits)
+    }
     b += round_2mib(nvox * cx);                 // adjoint field (backward)
     if (tc) {
         // adjoint partial fields (<= 8), scale, pixel table, y-phase operand tiles

@@ -67,3 +67,89 @@ def test_uniform_q_gradient_fp32():
     h.close()
     ref = oracle.gradient(s, g, w.double().cpu().numpy(), A, width=0.6)
     assert np.linalg.norm(grad - ref) / np.linalg.norm(ref) < 1e-4
+
+
+TC_PRECISIONS = [("tc_f16_split", 1e-3), ("tc_bf16_split", 1e-3), ("tc_f16", 2e-3), ("tc_bf16", 3e-3)]
+
+
+@pytest.mark.parametrize("prec,tol", TC_PRECISIONS)
+def test_uniform_q_tensor_core_parity(prec, tol):
+    """The x/z sum on the tensor cores: ragged pixel tiles (u), detector rows
+    grouped 8/4/2/1 per GEMM column block with a ragged last group, padded z (16)
+    and x (64) extents, pixels off the Ewald sphere, the largest grid the
+    operand tile holds (nx = nz = 128)."""
+    rng = np.random.default_rng(3)
+    cases = [
+        (Geometry(21, 19, 23, 1.0, 7.0, 30.0, 300, 137, DETECTOR_UNIFORM_Q),
+         Shape(ELLIPSOID, a=7.0, b=5.0, c=9.0, delta=0.02, beta=0.004, latitude=20, longitude=40, rotation=60)),
+        (Geometry(65, 30, 9, 1.0, 6.0, 60.0, 129, 40, DETECTOR_UNIFORM_Q),      # x pads to 128, z to 16
+         Shape(ELLIPSOID, a=28.0, b=12.0, c=4.0, delta=0.01, beta=0.002, latitude=5, longitude=10, rotation=30)),
+        (Geometry(24, 24, 24, 1.0, 5.0, 60.0, 64, 64, DETECTOR_UNIFORM_Q),      # corners off the Ewald sphere
+         Shape(SPHHARM, R0=7.0, lmax=6, alm=random_alm(rng, 6), delta=0.01, beta=0.001, latitude=-10,
+               longitude=80, rotation=200)),
+        (Geometry(30, 26, 40, 1.0, 6.0, 40.0, 150, 51, DETECTOR_UNIFORM_Q),     # z pads to 48: 2 rows per group
+         Shape(ELLIPSOID, a=12.0, b=9.0, c=17.0, delta=0.015, beta=0.002, latitude=-35, longitude=75, rotation=120)),
+        (Geometry(128, 40, 128, 1.0, 12.0, 30.0, 131, 3, DETECTOR_UNIFORM_Q),  # the largest operand tile
+         Shape(ELLIPSOID, a=50.0, b=15.0, c=55.0, delta=0.004, beta=0.0005, latitude=30, longitude=-50, rotation=10)),
+        fig8b_case(3.0, 96),
+    ]
+    for g, s in cases:
+        I, A = run_gpu(g, s, prec)
+        Ir, Ar = oracle_field(g, s)
+        Ar = np.where(oracle.detector_valid(g), Ar, 0.0)
+        Ir = np.abs(Ar) ** 2
+        assert rel_l2(I, Ir) < tol, (prec, g, rel_l2(I, Ir))
+        assert np.all(I[~oracle.detector_valid(g)] == 0.0)
+
+
+def test_uniform_q_tensor_core_gradient():
+    """The backward pass after a tensor-core forward (the adjoint runs in FP32 on the
+    CUDA cores from the tensor-core field)."""
+    import torch
+    import paper_2202_03411_gb300 as sm
+    from workloads import perturbed
+    g = Geometry(18, 18, 18, 1.0, 5.0, 45.0, 30, 30, DETECTOR_UNIFORM_Q)
+    s = Shape(ELLIPSOID, a=6.0, b=4.0, c=7.0, delta=0.03, beta=0.004, latitude=25, longitude=40, rotation=60)
+    t = perturbed(s, np.random.default_rng(1), rel=0.05)
+    target = oracle.forward(t, g, soft=True, width=0.6)[0]
+    _, A = oracle.forward(s, g, soft=True, width=0.6)
+    h = sm.scatman_create(g, "tc_bf16_split", soft=True, soft_width=0.6)
+    I = torch.empty(g.n_pix, dtype=torch.float32, device="cuda")
+    sm.scatman_voxelise(h, s)
+    sm.scatman_forward(h, I)
+    w = 2 * (I - torch.as_tensor(target, dtype=torch.float32, device="cuda"))
+    grad = sm.scatman_backward(h, w)
+    h.close()
+    ref = oracle.gradient(s, g, w.double().cpu().numpy(), A, width=0.6)
+    assert np.linalg.norm(grad - ref) / np.linalg.norm(ref) < 1e-3
+
+
+def test_uniform_q_tensor_core_matches_fp32_on_fig8b_grids():
+    """Fig. 8b grids (harmonics shape at 3 and 10 wavelengths) on a 256^2 detector:
+    tensor-core modes within their tolerance of the FP32 CUDA-core sums."""
+    for R in (3.0, 10.0):
+        g, s = fig8b_case(R, 256)
+        I32, _ = run_gpu(g, s, "fp32")
+        for prec, tol in TC_PRECISIONS:
+            I, _ = run_gpu(g, s, prec)
+            assert rel_l2(I, I32) < tol, (R, prec, rel_l2(I, I32))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tc_bf16_split", "tc_f16"])
+@pytest.mark.parametrize("detector", [0, DETECTOR_UNIFORM_Q])
+def test_footprint_covers_the_handle(prec, detector):
+    """The host-side footprint estimate (used for admission) is at least what a
+    handle allocates after a forward and a backward."""
+    import torch
+    import paper_2202_03411_gb300 as sm
+    from paper_2202_03411_gb300.serving import footprint_bytes
+    g = Geometry(40, 36, 44, 1.0, 6.0, 30.0, 200, 170, detector)
+    s = Shape(ELLIPSOID, a=14.0, b=11.0, c=16.0, delta=0.01, beta=0.001, latitude=10, longitude=20, rotation=30)
+    h = sm.scatman_create(g, prec, soft=True, soft_width=0.6)
+    I = torch.empty(g.n_pix, dtype=torch.float64 if prec == "fp64" else torch.float32, device="cuda")
+    sm.scatman_voxelise(h, s)
+    sm.scatman_forward(h, I)
+    sm.scatman_backward(h, torch.ones_like(I))
+    used = sm.scatman_device_bytes(h)
+    h.close()
+    assert used <= footprint_bytes(g, prec), (used, footprint_bytes(g, prec))
