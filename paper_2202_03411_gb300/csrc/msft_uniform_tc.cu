@@ -8,9 +8,9 @@
 // Rg at a time (Rg Jp = Jg <= 128 GEMM columns per plane, Jp = nz padded to
 // 16), so each K step of 16 x is two MMAs with N = 2 Jg:
 //   [Re G | Im G] += Er [Hr | Hi] + Ei [-Hi | Hr],
-// with the phase operand [Er | Ei] split hi + lo.  A work unit is a tile of
-// 128 pixel columns u and a run of row groups: its phase operand is built
-// once and serves every group of the run.  Warp roles (320 threads): warps
+// with the phase operand [Er | Ei] split hi + lo.  Each CTA takes one
+// contiguous range of (tile of 128 pixel columns u, row group) pairs; a phase
+// operand is built per tile and serves its run of groups.  Warp roles (320 threads): warps
 // 0-7 build the phase tile and sum the z-phases, warps 0-3 on even groups
 // and 4-7 on odd ones (each warp reads its TMEM lane quarter), warp 8 loads
 // H tiles by TMA, warp 9 issues the MMAs and owns the tensor memory, whose
@@ -41,7 +41,7 @@ struct UqParams {
     int Kx, Jp, Jg;             // x padded to 64, z padded to 16, Rg Jp
     int n_groups;               // ceil(det_ny / Rg)
     int nkb;                    // Kx / 64
-    int n_ut, gc, n_units;      // u tiles, groups per unit, units
+    int n_ut;                   // pixel tiles of 128 columns u
     int slots;
     uint32_t stage_bytes;       // one 64-x block of a group: 3 Jg rows of 128 bytes
     int split, bf16;
@@ -56,6 +56,27 @@ struct UqParams {
 
 __device__ __forceinline__ double uq_coord(int i, int n, double qmax) {
     return qmax * (double)(2 * i + 1 - n) / (double)n;
+}
+
+// Work split: the (pixel tile, row group) pairs, tile-major, cut into one
+// contiguous range per CTA (sizes differ by at most one group).  A segment is
+// the part of the range inside one pixel tile: one phase operand serves it.
+struct UqSeg {
+    int tile, gb, ge;
+};
+__device__ __forceinline__ bool uq_next_seg(const UqParams &P, long long &idx, long long hi, UqSeg &s) {
+    if (idx >= hi) return false;
+    s.tile = (int)(idx / P.n_groups);
+    s.gb = (int)(idx - (long long)s.tile * P.n_groups);
+    const long long end = min(hi, (long long)(s.tile + 1) * P.n_groups);
+    s.ge = s.gb + (int)(end - idx);
+    idx = end;
+    return true;
+}
+__device__ __forceinline__ void uq_range(const UqParams &P, long long &lo, long long &hi) {
+    const long long total = (long long)P.n_ut * P.n_groups;
+    lo = total * blockIdx.x / gridDim.x;
+    hi = total * (blockIdx.x + 1) / gridDim.x;
 }
 
 // q_z of every pixel as a float pair, or the off-sphere marker: decided from
@@ -156,11 +177,13 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
     uint32_t prod_it = 0;
 
     if (warp == kUqProdWarp) {
-        // ---------------- TMA producer: every group of every unit, every 64-x block ----------------
-        for (int unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
-            const int gb = (unit / P.n_ut) * P.gc, ge = min(P.n_groups, gb + P.gc);
+        // ---------------- TMA producer: every group of every segment, every 64-x block ----------------
+        long long idx, hi;
+        uq_range(P, idx, hi);
+        UqSeg sg;
+        while (uq_next_seg(P, idx, hi, sg)) {
             bool ok = true;
-            for (int g = gb; g < ge && ok; ++g)
+            for (int g = sg.gb; g < sg.ge && ok; ++g)
                 for (int kb = 0; kb < P.nkb; ++kb) {
                     const uint32_t s = prod_it % P.slots, ph = (prod_it / P.slots) & 1;
                     if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutProducer)) {
@@ -183,11 +206,13 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
         const uint64_t st0 = sw128_desc(smem_u32(stages));
         uint32_t it = 0, acc_it = 0, tl = 0;
         bool ok = true;
-        for (int unit = blockIdx.x; unit < P.n_units && ok; unit += gridDim.x, ++tl) {
-            const int gb = (unit / P.n_ut) * P.gc, ge = min(P.n_groups, gb + P.gc);
+        long long idx, hi;
+        uq_range(P, idx, hi);
+        UqSeg sg;
+        for (; ok && uq_next_seg(P, idx, hi, sg); ++tl) {
             if (!warp_wait(smem_u32(a_full), tl & 1, abort_flag, P.err, kErrTimeoutMma)) break;
             tc_fence_after();
-            for (int g = gb; g < ge && ok; ++g) {
+            for (int g = sg.gb; g < sg.ge && ok; ++g) {
                 const uint32_t b = acc_it & 1, aph = (acc_it >> 1) & 1;
                 if (!warp_wait(smem_u32(&tempty[b]), aph ^ 1, abort_flag, P.err, kErrTimeoutMma)) {
                     ok = false;
@@ -238,13 +263,15 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
         const int m = quarter * 32 + lane;
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         const float vf = (float)P.voxel;
-        const float zoff = 0.5f * (float)(P.nz - 1);
-        const int cpr = P.Jp >> 4;                     // 16-column chunks per row
+        const float z0 = -0.5f * (float)(P.nz - 1) * vf;   // z of slice 0
+        const int cpr = P.Jp >> 4;                         // 16-column chunks per row
         const float2 str = make_float2(P.str_re, P.str_im);
-        uint32_t git = 0;                              // groups seen by this CTA (both halves count all)
-        for (int unit = blockIdx.x; unit < P.n_units; unit += gridDim.x) {
-            const int u0 = (unit % P.n_ut) * kTileRows;
-            const int gb = (unit / P.n_ut) * P.gc, ge = min(P.n_groups, gb + P.gc);
+        uint32_t git = 0;                                  // groups seen by this CTA (both halves count all)
+        long long idx, hi;
+        uq_range(P, idx, hi);
+        UqSeg sg;
+        while (uq_next_seg(P, idx, hi, sg)) {
+            const int u0 = sg.tile * kTileRows;
             // Each half has seen the completion of its own last group; after
             // this barrier every MMA that read the previous phase tile is done.
             named_bar_sync(kUqEpiThreads);
@@ -253,7 +280,7 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
             mbar_arrive(smem_u32(a_full));
             const int u = u0 + m;
             const bool valid_u = u < P.det_nx;
-            for (int g = gb; g < ge; ++g, ++git) {
+            for (int g = sg.gb; g < sg.ge; ++g, ++git) {
                 if ((int)(git & 1) != half) continue;
                 // the rows' q_z before the accumulator wait, so the loads overlap it
                 float2 tq[kR];
@@ -270,23 +297,24 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
                 float2 out[kR];
 #pragma unroll
                 for (int r = 0; r < kR; ++r) {
-                    const float2 zs = expmi_fs(tq[r].x, tq[r].y, vf);
+                    // sum_j e^{-i q_z z_j} G_j = e^{-i q_z z_0} sum_j w^j G_j with w = e^{-i q_z dz},
+                    // the polynomial in w by Horner's rule from the top slice down
+                    const float2 w = expmi_fs(tq[r].x, tq[r].y, vf);
                     float2 acc = make_float2(0.f, 0.f);
-                    for (int cc = 0; cc < cpr; ++cc) {
+                    for (int cc = cpr - 1; cc >= 0; --cc) {
                         float gr[16], gi[16];
                         const uint32_t col = b * (uint32_t)(2 * P.Jg) + (uint32_t)(r * P.Jp + 16 * cc);
                         tmem_ld16(lane_base + col, gr);
                         tmem_ld16(lane_base + col + (uint32_t)P.Jg, gi);
                         tmem_ld_wait(gr, gi);
-                        float2 z = expmi_fs(tq[r].x, tq[r].y, ((float)(16 * cc) - zoff) * vf);   // e^{-i q_z z_j}
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            acc.x = fmaf(z.x, gr[k], fmaf(-z.y, gi[k], acc.x));
-                            acc.y = fmaf(z.x, gi[k], fmaf(z.y, gr[k], acc.y));
-                            z = cmul(z, zs);
+                        for (int k = 15; k >= 0; --k) {
+                            const float ax = acc.x;
+                            acc.x = fmaf(ax, w.x, fmaf(-acc.y, w.y, gr[k]));
+                            acc.y = fmaf(ax, w.y, fmaf(acc.y, w.x, gi[k]));
                         }
                     }
-                    out[r] = acc;
+                    out[r] = cmul(expmi_fs(tq[r].x, tq[r].y, z0), acc);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -423,10 +451,7 @@ cudaError_t launch_uq_tc(const CUtensorMap &map, const float2 *qz, int nx, int n
     if (P.slots < 2) return cudaErrorInvalidValue;
     P.stage_bytes = (uint32_t)(3 * P.Jg * 128);
     P.n_ut = (det_nx + kTileRows - 1) / kTileRows;
-    // groups per unit: about two units per SM, at most 32 groups per phase tile
-    long long want = ((long long)P.n_ut * P.n_groups + 2LL * sm_count - 1) / (2LL * sm_count);
-    P.gc = (int)(want < 1 ? 1 : want > 32 ? 32 : want);
-    P.n_units = P.n_ut * ((P.n_groups + P.gc - 1) / P.gc);
+    const long long total = (long long)P.n_ut * P.n_groups;
     P.split = split ? 1 : 0;
     P.bf16 = bf16 ? 1 : 0;
     const uint32_t N = (uint32_t)(2 * P.Jg), M = kTileRows;
@@ -442,7 +467,7 @@ cudaError_t launch_uq_tc(const CUtensorMap &map, const float2 *qz, int nx, int n
     P.I = I;
     P.err = err;
     const size_t smem = uq_a_bytes(P.Kx, split) + (size_t)P.slots * P.stage_bytes + uq_fixed_bytes();
-    const int grid = P.n_units < sm_count ? P.n_units : sm_count;
+    const int grid = (int)(total < sm_count ? total : sm_count);
     // per-function attribute shared by every thread of the process: always the maximum
     cudaError_t e;
     switch (Rg) {
