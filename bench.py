@@ -282,20 +282,31 @@ def detector_run(g, I, reps=20, photon_density=1e3):
     return out
 
 
-def fig8b_run(radii=(3.0, 5.0, 10.0, 20.0), dets=(256, 512, 1024, 2048), precision="fp32", reps=5):
+def fig8b_run(radii=(3.0, 5.0, 10.0, 20.0), dets=(256, 512, 1024, 2048), precisions=("fp32", "tc_bf16_split"),
+              reps=5):
     """Sec. 6 timing study (Fig. 8b): the Listing-2 harmonics shape scaled to a mean
     radius of 3/5/10/20 wavelengths on the paper's uniform-q virtual detector of
-    256^2 ... 2048^2 pixels at 30 deg (voxel = lambda / (2 sin 30 deg) = lambda)."""
+    256^2 ... 2048^2 pixels at 30 deg (voxel = lambda / (2 sin 30 deg) = lambda).
+    Each precision's ms per pattern (voxelise + forward, p50 of the runs); the
+    tensor-core rows add their rel. L2 difference from the FP32 intensities."""
+    import numpy as np
     from workloads import fig8b_case
     table = []
     for R in radii:
         for det in dets:
             g, shape = fig8b_case(R, det)
-            ms, _ = time_mode(g, [shape], precision, reps=reps)
-            table.append({"radius_lambda": R, "grid": g.nx, "detector": det, "ms_per_pattern": ms,
-                          "patterns_per_s": 1e3 / ms})
-    return {"precision": precision, "detector": "uniform-q (the paper's virtual detector), separable sums",
-            "cases": table}
+            row = {"radius_lambda": R, "grid": g.nx, "detector": det}
+            I32 = None
+            for prec in precisions:
+                ms, I = time_mode(g, [shape], prec, reps=reps)
+                row[prec] = {"ms_per_pattern": ms, "p50_ms": time_mode.last_p50_p99[0], "patterns_per_s": 1e3 / ms}
+                if prec == "fp32":
+                    I32 = I
+                elif I32 is not None:
+                    row[prec]["rel_l2_vs_fp32"] = float(np.linalg.norm(I - I32) / np.linalg.norm(I32))
+            table.append(row)
+    return {"precisions": list(precisions), "detector": "uniform-q (the paper's virtual detector), separable sums; "
+            "tensor-core modes run the x/z sum as one tcgen05 GEMM over all detector rows", "cases": table}
 
 
 def fp32_comparator(g, shapes, n=3):

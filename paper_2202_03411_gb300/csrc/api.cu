@@ -259,10 +259,12 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if ((rc = alloc_dev(h, &h->d_A, npix * cx, "field buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, &h->d_I, npix * (f64 ? 8 : 4), "intensity buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, (void **)&h->d_err, sizeof(int), "error word"))) return fail(rc);
+    if (h->uniform_q && (rc = alloc_dev(h, (void **)&h->d_uq_qz, npix * sizeof(float2), "q_z table")))
+        return fail(rc);
     if (h->uniform_tc) {
         const size_t hb = uq_tc_h_bytes(c.nx, c.nz, c.det_ny);
         if ((rc = alloc_dev(h, &h->d_H, hb, "y-contracted slices"))) return fail(rc);
-        if ((rc = alloc_dev(h, (void **)&h->d_uq_qz, npix * sizeof(float2), "q_z table"))) return fail(rc);
+
         // padding rows (z >= nz) and columns (x >= nx) stay zero for good
         if ((rc = check_cuda(h, cudaMemsetAsync(h->d_H, 0, hb, h->stream), "memset"))) return fail(rc);
     } else if (h->uniform_q) {
@@ -294,12 +296,13 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
             return fail(set_error(h, SCATMAN_ERR_CUDA, why));
         h->have_tmap = true;
     }
+    if (h->uniform_q &&
+        (rc = check_cuda(h, launch_uq_qz_table(h->d_q, h->n_pix, h->k0, h->d_uq_qz, h->stream), "q_z table")))
+        return fail(rc);
     if (h->uniform_tc) {
         std::string why;
         if (!encode_tmap_uq(&h->tmap_H, h->d_H, c.nx, c.nz, c.det_ny, h->bf16, &why))
             return fail(set_error(h, SCATMAN_ERR_CUDA, why));
-        if ((rc = check_cuda(h, launch_uq_qz_table(h->d_q, h->n_pix, h->k0, h->d_uq_qz, h->stream), "q_z table")))
-            return fail(rc);
     }
     *out = h;
     return SCATMAN_OK;
@@ -554,7 +557,8 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
                              h->sm_count, h->stream);
     } else if (h->uniform_q) {
         e = launch_msft_uniform(h->precision == SCATMAN_FP64, h->d_s, c.nx, c.ny, c.nz, c.det_nx, c.det_ny,
-                                c.theta_max_deg, h->k0, c.voxel, str_re, str_im, h->d_H, h->d_A, I_dev, h->stream);
+                                c.theta_max_deg, h->k0, c.voxel, str_re, str_im, h->d_uq_qz, h->d_H, h->d_A, I_dev,
+                                h->stream);
     } else if (h->tensor_core) {
         e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, c.voxel, str_re,
                            str_im, h->split, h->bf16, h->d_bounds, (uint2 *)(h->d_bounds + 4 * c.nz), (float2 *)h->d_A,

@@ -198,9 +198,11 @@ cudaError_t launch_detector_q(int det_nx, int det_ny, double theta_max_deg, doub
 // Uniform-q virtual detector (msft_uniform.cu).
 cudaError_t launch_detector_q_uniform(int det_nx, int det_ny, double theta_max_deg, double k0, double *q,
                                       cudaStream_t st);
+// q_z table marker (a quiet-NaN bit pattern) of a pixel off the Ewald sphere.
+constexpr uint32_t kUqOffSphereBits = 0x7fc00000u;
 cudaError_t launch_msft_uniform(bool fp64, const void *s, int nx, int ny, int nz, int det_nx, int det_ny,
                                 double theta_max_deg, double k0, double voxel, double str_re, double str_im,
-                                void *H, void *A, void *I, cudaStream_t st);
+                                const float2 *qz, void *H, void *A, void *I, cudaStream_t st);
 // Uniform-q detector on the tensor cores (msft_uniform.cu, msft_uniform_tc.cu): U1 with a
 // 16-bit three-plane output, then the x/z contraction by tcgen05.
 // Operand geometry: Kx = nx padded to 64, Jp = nz padded to 16, Rg rows per group.

@@ -32,7 +32,6 @@ constexpr int kUqProdWarp = 8;
 constexpr int kUqMmaWarp = 9;
 constexpr int kUqMaxSlots = 8;
 constexpr int kUqMaxSmem = 232448;
-constexpr uint32_t kUqOffSphere = 0x7fc00000u;   // q_z table marker of a pixel off the Ewald sphere
 
 struct UqParams {
     const float2 *qz;           // per pixel (q_z hi, lo); hi = NaN marker off the Ewald sphere
@@ -77,22 +76,6 @@ __device__ __forceinline__ void uq_range(const UqParams &P, long long &lo, long 
     const long long total = (long long)P.n_ut * P.n_groups;
     lo = total * blockIdx.x / gridDim.x;
     hi = total * (blockIdx.x + 1) / gridDim.x;
-}
-
-// q_z of every pixel as a float pair, or the off-sphere marker: decided from
-// the detector's stored q with the same FP64 operations that set q_z.
-__global__ void uq_qz_table_kernel(const double *q, long long n, double k0, float2 *tab) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
-    const double s2 = __ddiv_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(k0, k0));
-    const float h = (float)qz;
-    tab[p] = s2 <= 1.0 ? make_float2(h, (float)(qz - (double)h)) : make_float2(__uint_as_float(kUqOffSphere), 0.f);
-}
-
-cudaError_t launch_uq_qz_table(const double *q, long long n, double k0, float2 *tab, cudaStream_t st) {
-    uq_qz_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q, n, k0, tab);
-    return cudaGetLastError();
 }
 
 // Phase operand E[m, k] = [cos(q_x x_k) | -sin(q_x x_k)] of pixel column
@@ -288,7 +271,7 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
                 for (int r = 0; r < kR; ++r) {
                     const int v = g * kR + r;
                     tq[r] = (valid_u && v < P.det_ny) ? P.qz[(long long)v * P.det_nx + u]
-                                                      : make_float2(__uint_as_float(kUqOffSphere), 0.f);
+                                                      : make_float2(__uint_as_float(kUqOffSphereBits), 0.f);
                 }
                 const uint32_t b = git & 1, ph = (git >> 1) & 1;
                 const bool got = mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue);
@@ -325,7 +308,7 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
                         const int v = g * kR + r;
                         if (v >= P.det_ny) break;
                         // a pixel with no scattering direction has no field
-                        const bool on = __float_as_uint(tq[r].x) != kUqOffSphere;
+                        const bool on = __float_as_uint(tq[r].x) != kUqOffSphereBits;
                         const float2 a = on ? cmul(str, out[r]) : make_float2(0.f, 0.f);
                         const long long p = (long long)v * P.det_nx + u;
                         P.A[p] = a;

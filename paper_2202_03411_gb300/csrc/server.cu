@@ -323,6 +323,7 @@ long long scatman_footprint_bytes(const scatman_config *c) {
         b += round_2mib(npix * 8);                                                 // q_z table
     } else if (uniform) {
         b += round_2mib((long long)c->det_ny * c->nx * c->nz * cx);   // y-contracted slices
+        b += round_2mib(npix * 8);                                    // q_z table
     } else if (!tc) {
         b += round_2mib(64 * npix * cx);        // partial fields (upper bound on splits)
     }
