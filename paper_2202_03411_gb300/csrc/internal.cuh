@@ -232,6 +232,10 @@ cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix,
 // Real flops one contraction launch issues for the given per-slice boxes.
 double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
 bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why);
+// A 3D tiled tensor map over 16-bit elements with the 128-byte swizzle
+// (dims innermost first; strides of dims 1 and 2 in bytes).
+bool encode_tmap_3d_16bit(CUtensorMap *map, void *base, const uint64_t dims[3], const uint64_t strides[2],
+                          const uint32_t box[3], bool bf16, std::string *why);
 // Ideal detector (detector.cu): expected photons and Poisson counts per pixel.
 cudaError_t launch_photon_counts(const void *I, bool fp64, long long n, int det_nx, int det_ny, bool uniform,
                                  double theta_max_deg, double wavelength, double voxel, double photon_density,

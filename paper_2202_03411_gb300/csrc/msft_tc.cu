@@ -527,9 +527,8 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                   CUtensorMapFloatOOBfill);
 
-// One map per span width: map k-1 copies a box of 64 y x 16k rows x the
-// three planes of one slice.
-bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why) {
+bool encode_tmap_3d_16bit(CUtensorMap *map, void *base, const uint64_t dims[3], const uint64_t strides[2],
+                          const uint32_t box[3], bool bf16, std::string *why) {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         void *ptr = nullptr;
@@ -542,6 +541,24 @@ bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16,
         }
         fn = reinterpret_cast<EncodeTiledFn>(ptr);
     }
+    std::memset(map, 0, sizeof(CUtensorMap));
+    cuuint64_t d[3] = {dims[0], dims[1], dims[2]};
+    cuuint64_t st[2] = {strides[0], strides[1]};
+    cuuint32_t bx[3] = {box[0], box[1], box[2]};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, d, st, bx,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+
+// One map per span width: map k-1 copies a box of 64 y x 16k rows x the
+// three planes of one slice.
+bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why) {
     std::memset(maps, 0, sizeof(TcMaps));
     const int nch = Nxp / 16;
     if (nch < 1 || nch > kTcMaxChunks) {
@@ -549,17 +566,10 @@ bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16,
         return false;
     }
     for (int k = 1; k <= nch; ++k) {
-        cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)Nxp, (cuuint64_t)kPlanes * nz};
-        cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)Nxp * Kp * 2};
-        cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)(16 * k), (cuuint32_t)kPlanes};
-        cuuint32_t estr[3] = {1, 1, 1};
-        CUresult r = fn(&maps->m[k - 1], bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
-                        base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
-            return false;
-        }
+        const uint64_t dims[3] = {(uint64_t)Kp, (uint64_t)Nxp, (uint64_t)kPlanes * nz};
+        const uint64_t strides[2] = {(uint64_t)Kp * 2, (uint64_t)Nxp * Kp * 2};
+        const uint32_t box[3] = {(uint32_t)kBK, (uint32_t)(16 * k), (uint32_t)kPlanes};
+        if (!encode_tmap_3d_16bit(&maps->m[k - 1], base, dims, strides, box, bf16, why)) return false;
     }
     return true;
 }

@@ -21,8 +21,6 @@
 #include "tc_ptx.cuh"
 #include "tc_tiles.cuh"
 
-#include <cstring>
-
 namespace scm {
 
 constexpr int kUqThreads = 320;
@@ -365,38 +363,14 @@ int uq_tc_slots(int nx, int nz, bool split) {
     return (int)(n > (size_t)kUqMaxSlots ? kUqMaxSlots : n);
 }
 
-typedef CUresult (*UqEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                               const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
 bool encode_tmap_uq(CUtensorMap *map, void *H, int nx, int nz, int det_ny, bool bf16, std::string *why) {
-    static UqEncodeFn fn = nullptr;
-    if (!fn) {
-        void *ptr = nullptr;
-        cudaDriverEntryPointQueryResult qr;
-        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &qr);
-        if (e != cudaSuccess || qr != cudaDriverEntryPointSuccess || !ptr) {
-            *why = "cuTensorMapEncodeTiled is not available from the driver";
-            return false;
-        }
-        fn = reinterpret_cast<UqEncodeFn>(ptr);
-    }
     int Kx, Jp, Rg;
     uq_tc_geometry(nx, nz, &Kx, &Jp, &Rg);
     const int Jg = Rg * Jp, n_groups = (det_ny + Rg - 1) / Rg;
-    std::memset(map, 0, sizeof(CUtensorMap));
-    cuuint64_t dims[3] = {(cuuint64_t)Kx, (cuuint64_t)Jg, (cuuint64_t)3 * n_groups};
-    cuuint64_t strides[2] = {(cuuint64_t)Kx * 2, (cuuint64_t)Jg * Kx * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kTileKBlock, (cuuint32_t)Jg, 3u};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, H, dims, strides,
-                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
-        return false;
-    }
-    return true;
+    const uint64_t dims[3] = {(uint64_t)Kx, (uint64_t)Jg, (uint64_t)3 * n_groups};
+    const uint64_t strides[2] = {(uint64_t)Kx * 2, (uint64_t)Jg * Kx * 2};
+    const uint32_t box[3] = {(uint32_t)kTileKBlock, (uint32_t)Jg, 3u};
+    return encode_tmap_3d_16bit(map, H, dims, strides, box, bf16, why);
 }
 
 // Bytes of the y-contracted 16-bit operand: every row group, three planes.
