@@ -144,6 +144,7 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_partial);
     cudaFree(h->d_H);
     cudaFree(h->d_uq_qz);
+    cudaFree(h->d_uq_qrow);
     cudaFree(h->d_adj_part);
     cudaFree(h->d_gmax);
     cudaFree(h->d_adj_tab);
@@ -197,17 +198,16 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if (h->uniform_q && c.nz > 128)
         return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector supports nz <= 128"));
     h->precision = c.precision;
-    // The uniform-q detector keeps FP32 slices (its y sum runs on the CUDA
-    // cores); in the tensor-core modes its x/z sum runs on the tensor cores.
+    // In the tensor-core modes the uniform-q detector runs both of its sums on
+    // the tensor cores: the y sum as the flat contraction kernel in store mode
+    // (FP16 slice and phase operands: |s| <= 1 and |phase| <= 1 fit its range),
+    // the x/z sum in the mode's 16-bit type.
     h->uniform_tc = h->uniform_q && is_tc(c.precision);
-    h->tensor_core = is_tc(c.precision) && !h->uniform_q;
-    if (h->uniform_tc) {
-        uq_tc_geometry(c.nx, c.nz, &h->uq_Kx, &h->uq_Jp, &h->uq_Rg);
-        if (c.nx > 128)
-            return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector's tensor-core modes support nx <= 128"));
-    }
+    h->tensor_core = is_tc(c.precision);
+    if (h->uniform_tc) uq_tc_geometry(c.nx, c.nz, &h->uq_Kx, &h->uq_Jp, &h->uq_Rg);
     h->split = (c.precision == SCATMAN_TC_F16_SPLIT || c.precision == SCATMAN_TC_BF16_SPLIT);
     h->bf16 = (c.precision == SCATMAN_TC_BF16_SPLIT || c.precision == SCATMAN_TC_BF16);
+    h->s_bf16 = h->bf16 && !h->uniform_tc;
     h->k0 = 2.0 * kPi / c.wavelength;
 
     // device
@@ -261,6 +261,9 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if ((rc = alloc_dev(h, (void **)&h->d_err, sizeof(int), "error word"))) return fail(rc);
     if (h->uniform_q && (rc = alloc_dev(h, (void **)&h->d_uq_qz, npix * sizeof(float2), "q_z table")))
         return fail(rc);
+    if (h->uniform_tc &&
+        (rc = alloc_dev(h, (void **)&h->d_uq_qrow, (size_t)c.det_ny * 3 * sizeof(double), "detector row q")))
+        return fail(rc);
     if (h->uniform_tc) {
         const size_t hb = uq_tc_h_bytes(c.nx, c.nz, c.det_ny);
         if ((rc = alloc_dev(h, &h->d_H, hb, "y-contracted slices"))) return fail(rc);
@@ -292,12 +295,18 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     }
     if (h->tensor_core) {
         std::string why;
-        if (!encode_tmap_B(&h->tmap_B, h->d_s, h->Kp, h->Nxp, c.nz, h->bf16, &why))
+        if (!encode_tmap_B(&h->tmap_B, h->d_s, h->Kp, h->Nxp, c.nz, h->s_bf16, &why))
             return fail(set_error(h, SCATMAN_ERR_CUDA, why));
         h->have_tmap = true;
     }
     if (h->uniform_q &&
         (rc = check_cuda(h, launch_uq_qz_table(h->d_q, h->n_pix, h->k0, h->d_uq_qz, h->stream), "q_z table")))
+        return fail(rc);
+    if (h->uniform_tc &&
+        (rc = check_cuda(h, cudaMemcpy2DAsync(h->d_uq_qrow, 3 * sizeof(double), h->d_q,
+                                              (size_t)c.det_nx * 3 * sizeof(double), 3 * sizeof(double), c.det_ny,
+                                              cudaMemcpyDeviceToDevice, h->stream),
+                         "detector row q")))
         return fail(rc);
     if (h->uniform_tc) {
         std::string why;
@@ -515,7 +524,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     SliceOut so;
     so.layout = h->precision == SCATMAN_FP64 ? kLayoutC64
                 : !h->tensor_core ? kLayoutC32
-                : h->bf16 ? kLayoutTcBF16 : kLayoutTcF16;
+                : h->s_bf16 ? kLayoutTcBF16 : kLayoutTcF16;
     so.Nxp = h->Nxp;
     so.Nyp = h->Nyp;
     so.Kp = h->Kp;
@@ -549,8 +558,14 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
     const double str_re = h->str_re, str_im = h->str_im;     // set by voxelise
     cudaError_t e;
     if (h->uniform_tc) {
-        e = launch_uq_y_tc((const float2 *)h->d_s, c.nx, c.ny, c.nz, c.det_ny, c.theta_max_deg, h->k0, c.voxel,
-                           h->bf16, h->uq_Jp, h->uq_Rg, h->uq_Kx, (uint16_t *)h->d_H, h->stream);
+        // the y sum writes only occupied slices and x spans: the rest of H is zero
+        e = cudaMemsetAsync(h->d_H, 0, uq_tc_h_bytes(c.nx, c.nz, c.det_ny), h->stream);
+        if (e == cudaSuccess) {
+            const UqStore store{(uint16_t *)h->d_H, h->uq_Jp, h->uq_Rg, h->uq_Kx, h->bf16};
+            e = launch_uq_y_tc_mma(h->tmap_B, h->d_uq_qrow, c.det_ny, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, c.voxel,
+                                   h->split, h->s_bf16, h->d_bounds, (uint2 *)(h->d_bounds + 4 * c.nz), store,
+                                   h->d_err, h->sm_count, h->stream);
+        }
         if (e == cudaSuccess)
             e = launch_uq_tc(h->tmap_H, h->d_uq_qz, c.nx, c.nz, c.det_nx, c.det_ny, c.theta_max_deg, h->k0, c.voxel,
                              str_re, str_im, h->split, h->bf16, (float2 *)h->d_A, (float *)I_dev, h->d_err,
@@ -657,8 +672,8 @@ int scatman_get_slices(scatman_handle *h, double *s_host) {
                 for (int iy = 0; iy < c.ny; ++iy) {
                     size_t row_r = ((size_t)iz * 3 + 1) * h->Nxp + ix;     // Re plane; Im plane follows
                     size_t v = ((size_t)iz * c.nx + ix) * c.ny + iy;
-                    s_host[2 * v] = half_bits_to_float(B[row_r * h->Kp + iy], h->bf16);
-                    s_host[2 * v + 1] = half_bits_to_float(B[(row_r + h->Nxp) * h->Kp + iy], h->bf16);
+                    s_host[2 * v] = half_bits_to_float(B[row_r * h->Kp + iy], h->s_bf16);
+                    s_host[2 * v + 1] = half_bits_to_float(B[(row_r + h->Nxp) * h->Kp + iy], h->s_bf16);
                 }
     }
     return SCATMAN_OK;

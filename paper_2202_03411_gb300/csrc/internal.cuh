@@ -128,6 +128,7 @@ struct scatman_handle {
     bool tensor_core = false;
     bool split = false;
     bool bf16 = false;
+    bool s_bf16 = false;            // 16-bit type of the tensor-core slice operand
     bool scan_fp64 = false;
     // tensor-core operand geometry
     int Nxp = 0, Nyp = 0, Kp = 0;
@@ -153,6 +154,7 @@ struct scatman_handle {
     int uq_Jp = 0, uq_Kx = 0, uq_Rg = 1;   // its operand geometry: nz padded to 16, nx padded to 64,
                                            // detector rows per GEMM column group
     float2 *d_uq_qz = nullptr;      // its per-pixel q_z (float pair; marker off the Ewald sphere)
+    double *d_uq_qrow = nullptr;    // q of each detector row's first pixel (q_y of the row), tensor-core modes
     CUtensorMap tmap_H;
     bool from_q_list = false;       // q given by the caller: no pixel geometry
     float2 *d_adj_part = nullptr;   // tensor-core adjoint: per-pixel-range partial fields
@@ -203,13 +205,11 @@ constexpr uint32_t kUqOffSphereBits = 0x7fc00000u;
 cudaError_t launch_msft_uniform(bool fp64, const void *s, int nx, int ny, int nz, int det_nx, int det_ny,
                                 double theta_max_deg, double k0, double voxel, double str_re, double str_im,
                                 const float2 *qz, void *H, void *A, void *I, cudaStream_t st);
-// Uniform-q detector on the tensor cores (msft_uniform.cu, msft_uniform_tc.cu): U1 with a
-// 16-bit three-plane output, then the x/z contraction by tcgen05.
+// Uniform-q detector on the tensor cores (msft_tc.cu in store mode for U1,
+// msft_uniform_tc.cu for the x/z contraction).
 // Operand geometry: Kx = nx padded to 64, Jp = nz padded to 16, Rg rows per group.
 void uq_tc_geometry(int nx, int nz, int *Kx, int *Jp, int *Rg);
 size_t uq_tc_h_bytes(int nx, int nz, int det_ny);
-cudaError_t launch_uq_y_tc(const float2 *s, int nx, int ny, int nz, int det_ny, double theta_max_deg, double k0,
-                           double voxel, bool bf16, int Jp, int Rg, int Kx, uint16_t *Ht, cudaStream_t st);
 int uq_tc_slots(int nx, int nz, bool split);
 bool encode_tmap_uq(CUtensorMap *map, void *H, int nx, int nz, int det_ny, bool bf16, std::string *why);
 double uq_tc_issued_flops(int nx, int nz, int det_nx, int det_ny, bool split);
@@ -229,6 +229,17 @@ cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix,
                            int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
                            bool bf16, const int *bounds, uint2 *list, float2 *A, float *I, int *err,
                            int sm_count, cudaStream_t st);
+// The same kernel in store mode, the uniform-q detector's y-contraction on the
+// tensor cores: rows are detector rows v (q_y(v) = qrow[3 v + 1]) and G is
+// written to the x/z operand H as 16-bit planes.
+struct UqStore {
+    uint16_t *Ht;
+    int Jp, Rg, Kx;
+    bool bf16;                  // H's 16-bit type
+};
+cudaError_t launch_uq_y_tc_mma(const TcMaps &maps, const double *qrow, int det_ny, int nx, int ny, int nz, int Nxp,
+                               int Nyp, double voxel, bool split, bool bf16, const int *bounds, uint2 *list,
+                               const UqStore &store, int *err, int sm_count, cudaStream_t st);
 // Real flops one contraction launch issues for the given per-slice boxes.
 double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
 bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why);

@@ -58,6 +58,8 @@ struct TcParams {
     uint32_t ring_bytes;        // slice-stage ring (multiple of 1024)
     int split, bf16;
     int num_m_tiles;
+    int parts, num_units;       // store mode: each pixel tile's slice list cut into `parts` ranges
+                                // (units = tiles x parts); the field sum keeps parts = 1
     uint32_t idesc;             // without the N field (set per slice)
     uint32_t tmem_cols;
     double voxel;
@@ -65,6 +67,11 @@ struct TcParams {
     float2 *A;
     float *I;
     int *err;
+    // store mode (the uniform-q detector's y-contraction): rows m are detector
+    // rows v with q_y(v) = q[3 v + 1]; G is written as 16-bit planes
+    // [-Im | Re | Im] of H at rows (3 (v / h_Rg) + plane) h_Jg + (v % h_Rg) h_Jp + j
+    uint16_t *Ht;
+    int h_Jp, h_Jg, h_Rg, h_Kx, h_bf16;
 };
 
 // Which part of slice t the contraction touches: x chunks [c_lo, c_hi) of 16
@@ -134,6 +141,13 @@ __global__ void pack_spans_kernel(const int *bounds, int nz, int Nxp, int Nyp, u
     if (threadIdx.x == 0) list[0] = make_uint2((uint32_t)s_base, 0u);
 }
 
+// The occupied-slice range [i_lo, i_hi) of work unit u (tile u % num_m_tiles).
+__device__ __forceinline__ void unit_slices(const TcParams &P, int u, int n_occ, int &i_lo, int &i_hi) {
+    const int part = u / P.num_m_tiles;
+    i_lo = (int)((long long)part * n_occ / P.parts);
+    i_hi = (int)((long long)(part + 1) * n_occ / P.parts);
+}
+
 // Placement of a stage of `sz` bytes in the ring: a stage never wraps, it
 // starts over at offset 0 when it does not fit before the end.
 __device__ __forceinline__ uint32_t ring_start(uint32_t head_off, uint32_t sz, uint32_t ring) {
@@ -179,6 +193,7 @@ __device__ __forceinline__ void build_phase_tile(const TcParams &P, double qy, b
     }
 }
 
+template <bool kStoreH>
 __global__ void __launch_bounds__(kTcThreads, 1)
     msft_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -235,12 +250,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         unsigned long long ends[kSlots];            // end of each stage in flight, by slot
         uint32_t head_off = 0;                      // head modulo the ring
         const int n_occ = (int)__ldg(&P.list[0].x);
-        for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x) {
-            uint2 nxt = n_occ > 0 ? __ldg(&P.list[1]) : make_uint2(0u, 0u);
-            for (int i = 0; i < n_occ && ok; ++i) {
+        for (int u = blockIdx.x; u < P.num_units && ok; u += gridDim.x) {
+            int i_lo, i_hi;
+            unit_slices(P, u, n_occ, i_lo, i_hi);
+            uint2 nxt = i_lo < i_hi ? __ldg(&P.list[1 + i_lo]) : make_uint2(0u, 0u);
+            for (int i = i_lo; i < i_hi && ok; ++i) {
                 const int t = (int)nxt.x;
                 const uint32_t w = nxt.y;
-                if (i + 1 < n_occ) nxt = __ldg(&P.list[i + 2]);
+                if (i + 1 < i_hi) nxt = __ldg(&P.list[i + 2]);
                 const int c_lo = (int)(w & 15u), nchunks = (int)((w >> 4) & 15u) - c_lo;
                 const uint32_t kmask = w >> 8;
                 const uint32_t sz = (uint32_t)(kPlanes * 16 * nchunks * 128);
@@ -287,13 +304,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         uint32_t head_off = 0;
         uint32_t tl = 0;
         const int n_occ = (int)__ldg(&P.list[0].x);
-        for (int mt = blockIdx.x; mt < P.num_m_tiles && ok; mt += gridDim.x, ++tl) {
+        for (int u = blockIdx.x; u < P.num_units && ok; u += gridDim.x, ++tl) {
             if (!warp_wait(smem_u32(a_full), tl & 1, abort_flag, P.err, kErrTimeoutMma)) break;
             tc_fence_after();
-            uint2 nxt = n_occ > 0 ? __ldg(&P.list[1]) : make_uint2(0u, 0u);
-            for (int i = 0; i < n_occ && ok; ++i) {
+            int i_lo, i_hi;
+            unit_slices(P, u, n_occ, i_lo, i_hi);
+            uint2 nxt = i_lo < i_hi ? __ldg(&P.list[1 + i_lo]) : make_uint2(0u, 0u);
+            for (int i = i_lo; i < i_hi && ok; ++i) {
                 const uint32_t w = nxt.y;
-                if (i + 1 < n_occ) nxt = __ldg(&P.list[i + 2]);
+                if (i + 1 < i_hi) nxt = __ldg(&P.list[i + 2]);
                 const uint32_t nr = 16u * (((w >> 4) & 15u) - (w & 15u));
                 const uint32_t kmask = w >> 8;
                 const uint32_t sz = (uint32_t)kPlanes * nr * 128u;
@@ -356,6 +375,72 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (elect_one()) mma_commit(smem_u32(&tfull[b]));
                 __syncwarp();
                 ++acc_it;
+            }
+        }
+    } else if constexpr (kStoreH) {
+        // ---------------- phase tile + 16-bit stores of [Re G | Im G] ----------------
+        // Each thread waits for every slice's accumulator, so it has seen the
+        // completion of the previous tile's MMAs before it rebuilds the phase tile.
+        const int quarter = warp & 3, half = warp >> 2;
+        const int m = quarter * 32 + lane;
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        const int n_occ = (int)__ldg(&P.list[0].x);
+        const size_t plane = (size_t)P.h_Jg * P.h_Kx;
+        for (int u = blockIdx.x; u < P.num_units; u += gridDim.x) {
+            const int mt = u % P.num_m_tiles;
+            const long long v = (long long)mt * kBM + m;
+            const bool valid = v < P.n_pix;
+            const double qy = valid ? P.q[3 * v + 1] : 0.0;
+            if (!*abort_flag) build_phase_tile(P, qy, valid, sA_hi, sA_lo, threadIdx.x);
+            fence_async_smem();
+            mbar_arrive(smem_u32(a_full));
+            const long long g = valid ? v / P.h_Rg : 0, r = valid ? v % P.h_Rg : 0;
+            uint16_t *row0 = P.Ht + ((size_t)(3 * g) * P.h_Jg + (size_t)r * P.h_Jp) * P.h_Kx;   // plane 0, slice 0
+            int i_lo, i_hi;
+            unit_slices(P, u, n_occ, i_lo, i_hi);
+            uint2 nxt = i_lo < i_hi ? __ldg(&P.list[1 + i_lo]) : make_uint2(0u, 0u);
+            for (int i = i_lo; i < i_hi; ++i) {
+                const int t = (int)nxt.x;
+                const uint32_t w = nxt.y;
+                if (i + 1 < i_hi) nxt = __ldg(&P.list[i + 2]);
+                const int c_lo = (int)(w & 15u), c_hi = (int)((w >> 4) & 15u);
+                const uint32_t b = epi_it & 1, ph = (epi_it >> 1) & 1;
+                const bool got = mbar_wait(smem_u32(&tfull[b]), ph, abort_flag, P.err, kErrTimeoutEpilogue);
+                if (!__all_sync(0xffffffffu, got)) break;
+                tc_fence_after();
+                const uint32_t nr = 16u * (uint32_t)(c_hi - c_lo);
+#pragma unroll 1
+                for (int c = c_lo + ((c_lo & 1) != half); c < c_hi; c += 2) {
+                    // chunks alternate between the two halves
+                    const uint32_t col = b * (uint32_t)(2 * P.Nxp) + 16u * (uint32_t)(c - c_lo);
+                    float gr[16], gi[16];
+                    tmem_ld16(lane_base + col, gr);
+                    tmem_ld16(lane_base + col + nr, gi);
+                    tmem_ld_wait(gr, gi);
+                    if (valid) {
+                        uint32_t re[8], im[8], mi[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            re[e] = pack_pair(gr[2 * e], gr[2 * e + 1], P.h_bf16);
+                            im[e] = pack_pair(gi[2 * e], gi[2 * e + 1], P.h_bf16);
+                            mi[e] = im[e] ^ 0x80008000u;        // both formats keep the sign in the top bit
+                        }
+                        uint16_t *dst = row0 + (size_t)t * P.h_Kx + 16 * c;
+                        uint4 *d0 = reinterpret_cast<uint4 *>(dst);
+                        uint4 *d1 = reinterpret_cast<uint4 *>(dst + plane);
+                        uint4 *d2 = reinterpret_cast<uint4 *>(dst + 2 * plane);
+                        d0[0] = make_uint4(mi[0], mi[1], mi[2], mi[3]);
+                        d0[1] = make_uint4(mi[4], mi[5], mi[6], mi[7]);
+                        d1[0] = make_uint4(re[0], re[1], re[2], re[3]);
+                        d1[1] = make_uint4(re[4], re[5], re[6], re[7]);
+                        d2[0] = make_uint4(im[0], im[1], im[2], im[3]);
+                        d2[1] = make_uint4(im[4], im[5], im[6], im[7]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+                ++epi_it;
             }
         }
     } else {
@@ -574,10 +659,10 @@ bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16,
     return true;
 }
 
-cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
-                           int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
-                           bool bf16, const int *bounds, uint2 *list, float2 *A, float *I, int *err,
-                           int sm_count, cudaStream_t st) {
+static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz, int Nxp,
+                             int Nyp, double voxel, double str_re, double str_im, bool split, bool bf16,
+                             const int *bounds, uint2 *list, float2 *A, float *I, int *err, int sm_count,
+                             cudaStream_t st, const UqStore *store) {
     TcParams P;
     P.q = q;
     P.list = list;
@@ -595,6 +680,13 @@ cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix,
     P.split = split ? 1 : 0;
     P.bf16 = bf16 ? 1 : 0;
     P.num_m_tiles = (int)((n_pix + kBM - 1) / kBM);
+    // store mode: about one unit per SM (slices are independent there)
+    P.parts = 1;
+    if (store) {
+        const int want = (sm_count + P.num_m_tiles - 1) / P.num_m_tiles;
+        P.parts = want < 1 ? 1 : want > nz ? nz : want;
+    }
+    P.num_units = P.num_m_tiles * P.parts;
     const uint32_t M = kBM;
     P.idesc = (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((M >> 4) << 24);
     uint32_t cols = 32;
@@ -606,17 +698,45 @@ cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix,
     P.A = A;
     P.I = I;
     P.err = err;
+    P.Ht = store ? store->Ht : nullptr;
+    P.h_Jp = store ? store->Jp : 0;
+    P.h_Jg = store ? store->Rg * store->Jp : 0;
+    P.h_Rg = store ? store->Rg : 1;
+    P.h_Kx = store ? store->Kx : 0;
+    P.h_bf16 = store && store->bf16 ? 1 : 0;
+    if (store && (store->Kx < Nxp || store->Kx % 8 != 0 || store->Jp < nz)) return cudaErrorInvalidValue;
     const size_t smem = (size_t)(split ? 2 : 1) * P.nkb_a * kKBlockBytes + ring + tc_fixed_bytes();
     // The attribute is per function and shared by every thread of the process:
     // always raise it to the largest size any launch uses, never to this
     // launch's size, so concurrent launches from other threads stay valid.
-    cudaError_t e = cudaFuncSetAttribute(msft_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaError_t e = store ? cudaFuncSetAttribute(msft_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kMaxSmem)
+                          : cudaFuncSetAttribute(msft_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 kMaxSmem);
     if (e != cudaSuccess) return e;
     pack_spans_kernel<<<1, 256, 0, st>>>(bounds, nz, Nxp, Nyp, list);
-    int grid = P.num_m_tiles < sm_count ? P.num_m_tiles : sm_count;
+    int grid = P.num_units < sm_count ? P.num_units : sm_count;
     if (grid < 1) grid = 1;
-    msft_tc_kernel<<<grid, kTcThreads, smem, st>>>(maps, P);
+    if (store)
+        msft_tc_kernel<true><<<grid, kTcThreads, smem, st>>>(maps, P);
+    else
+        msft_tc_kernel<false><<<grid, kTcThreads, smem, st>>>(maps, P);
     return cudaGetLastError();
+}
+
+cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
+                           int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
+                           bool bf16, const int *bounds, uint2 *list, float2 *A, float *I, int *err,
+                           int sm_count, cudaStream_t st) {
+    return launch_tc(maps, q, n_pix, nx, ny, nz, Nxp, Nyp, voxel, str_re, str_im, split, bf16, bounds, list, A, I,
+                     err, sm_count, st, nullptr);
+}
+
+cudaError_t launch_uq_y_tc_mma(const TcMaps &maps, const double *qrow, int det_ny, int nx, int ny, int nz, int Nxp,
+                               int Nyp, double voxel, bool split, bool bf16, const int *bounds, uint2 *list,
+                               const UqStore &store, int *err, int sm_count, cudaStream_t st) {
+    return launch_tc(maps, qrow, det_ny, nx, ny, nz, Nxp, Nyp, voxel, 1.0, 0.0, split, bf16, bounds, list, nullptr,
+                     nullptr, err, sm_count, st, &store);
 }
 
 }  // namespace scm

@@ -86,15 +86,12 @@ constexpr int kUK = 16;        // K chunk
 
 // U1: H[v][c] = sum_y s[c][y] P(v, y), c = (j, x).  Block tile 64 v x 64 c,
 // thread 4 v x 4 c (c strided by 16 so shared reads are conflict-free).
-// kOut = 0 stores complex H[v][j][x]; kOut = 1 / 2 stores the tensor-core
-// operand of the x/z contraction instead: FP16 / BF16 planes -Im, Re, Im of
-// each group of Rg rows v = Rg g + r, rows (3 g + plane) Rg Jp + r Jp + j,
-// columns x, row pitch Kx.
-template <typename R, int kOut>
+// (In the tensor-core modes this stage runs on the tensor cores instead: the
+// flat contraction kernel in store mode, csrc/msft_tc.cu.)
+template <typename R>
 __global__ void __launch_bounds__(256) uq_y_kernel(const typename UC<R>::T *__restrict__ s, int ny, int ncol,
                                                    int ndv, double qmax, double voxel,
-                                                   typename UC<R>::T *__restrict__ H, int nx, int Jp, int Rg,
-                                                   int Kx, uint16_t *__restrict__ Ht) {
+                                                   typename UC<R>::T *__restrict__ H) {
     using C = typename UC<R>::T;
     __shared__ C Ps[kUK][kUT];
     __shared__ C Ss[kUK][kUT];
@@ -146,26 +143,7 @@ __global__ void __launch_bounds__(256) uq_y_kernel(const typename UC<R>::T *__re
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int c = c0 + tc + 16 * b;
-            if (c >= ncol) continue;
-            if constexpr (kOut == 0) {
-                H[(size_t)v * ncol + c] = acc[a][b];
-            } else {
-                const int j = c / nx, x = c % nx;
-                uint16_t re, im, mim;
-                if constexpr (kOut == 2) {
-                    re = __bfloat16_as_ushort(__float2bfloat16_rn((float)acc[a][b].x));
-                    im = __bfloat16_as_ushort(__float2bfloat16_rn((float)acc[a][b].y));
-                } else {
-                    re = __half_as_ushort(__float2half_rn((float)acc[a][b].x));
-                    im = __half_as_ushort(__float2half_rn((float)acc[a][b].y));
-                }
-                mim = (uint16_t)(im ^ 0x8000u);          // both formats keep the sign in the top bit
-                const size_t Jg = (size_t)Rg * Jp;
-                const size_t row = (size_t)3 * (v / Rg) * Jg + (size_t)(v % Rg) * Jp + j;
-                Ht[row * Kx + x] = mim;
-                Ht[(row + Jg) * Kx + x] = re;
-                Ht[(row + 2 * Jg) * Kx + x] = im;
-            }
+            if (c < ncol) H[(size_t)v * ncol + c] = acc[a][b];
         }
     }
 }
@@ -322,27 +300,12 @@ cudaError_t launch_msft_uniform(bool fp64, const void *s, int nx, int ny, int nz
     if (nz > 128) return cudaErrorInvalidValue;
     const int JP = nz <= 16 ? 1 : nz <= 32 ? 2 : nz <= 64 ? 4 : 8;
     if (fp64) {
-        uq_y_kernel<double, 0><<<g1, 256, 0, st>>>((const double2 *)s, ny, ncol, det_ny, qmax, voxel, (double2 *)H,
-                                                    nx, 0, 1, 0, nullptr);
+        uq_y_kernel<double><<<g1, 256, 0, st>>>((const double2 *)s, ny, ncol, det_ny, qmax, voxel, (double2 *)H);
         launch_uq_xz<double, 8>(JP, g2, st, H, nx, nz, det_nx, det_ny, qmax, k0, voxel, str_re, str_im, qz, A, I);
     } else {
-        uq_y_kernel<float, 0><<<g1, 256, 0, st>>>((const float2 *)s, ny, ncol, det_ny, qmax, voxel, (float2 *)H, nx,
-                                                   0, 1, 0, nullptr);
+        uq_y_kernel<float><<<g1, 256, 0, st>>>((const float2 *)s, ny, ncol, det_ny, qmax, voxel, (float2 *)H);
         launch_uq_xz<float, 16>(JP, g2, st, H, nx, nz, det_nx, det_ny, qmax, k0, voxel, str_re, str_im, qz, A, I);
     }
-    return cudaGetLastError();
-}
-
-// U1 for the tensor-core x/z contraction: FP32 sums, 16-bit three-plane output.
-cudaError_t launch_uq_y_tc(const float2 *s, int nx, int ny, int nz, int det_ny, double theta_max_deg, double k0,
-                           double voxel, bool bf16, int Jp, int Rg, int Kx, uint16_t *Ht, cudaStream_t st) {
-    const double qmax = k0 * sin(theta_max_deg * kPi / 180.0);
-    const int ncol = nx * nz;
-    dim3 g1((ncol + kUT - 1) / kUT, (det_ny + kUT - 1) / kUT);
-    if (bf16)
-        uq_y_kernel<float, 2><<<g1, 256, 0, st>>>(s, ny, ncol, det_ny, qmax, voxel, nullptr, nx, Jp, Rg, Kx, Ht);
-    else
-        uq_y_kernel<float, 1><<<g1, 256, 0, st>>>(s, ny, ncol, det_ny, qmax, voxel, nullptr, nx, Jp, Rg, Kx, Ht);
     return cudaGetLastError();
 }
 

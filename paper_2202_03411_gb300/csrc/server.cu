@@ -301,8 +301,7 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     if (npix < 1) return -1;
     const bool f64 = c->precision == SCATMAN_FP64;
     const bool uniform = !c->q_list && c->detector == SCATMAN_DETECTOR_UNIFORM_Q;
-    // the uniform-q detector keeps FP32 slices and runs its own x/z operand
-    const bool tc = c->precision >= SCATMAN_TC_F16_SPLIT && !uniform;
+    const bool tc = c->precision >= SCATMAN_TC_F16_SPLIT;
     const long long cx = f64 ? 16 : 8;
     long long s_bytes;
     if (tc) {
@@ -321,6 +320,7 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     if (uniform && c->precision >= SCATMAN_TC_F16_SPLIT) {
         b += round_2mib((long long)scm::uq_tc_h_bytes(c->nx, c->nz, c->det_ny));   // y-contracted 16-bit planes
         b += round_2mib(npix * 8);                                                 // q_z table
+        b += round_2mib(24LL * c->det_ny);                                         // detector row q
     } else if (uniform) {
         b += round_2mib((long long)c->det_ny * c->nx * c->nz * cx);   // y-contracted slices
         b += round_2mib(npix * 8);                                    // q_z table

@@ -30,6 +30,16 @@ __device__ __forceinline__ void split_pair(float a, float b, int bf16, uint32_t 
     }
 }
 
+// Two values as one packed 16-bit pair (first value in the low half).
+__device__ __forceinline__ uint32_t pack_pair(float a, float b, int bf16) {
+    if (bf16) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
 // Byte offset of K element k (a multiple of 16) from the start of a 128-row
 // operand made of 64-element K blocks: the descriptor start of that K step.
 __device__ __forceinline__ uint32_t a_k_offset(int k) { return (uint32_t)((k >> 6) * kTileKBlockBytes + (k & 63) * 2); }
