@@ -153,3 +153,21 @@ def test_footprint_covers_the_handle(prec, detector):
     used = sm.scatman_device_bytes(h)
     h.close()
     assert used <= footprint_bytes(g, prec), (used, footprint_bytes(g, prec))
+
+
+@pytest.mark.parametrize("prec,tol", [("tc_bf16_split", 1e-3), ("fp32", 1e-5)])
+def test_uniform_q_fig8b_worst_case_sampled(prec, tol):
+    """Fig. 8b's largest case (harmonics shape at 20 wavelengths, 56^3, 2048^2
+    uniform-q detector) in the configuration the benchmark times: the central
+    pixels plus a uniform sample of the rest against the oracle."""
+    g, s = fig8b_case(20.0, 2048)
+    rng = np.random.default_rng(11)
+    centre = [(g.det_ny // 2 + dv) * g.det_nx + g.det_nx // 2 + du for dv in range(-4, 4) for du in range(-4, 4)]
+    sample = np.unique(np.concatenate([np.array(centre), rng.choice(g.n_pix, size=960, replace=False)]))
+    Ir, Ar = oracle_field(g, s, sample=sample)
+    valid = oracle.detector_valid(g)[sample]
+    Ir = np.where(valid, Ir, 0.0)
+    I, _ = run_gpu(g, s, prec)
+    err = rel_l2(I[sample], Ir)
+    assert err < tol, err
+    assert np.all(I[sample][~valid] == 0.0)
