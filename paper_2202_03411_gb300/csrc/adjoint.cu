@@ -139,6 +139,7 @@ int grad_param_count(const ShapeParams &sp) { return n_geom_params(sp.kind, sp.l
 constexpr int kGradThreads = 256;
 constexpr int kGradMaxRun = 8;
 constexpr int kMaxGeom = (SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1);
+constexpr int kGradWarpSlots = (kMaxGeom + 31) / 32;
 
 int grad_voxel_blocks(const GridParams &gp) {
     long long cols = (long long)gp.nx * gp.ny;
@@ -191,14 +192,23 @@ __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridPara
     chi = (R)1 / ((R)1 + exp(-(rs - rr) * (R)sp.inv_w));
 }
 
-template <typename R>
+// kRun: voxels per lane along z (nz <= 32 kRun), a compile-time bound so the
+// per-lane runs stay in registers.
+template <typename R, int kRun>
 __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp, GridParams gp,
                                                                   const typename Cx<R>::T *__restrict__ S,
                                                                   double *__restrict__ partials) {
     using C = typename Cx<R>::T;
     const int ng = n_geom_params(sp.kind, sp.lmax);
-    R acc[kMaxGeom];
-    for (int k = 0; k < ng; ++k) acc[k] = (R)0;
+    // Sphere / ellipsoid parameters and the harmonics' R0 accumulate per
+    // thread (acc[0..2]); the harmonics' a_lm (index j = l^2 + l + m - 1)
+    // accumulate warp-summed, coefficient j held by lane j % 32 in slot j / 32,
+    // so no per-thread array of (lmax + 1)^2 sums is needed.
+    R acc[3] = {(R)0, (R)0, (R)0};
+    R aw[kGradWarpSlots];
+#pragma unroll
+    for (int k = 0; k < kGradWarpSlots; ++k) aw[k] = (R)0;
+    const bool sh = sp.kind == SCATMAN_SPHHARM;
     C D;
     D.x = D.y = (R)0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -215,12 +225,12 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
     const long long wstride = (long long)gridDim.x * (kGradThreads / 32);
     for (long long col = (long long)blockIdx.x * (kGradThreads / 32) + warp; col < ncols; col += wstride) {
         const int ix = (int)(col / gp.ny), iy = (int)(col % gp.ny);
-        R chi[kGradMaxRun], rs[kGradMaxRun], ux[kGradMaxRun], uy[kGradMaxRun], uz[kGradMaxRun];
-        int clip[kGradMaxRun];
-        C T[kGradMaxRun], Rv[kGradMaxRun];
+        R chi[kRun], rs[kRun], ux[kRun], uy[kRun], uz[kRun];
+        int clip[kRun];
+        C T[kRun], Rv[kRun];
         R local = (R)0;
 #pragma unroll
-        for (int k = 0; k < kGradMaxRun; ++k) {
+        for (int k = 0; k < kRun; ++k) {
             const int iz = lane * run + k;
             chi[k] = (R)0;
             if (k < run && iz < nz) soft_voxel<R>(sp, gp, ix, iy, iz, chi[k], rs[k], clip[k], ux[k], uy[k], uz[k]);
@@ -236,7 +246,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
         C rsum;
         rsum.x = rsum.y = (R)0;
 #pragma unroll
-        for (int k = 0; k < kGradMaxRun; ++k) {
+        for (int k = 0; k < kRun; ++k) {
             const int iz = lane * run + k;
             T[k].x = T[k].y = (R)0;
             Rv[k].x = Rv[k].y = (R)0;
@@ -278,9 +288,11 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
         suffix.x = above.x - rsum.x;
         suffix.y = above.y - rsum.y;
 #pragma unroll
-        for (int k = kGradMaxRun - 1; k >= 0; --k) {
+        for (int k = kRun - 1; k >= 0; --k) {
+            if (k >= run) continue;                       // warp-uniform
             const int iz = lane * run + k;
-            if (k < run && iz < nz) {
+            R w0 = (R)0, ct = (R)1, st = (R)0, cph = (R)1, sph = (R)0;
+            if (iz < nz) {
                 // chibar = R T + i kdz (n-1) suffix
                 C t1 = cmul(Rv[k], T[k]);
                 C t2 = cmul(nm1, suffix);
@@ -300,31 +312,55 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
                     acc[1] += coef * r3 * uy[k] * uy[k] / (R)(sp.b * sp.b * sp.b);
                     acc[2] += coef * r3 * uz[k] * uz[k] / (R)(sp.c * sp.c * sp.c);
                 } else if (clip[k] == 0) {
-                    const R w0 = coef * (R)sp.R0;
-                    R ct = uz[k], st = sqrt(ux[k] * ux[k] + uy[k] * uy[k]);
-                    R cph = (R)1, sph = (R)0;
+                    w0 = coef * (R)sp.R0;
+                    ct = uz[k];
+                    st = sqrt(ux[k] * ux[k] + uy[k] * uy[k]);
                     if (st > (R)0) {
                         cph = ux[k] / st;
                         sph = uy[k] / st;
                     }
-                    const ShTab<R> tb(sp);
-                    real_sh_all<R>(tb, sp.lmax, ct, st, cph, sph, [&](int idx, R y) {
-                        if (idx > 0) acc[idx - 1] += w0 * y;
-                    });
-                    acc[ng - 1] += coef * rs[k] / (R)sp.R0;
+                    acc[0] += coef * rs[k] / (R)sp.R0;
                 } else if (clip[k] < 0) {
-                    acc[ng - 1] += coef * (R)0.1;
+                    acc[0] += coef * (R)0.1;
                 }
+            }
+            // d radius / d a_lm = R0 Y_lm: every lane evaluates its direction (w0 = 0
+            // where the voxel does not contribute) and the warp sums each term
+            if (sh && __any_sync(0xffffffffu, w0 != (R)0)) {
+                const ShTab<R> tb(sp);
+                real_sh_all<R>(tb, sp.lmax, ct, st, cph, sph, [&](int idx, R y) {
+                    if (idx == 0) return;
+                    R v = w0 * y;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    const int j = idx - 1;
+                    if (lane == (j & 31)) {
+#pragma unroll
+                        for (int q = 0; q < kGradWarpSlots; ++q)
+                            if (q == (j >> 5)) aw[q] += v;
+                    }
+                });
             }
         }
     }
     // deterministic reduction: warp tree, then warps in order
     __shared__ double red[kGradThreads / 32][kMaxGeom + 2];
-    for (int k = 0; k < ng + 2; ++k) {
-        double v = k < ng ? (double)acc[k] : (k == ng ? (double)D.x : (double)D.y);
+    // per-thread sums: sphere / ellipsoid parameters, or R0 (the last index)
+    const int n_thread = sh ? 1 : ng;
+    for (int k = 0; k < n_thread + 2; ++k) {
+        double v = k < n_thread ? (double)acc[k] : (k == n_thread ? (double)D.x : (double)D.y);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][k] = v;
+        const int at = k < n_thread ? (sh ? ng - 1 : k) : ng + (k - n_thread);
+        if (lane == 0) red[warp][at] = v;
+    }
+    if (sh) {
+        // a_lm sums are already warp totals
+#pragma unroll
+        for (int q = 0; q < kGradWarpSlots; ++q) {
+            const int j = 32 * q + lane;
+            if (j < ng - 1) red[warp][j] = (double)aw[q];
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < ng + 2; k += kGradThreads) {
@@ -337,10 +373,24 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
 cudaError_t launch_grad_voxels(bool fp64, const ShapeParams &sp, const GridParams &gp, const void *S,
                                double *partials, int n_blocks, cudaStream_t st) {
     if (gp.nz > 32 * kGradMaxRun) return cudaErrorInvalidValue;
-    if (fp64)
-        grad_voxel_kernel<double><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, (const double2 *)S, partials);
-    else
-        grad_voxel_kernel<float><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, (const float2 *)S, partials);
+    const int run = (gp.nz + 31) / 32;
+    if (fp64) {
+        const double2 *Sd = (const double2 *)S;
+        if (run <= 2)
+            grad_voxel_kernel<double, 2><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
+        else if (run <= 4)
+            grad_voxel_kernel<double, 4><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
+        else
+            grad_voxel_kernel<double, 8><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
+    } else {
+        const float2 *Sf = (const float2 *)S;
+        if (run <= 2)
+            grad_voxel_kernel<float, 2><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
+        else if (run <= 4)
+            grad_voxel_kernel<float, 4><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
+        else
+            grad_voxel_kernel<float, 8><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
+    }
     return cudaGetLastError();
 }
 
