@@ -49,6 +49,9 @@ def parse():
                     help="time this many forward+gradient fit steps of the 96^3 l<=6 workload and print a JSON line")
     ap.add_argument("--short-serving", type=int, default=240,
                     help="requests of the short serving run folded into the default line (0: skip)")
+    ap.add_argument("--fig8b-case", type=float, nargs=2, metavar=("RADIUS_LAMBDA", "DETECTOR"),
+                    help="time one Fig. 8b case (uniform-q detector) in --precision and print a JSON line; "
+                         "for profiler runs")
     ap.add_argument("--main-only", action="store_true",
                     help="time the main step only (no comparator, fit step, plain configs, timing study, "
                          "CPU baseline or serving); for profiler runs")
@@ -519,6 +522,14 @@ def main():
                           "value": res["fit_steps_per_s"], "unit": "fit steps/s", "n_gpus": 1,
                           "higher_is_better": True, "data": "synthetic", "fit_step": res}), flush=True)
         return
+    if args.fig8b_case:
+        import __graft_entry__
+        __graft_entry__.build()
+        res = fig8b_run(radii=(args.fig8b_case[0],), dets=(int(args.fig8b_case[1]),), precisions=(args.precision,),
+                        reps=3)
+        print(json.dumps({"metric": "MSFT ms per pattern (Fig. 8b case, uniform-q detector)", "unit": "ms",
+                          "higher_is_better": False, "data": "synthetic", "fig8b": res}), flush=True)
+        return
     if args.serving > 0:
         import __graft_entry__
         __graft_entry__.build()
@@ -635,16 +646,15 @@ def main():
                 "note": "one spherical-harmonics radius (l <= 8) per voxel; the writes are far below HBM speed"}
 
     # end to end through the C ABI with host memory: voxelise + forward + D2H per pattern
+    # (the pipelined batch call: pattern i computes while pattern i - 1 downloads)
     I_host = torch.empty((B, g.n_pix), dtype=torch.float32, pin_memory=True)
-    for s_i, s in enumerate(shapes[:2]):
-        sm.scatman_acquire(h, s, I_host[s_i].numpy())
+    sm.scatman_acquire_batch(h, shapes[:2], I_host[:2])
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
     for _ in range(args.steps):
-        for b, s in enumerate(shapes):
-            sm.scatman_acquire(h, s, I_host[b].numpy())
+        sm.scatman_acquire_batch(h, shapes, I_host)
     e_el = max_over_ranks(time.perf_counter() - e0, dist, "cuda")
     h2d = B * (8 * (shapes[0].lmax + 1) ** 2 + 160)      # shape struct + coefficients handed over
     d2h = B * g.n_pix * 4

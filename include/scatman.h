@@ -209,6 +209,18 @@ SCATMAN_API int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev);
 SCATMAN_API int scatman_acquire(scatman_handle *h, const scatman_shape *shape, void *I_host);
 
 /*
+ * scatman_acquire over n shapes, pipelined: pattern i is computed while
+ * pattern i - 1 is copied to the host (a second intensity buffer and a copy
+ * stream, created on the first call and owned by the handle).  I_host[i]
+ * receives pattern i's intensity (n_pix elements; page-locked host memory
+ * lets the copies overlap the computation).  Returns after every copy has
+ * landed, with the same results as n calls of scatman_acquire.  n = 0 is a
+ * no-op.  Errors as scatman_acquire; on an error the later patterns are not
+ * computed and their arrays are left untouched.
+ */
+SCATMAN_API int scatman_acquire_batch(scatman_handle *h, const scatman_shape *shapes, int n, void *const *I_host);
+
+/*
  * The Ideal detector (Sec. 5.2, Listing 2: "photon statistics"): turns an
  * intensity I (device array from scatman_forward on this handle, n_pix
  * elements of its element type) into the expected number of scattered photons

@@ -6,14 +6,14 @@ not load the library; the first call does, and fails loudly if the library has
 not been built (``paper_2202_03411_gb300.build.build()``).
 """
 from . import _lib
-from .api import (Handle, ScatmanError, scatman_acquire, scatman_backward, scatman_contraction_flops,
+from .api import (Handle, ScatmanError, scatman_acquire, scatman_acquire_batch, scatman_backward, scatman_contraction_flops,
                   scatman_create, scatman_destroy,
                   scatman_device_bytes, scatman_elem_size, scatman_forward, scatman_forward_noalloc, scatman_get_occupancy,
                   scatman_get_q, scatman_get_slices, scatman_last_error, scatman_n_pix, scatman_param_count,
                   scatman_photon_counts, scatman_sync, scatman_version, scatman_voxelise)
 
 __all__ = [
-    "Handle", "ScatmanError", "scatman_acquire", "scatman_backward", "scatman_contraction_flops", "scatman_create", "scatman_destroy",
+    "Handle", "ScatmanError", "scatman_acquire", "scatman_acquire_batch", "scatman_backward", "scatman_contraction_flops", "scatman_create", "scatman_destroy",
     "scatman_device_bytes", "scatman_elem_size", "scatman_forward", "scatman_forward_noalloc", "scatman_get_occupancy", "scatman_get_q",
     "scatman_get_slices", "scatman_last_error", "scatman_n_pix", "scatman_param_count", "scatman_photon_counts",
     "scatman_sync",

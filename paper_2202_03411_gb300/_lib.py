@@ -87,6 +87,8 @@ SIGNATURES = {
     "scatman_voxelise": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(scatman_shape)]),
     "scatman_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "scatman_acquire": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(scatman_shape), ctypes.c_void_p]),
+    "scatman_acquire_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(scatman_shape), ctypes.c_int,
+                                             ctypes.POINTER(ctypes.c_void_p)]),
     "scatman_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _D]),
     "scatman_photon_counts": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_ulonglong, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p]),

@@ -151,6 +151,21 @@ def scatman_acquire(h: Handle, shape, I_host) -> None:
     _check(_lib.load().scatman_acquire(h.ptr, ctypes.byref(st), ctypes.c_void_p(ptr)), h, "acquire")
 
 
+def scatman_acquire_batch(h: Handle, shapes, I_host) -> None:
+    """I_host: one host array per shape (numpy arrays or pinned CPU tensors of
+    n_pix elements), or a 2D array / tensor whose rows are the patterns."""
+    n = len(shapes)
+    arr = (scatman_shape * max(n, 1))()
+    keep = []
+    for i, s in enumerate(shapes):
+        st, k = make_shape(s)
+        arr[i] = st
+        keep.append(k)
+    rows = [I_host[i] for i in range(n)]
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[r.ctypes.data if isinstance(r, np.ndarray) else r.data_ptr() for r in rows])
+    _check(_lib.load().scatman_acquire_batch(h.ptr, arr, n, ptrs), h, "acquire_batch")
+
+
 def scatman_backward(h: Handle, dLdI) -> np.ndarray:
     lib = _lib.load()
     n = lib.scatman_param_count(h.ptr)

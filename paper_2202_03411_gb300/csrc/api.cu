@@ -138,6 +138,13 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_s);
     cudaFree(h->d_A);
     cudaFree(h->d_I);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    cudaFree(h->d_I2);
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_fwd[b]) cudaEventDestroy(h->ev_fwd[b]);
+        if (h->ev_copy[b]) cudaEventDestroy(h->ev_copy[b]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
     cudaFree(h->d_err);
     cudaFree(h->d_part);
     cudaFree(h->d_S);
@@ -620,6 +627,45 @@ int scatman_acquire(scatman_handle *h, const scatman_shape *shape, void *I_host)
                                        cudaMemcpyDeviceToHost, h->stream),
                     "intensity download");
     if (rc) return rc;
+    return scatman_sync(h);
+}
+
+int scatman_acquire_batch(scatman_handle *h, const scatman_shape *shapes, int n, void *const *I_host) {
+    if (!h || (n > 0 && (!shapes || !I_host))) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
+    if (n < 0) return set_error(h, SCATMAN_ERR_ARG, "n must be >= 0");
+    for (int i = 0; i < n; ++i)
+        if (!I_host[i]) return set_error(h, SCATMAN_ERR_ARG, "NULL host array");
+    const size_t bytes = (size_t)h->n_pix * scatman_elem_size(h);
+    int rc;
+    if (!h->copy_stream) {
+        if ((rc = alloc_dev(h, &h->d_I2, bytes, "second intensity buffer"))) return rc;
+        if ((rc = check_cuda(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking), "copy stream")))
+            return rc;
+        for (int b = 0; b < 2; ++b) {
+            if ((rc = check_cuda(h, cudaEventCreateWithFlags(&h->ev_fwd[b], cudaEventDisableTiming), "event")))
+                return rc;
+            if ((rc = check_cuda(h, cudaEventCreateWithFlags(&h->ev_copy[b], cudaEventDisableTiming), "event")))
+                return rc;
+        }
+    }
+    // Two intensity buffers: pattern i computes into buffer i % 2 on the handle's
+    // stream while the copy stream downloads pattern i - 1; a buffer is reused
+    // only after its previous download has finished.
+    for (int i = 0; i < n; ++i) {
+        const int b = i & 1;
+        void *buf = b ? h->d_I2 : h->d_I;
+        if (i >= 2 && (rc = check_cuda(h, cudaStreamWaitEvent(h->stream, h->ev_copy[b], 0), "stream wait")))
+            return rc;
+        if ((rc = scatman_voxelise(h, &shapes[i]))) return rc;
+        if ((rc = scatman_forward(h, buf, nullptr))) return rc;
+        if ((rc = check_cuda(h, cudaEventRecord(h->ev_fwd[b], h->stream), "event record"))) return rc;
+        if ((rc = check_cuda(h, cudaStreamWaitEvent(h->copy_stream, h->ev_fwd[b], 0), "stream wait"))) return rc;
+        if ((rc = check_cuda(h, cudaMemcpyAsync(I_host[i], buf, bytes, cudaMemcpyDeviceToHost, h->copy_stream),
+                             "intensity download")))
+            return rc;
+        if ((rc = check_cuda(h, cudaEventRecord(h->ev_copy[b], h->copy_stream), "event record"))) return rc;
+    }
+    if ((rc = check_cuda(h, cudaStreamSynchronize(h->copy_stream), "copy stream synchronize"))) return rc;
     return scatman_sync(h);
 }
 

@@ -142,6 +142,9 @@ struct scatman_handle {
     size_t s_bytes = 0;
     void *d_A = nullptr;            // field cache (double2 or float2)
     void *d_I = nullptr;            // intensity scratch for acquire
+    void *d_I2 = nullptr;           // second intensity buffer of the batched acquire (on first use)
+    cudaStream_t copy_stream = nullptr;   // batched acquire: device-to-host copies
+    cudaEvent_t ev_fwd[2] = {nullptr, nullptr}, ev_copy[2] = {nullptr, nullptr};
     int *d_err = nullptr;
     double *d_part = nullptr;       // backward partial sums
     size_t part_count = 0;
