@@ -171,3 +171,28 @@ def test_uniform_q_fig8b_worst_case_sampled(prec, tol):
     err = rel_l2(I[sample], Ir)
     assert err < tol, err
     assert np.all(I[sample][~valid] == 0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tc_f16_split", "tc_bf16"])
+def test_uniform_q_edge_cases(prec):
+    """Empty shape (exactly zero), a single slice, a single pixel, a one-row
+    detector, and a one-voxel grid on the uniform-q detector."""
+    from workloads import SPHERE
+    # A handful of nearly coherent terms does not average rounding out: with one
+    # BF16 phase product the bound is the coherent one, I off by at most
+    # 2 (2^-9 phase + 2^-9 data) = 7.8e-3 (the 3e-3 of larger grids relies on
+    # averaging over many terms).
+    tol = {"fp64": 1e-10, "fp32": 1e-5, "tc_f16_split": 1e-3, "tc_bf16": 7.8e-3}[prec]
+    g = Geometry(16, 16, 16, 1.0, 6.0, 30.0, 20, 20, DETECTOR_UNIFORM_Q)
+    empty = Shape(SPHERE, r=0.1, cx=0.25, cy=0.25, cz=0.25, delta=0.01, beta=0.001)
+    I, _ = run_gpu(g, empty, prec)
+    assert np.all(I == 0.0)
+    s = Shape(SPHERE, r=3.0, delta=0.02, beta=0.01)
+    for g in (Geometry(9, 9, 1, 1.0, 6.0, 30.0, 5, 4, DETECTOR_UNIFORM_Q),
+              Geometry(9, 9, 9, 1.0, 6.0, 30.0, 1, 1, DETECTOR_UNIFORM_Q),
+              Geometry(9, 9, 9, 1.0, 6.0, 30.0, 131, 1, DETECTOR_UNIFORM_Q),
+              Geometry(1, 1, 1, 1.0, 6.0, 30.0, 3, 2, DETECTOR_UNIFORM_Q)):
+        I, _ = run_gpu(g, s, prec)
+        Ir, Ar = oracle_field(g, s)
+        Ir = np.abs(np.where(oracle.detector_valid(g), Ar, 0.0)) ** 2
+        assert rel_l2(I, Ir) < tol, (g, prec, rel_l2(I, Ir))
