@@ -501,12 +501,19 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def launches_per_pattern(precision: str) -> int:
+def launches_per_pattern(precision: str, n_pix: int, sm_count: int) -> int:
     """Kernels one voxelise + forward launches: tensor-core modes reset the
     slice boxes, voxelise with the scan, pack the occupied-slice list and run
-    the contraction; the CUDA-core modes voxelise and run the contraction with
-    its fixed-order partial-sum reduction."""
-    return 4 if precision.startswith("tc_") else 3
+    the contraction, plus the sum of the cut tiles' partial fields when the
+    last wave of 128-pixel tiles is cut into slice ranges; the CUDA-core modes
+    voxelise and run the contraction with its fixed-order partial-sum
+    reduction."""
+    if not precision.startswith("tc_"):
+        return 3
+    tiles = (n_pix + 127) // 128
+    rem = tiles % sm_count if tiles > sm_count else tiles
+    parts = min(4, max(1, (sm_count + rem // 2) // rem)) if rem else 1
+    return 5 if parts > 1 else 4
 
 
 def main():
@@ -713,7 +720,9 @@ def main():
         "serving_short": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "gpu_launches": launches_per_pattern(args.precision) * B * args.steps,
+        "gpu_launches": launches_per_pattern(args.precision, g.n_pix,
+                                             torch.cuda.get_device_properties(local_rank).multi_processor_count)
+                        * B * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": wall,
     }

@@ -149,6 +149,7 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_part);
     cudaFree(h->d_S);
     cudaFree(h->d_partial);
+    cudaFree(h->d_tail);
     cudaFree(h->d_H);
     cudaFree(h->d_uq_qz);
     cudaFree(h->d_uq_qrow);
@@ -274,12 +275,14 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if (h->uniform_tc) {
         const size_t hb = uq_tc_h_bytes(c.nx, c.nz, c.det_ny);
         if ((rc = alloc_dev(h, &h->d_H, hb, "y-contracted slices"))) return fail(rc);
-
         // padding rows (z >= nz) and columns (x >= nx) stay zero for good
         if ((rc = check_cuda(h, cudaMemsetAsync(h->d_H, 0, hb, h->stream), "memset"))) return fail(rc);
     } else if (h->uniform_q) {
         if ((rc = alloc_dev(h, &h->d_H, (size_t)c.det_ny * nvox / c.ny * cx, "y-contracted slices"))) return fail(rc);
-    } else if (!h->tensor_core) {
+    } else if (h->tensor_core) {
+        const size_t tb = tc_tail_part_bytes(h->n_pix, h->sm_count);
+        if (tb && (rc = alloc_dev(h, (void **)&h->d_tail, tb, "tail partial fields"))) return fail(rc);
+    } else {
         h->splits = simt_splits(h->n_pix, c.nx, c.nz, h->sm_count);
         if ((rc = alloc_dev(h, &h->d_partial, (size_t)h->splits * npix * cx, "partial fields"))) return fail(rc);
     }
@@ -584,8 +587,7 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
     } else if (h->tensor_core) {
         e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, c.voxel, str_re,
                            str_im, h->split, h->bf16, h->d_bounds, (uint2 *)(h->d_bounds + 4 * c.nz), (float2 *)h->d_A,
-                           (float *)I_dev, h->d_err,
-                           h->sm_count, h->stream);
+                           (float *)I_dev, h->d_err, h->sm_count, h->stream, h->d_tail);
     } else {
         e = launch_msft_simt(h->precision == SCATMAN_FP64, h->d_s, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
                              str_re, str_im, h->d_A, I_dev, h->d_partial, h->splits, h->stream);

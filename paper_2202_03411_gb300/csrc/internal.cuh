@@ -150,6 +150,7 @@ struct scatman_handle {
     size_t part_count = 0;
     void *d_S = nullptr;            // backward adjoint field (complex, nvox)
     void *d_partial = nullptr;      // CUDA-core contraction: per-split partial fields
+    float2 *d_tail = nullptr;       // tensor-core contraction: partial fields of the last wave's cut tiles
     void *d_H = nullptr;            // uniform-q detector: y-contracted slices [v][z][x], or in the
                                     // tensor-core modes 16-bit planes [row group][-Im | Re | Im][Rg Jp][Kx]
     bool uniform_q = false;
@@ -228,10 +229,13 @@ cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long lon
                              void *partial, int splits, cudaStream_t st);
 // Tensor-core contraction (msft_tc.cu).
 size_t tc_ring_bytes(int Nyp, int Nxp, bool split);
+// tail_part: scratch of tc_tail_part_bytes for the partial fields of the last
+// partial wave's tiles (null: every tile whole).
 cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
                            int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
                            bool bf16, const int *bounds, uint2 *list, float2 *A, float *I, int *err,
-                           int sm_count, cudaStream_t st);
+                           int sm_count, cudaStream_t st, float2 *tail_part);
+size_t tc_tail_part_bytes(long long n_pix, int sm_count);
 // The same kernel in store mode, the uniform-q detector's y-contraction on the
 // tensor cores: rows are detector rows v (q_y(v) = qrow[3 v + 1]) and G is
 // written to the x/z operand H as 16-bit planes.

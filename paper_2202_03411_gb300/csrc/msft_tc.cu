@@ -47,6 +47,7 @@ constexpr int kKBlockBytes = kBM * 128;    // one 128 x 64 operand block
 constexpr int kSlots = 8;                  // stages in flight at most
 constexpr int kPlanes = 3;                 // slice operand planes: -Im, Re, Im
 constexpr int kMaxSmem = 232448;           // 227 KB opt-in per block
+constexpr int kTcMaxTailParts = 4;         // slice ranges per tile of the last partial wave
 
 struct TcParams {
     const double *q;
@@ -58,8 +59,13 @@ struct TcParams {
     uint32_t ring_bytes;        // slice-stage ring (multiple of 1024)
     int split, bf16;
     int num_m_tiles;
-    int parts, num_units;       // store mode: each pixel tile's slice list cut into `parts` ranges
-                                // (units = tiles x parts); the field sum keeps parts = 1
+    // Work units: tiles [0, whole) whole, then each of the remaining tiles cut
+    // into `parts` ranges of its occupied-slice list (units whole + (tiles -
+    // whole) x parts).  The field sum cuts only the last partial wave (their
+    // partial fields go to Apart and a finishing kernel adds them); store
+    // mode cuts every tile (slices are independent there).
+    int whole, parts, num_units;
+    float2 *Apart;              // [part][(tile - whole) * 128 + m]
     uint32_t idesc;             // without the N field (set per slice)
     uint32_t tmem_cols;
     double voxel;
@@ -141,11 +147,30 @@ __global__ void pack_spans_kernel(const int *bounds, int nz, int Nxp, int Nyp, u
     if (threadIdx.x == 0) list[0] = make_uint2((uint32_t)s_base, 0u);
 }
 
-// The occupied-slice range [i_lo, i_hi) of work unit u (tile u % num_m_tiles).
+// Tile, part (-1: whole tile) and occupied-slice range [i_lo, i_hi) of work unit u.
+struct TcUnit {
+    int mt, part, i_lo, i_hi;
+};
+__device__ __forceinline__ TcUnit unit_info(const TcParams &P, int u, int n_occ) {
+    TcUnit w;
+    if (u < P.whole) {
+        w.mt = u;
+        w.part = -1;
+        w.i_lo = 0;
+        w.i_hi = n_occ;
+    } else {
+        const int v = u - P.whole;
+        w.mt = P.whole + v / P.parts;
+        w.part = v % P.parts;
+        w.i_lo = (int)((long long)w.part * n_occ / P.parts);
+        w.i_hi = (int)((long long)(w.part + 1) * n_occ / P.parts);
+    }
+    return w;
+}
 __device__ __forceinline__ void unit_slices(const TcParams &P, int u, int n_occ, int &i_lo, int &i_hi) {
-    const int part = u / P.num_m_tiles;
-    i_lo = (int)((long long)part * n_occ / P.parts);
-    i_hi = (int)((long long)(part + 1) * n_occ / P.parts);
+    const TcUnit w = unit_info(P, u, n_occ);
+    i_lo = w.i_lo;
+    i_hi = w.i_hi;
 }
 
 // Placement of a stage of `sz` bytes in the ring: a stage never wraps, it
@@ -387,7 +412,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int n_occ = (int)__ldg(&P.list[0].x);
         const size_t plane = (size_t)P.h_Jg * P.h_Kx;
         for (int u = blockIdx.x; u < P.num_units; u += gridDim.x) {
-            const int mt = u % P.num_m_tiles;
+            const int mt = unit_info(P, u, n_occ).mt;
             const long long v = (long long)mt * kBM + m;
             const bool valid = v < P.n_pix;
             const double qy = valid ? P.q[3 * v + 1] : 0.0;
@@ -451,22 +476,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // Every epilogue thread runs every tile iteration (after an abort the
         // waits return at once), so the named barriers below always meet.
         const int n_occ = (int)__ldg(&P.list[0].x);
-        // q of this thread's pixel, loaded one tile ahead
+        // q of this thread's pixel, loaded one unit ahead
         double nq0 = 0.0, nq1 = 0.0, nq2 = 0.0;
-        {
-            const long long p0 = (long long)blockIdx.x * kBM + m;
+        if (blockIdx.x < (unsigned)P.num_units) {
+            const long long p0 = (long long)unit_info(P, blockIdx.x, n_occ).mt * kBM + m;
             if (p0 < P.n_pix) {
                 nq0 = P.q[3 * p0];
                 nq1 = P.q[3 * p0 + 1];
                 nq2 = P.q[3 * p0 + 2];
             }
         }
-        for (int mt = blockIdx.x; mt < P.num_m_tiles; mt += gridDim.x) {
+        for (int u = blockIdx.x; u < P.num_units; u += gridDim.x) {
+            const TcUnit un = unit_info(P, u, n_occ);
+            const int mt = un.mt;
             const long long p = (long long)mt * kBM + m;
             const bool valid = p < P.n_pix;
             const double qx = nq0, qy = nq1, qz = nq2;
-            {
-                const long long pn = (long long)(mt + gridDim.x) * kBM + m;
+            if (u + (int)gridDim.x < P.num_units) {
+                const long long pn = (long long)unit_info(P, u + gridDim.x, n_occ).mt * kBM + m;
                 if (pn < P.n_pix) {
                     nq0 = P.q[3 * pn];
                     nq1 = P.q[3 * pn + 1];
@@ -495,11 +522,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float2 Z = make_float2(1.f, 0.f);
             int t_prev = -2;
             float2 acc = make_float2(0.f, 0.f);
-            uint2 nxt = n_occ > 0 ? __ldg(&P.list[1]) : make_uint2(0u, 0u);
-            for (int i = 0; i < n_occ; ++i) {
+            uint2 nxt = un.i_lo < un.i_hi ? __ldg(&P.list[1 + un.i_lo]) : make_uint2(0u, 0u);
+            for (int i = un.i_lo; i < un.i_hi; ++i) {
                 const int t = (int)nxt.x;
                 const uint32_t w = nxt.y;
-                if (i + 1 < n_occ) nxt = __ldg(&P.list[i + 2]);
+                if (i + 1 < un.i_hi) nxt = __ldg(&P.list[i + 2]);
                 // e^{-i q_z z_t}: advanced by one slice step, re-anchored after a
                 // gap and every 16 occupied slices
                 if (t == t_prev + 1 && (i & 15) != 0)
@@ -549,8 +576,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const float2 o = red[m];
                 float2 a = make_float2(acc.x + o.x, acc.y + o.y);
                 a = cmul(make_float2(P.str_re, P.str_im), a);
-                P.A[p] = a;
-                P.I[p] = a.x * a.x + a.y * a.y;
+                if (un.part < 0) {
+                    P.A[p] = a;
+                    P.I[p] = a.x * a.x + a.y * a.y;
+                } else {
+                    const long long tail = (long long)(P.num_m_tiles - P.whole) * kBM;
+                    P.Apart[un.part * tail + (long long)(mt - P.whole) * kBM + m] = a;
+                }
             }
             named_bar_sync(kEpiThreads);
         }
@@ -577,6 +609,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         tc_fence_after();
         tmem_dealloc(tmem_base, P.tmem_cols);
     }
+}
+
+// Fields of the tiles whose slice lists were cut into parts: A = the parts'
+// sum in part order, I = |A|^2.
+__global__ void tc_tail_sum_kernel(const float2 *__restrict__ Apart, int parts, long long tail, long long p0,
+                                   long long n_pix, float2 *__restrict__ A, float *__restrict__ I) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tail || p0 + t >= n_pix) return;
+    float2 a = Apart[t];
+    for (int k = 1; k < parts; ++k) {
+        const float2 b = Apart[k * tail + t];
+        a.x += b.x;
+        a.y += b.y;
+    }
+    A[p0 + t] = a;
+    I[p0 + t] = a.x * a.x + a.y * a.y;
 }
 
 // ---- host side ------------------------------------------------------------------
@@ -662,7 +710,7 @@ bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16,
 static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz, int Nxp,
                              int Nyp, double voxel, double str_re, double str_im, bool split, bool bf16,
                              const int *bounds, uint2 *list, float2 *A, float *I, int *err, int sm_count,
-                             cudaStream_t st, const UqStore *store) {
+                             cudaStream_t st, const UqStore *store, float2 *tail_part) {
     TcParams P;
     P.q = q;
     P.list = list;
@@ -680,13 +728,29 @@ static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pi
     P.split = split ? 1 : 0;
     P.bf16 = bf16 ? 1 : 0;
     P.num_m_tiles = (int)((n_pix + kBM - 1) / kBM);
-    // store mode: about one unit per SM (slices are independent there)
+    P.whole = P.num_m_tiles;
     P.parts = 1;
+    P.Apart = nullptr;
     if (store) {
+        // about one unit per SM (slices are independent there)
         const int want = (sm_count + P.num_m_tiles - 1) / P.num_m_tiles;
+        P.whole = 0;
         P.parts = want < 1 ? 1 : want > nz ? nz : want;
+    } else if (tail_part) {
+        // the last partial wave (every tile when there are fewer tiles than
+        // SMs): cut its tiles so that wave fills the SMs
+        const int rem = P.num_m_tiles > sm_count ? P.num_m_tiles % sm_count : P.num_m_tiles;
+        if (rem > 0) {
+            int parts = (sm_count + rem / 2) / rem;
+            parts = parts < 1 ? 1 : parts > kTcMaxTailParts ? kTcMaxTailParts : parts;
+            if (parts > 1) {
+                P.whole = P.num_m_tiles - rem;
+                P.parts = parts;
+                P.Apart = tail_part;
+            }
+        }
     }
-    P.num_units = P.num_m_tiles * P.parts;
+    P.num_units = P.whole + (P.num_m_tiles - P.whole) * P.parts;
     const uint32_t M = kBM;
     P.idesc = (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((M >> 4) << 24);
     uint32_t cols = 32;
@@ -717,26 +781,39 @@ static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pi
     pack_spans_kernel<<<1, 256, 0, st>>>(bounds, nz, Nxp, Nyp, list);
     int grid = P.num_units < sm_count ? P.num_units : sm_count;
     if (grid < 1) grid = 1;
-    if (store)
+    if (store) {
         msft_tc_kernel<true><<<grid, kTcThreads, smem, st>>>(maps, P);
-    else
+    } else {
         msft_tc_kernel<false><<<grid, kTcThreads, smem, st>>>(maps, P);
+        if (P.whole < P.num_m_tiles) {
+            const long long tail = (long long)(P.num_m_tiles - P.whole) * kBM;
+            tc_tail_sum_kernel<<<(unsigned)((tail + 255) / 256), 256, 0, st>>>(
+                P.Apart, P.parts, tail, (long long)P.whole * kBM, n_pix, A, I);
+        }
+    }
     return cudaGetLastError();
+}
+
+size_t tc_tail_part_bytes(long long n_pix, int sm_count) {
+    // at most kTcMaxTailParts parts of fewer than sm_count tiles
+    const long long tiles = (n_pix + kBM - 1) / kBM;
+    const long long rem = tiles > sm_count ? tiles % sm_count : tiles;
+    return (size_t)(rem * kBM * kTcMaxTailParts) * sizeof(float2);
 }
 
 cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
                            int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
                            bool bf16, const int *bounds, uint2 *list, float2 *A, float *I, int *err,
-                           int sm_count, cudaStream_t st) {
+                           int sm_count, cudaStream_t st, float2 *tail_part) {
     return launch_tc(maps, q, n_pix, nx, ny, nz, Nxp, Nyp, voxel, str_re, str_im, split, bf16, bounds, list, A, I,
-                     err, sm_count, st, nullptr);
+                     err, sm_count, st, nullptr, tail_part);
 }
 
 cudaError_t launch_uq_y_tc_mma(const TcMaps &maps, const double *qrow, int det_ny, int nx, int ny, int nz, int Nxp,
                                int Nyp, double voxel, bool split, bool bf16, const int *bounds, uint2 *list,
                                const UqStore &store, int *err, int sm_count, cudaStream_t st) {
     return launch_tc(maps, qrow, det_ny, nx, ny, nz, Nxp, Nyp, voxel, 1.0, 0.0, split, bf16, bounds, list, nullptr,
-                     nullptr, err, sm_count, st, &store);
+                     nullptr, err, sm_count, st, &store, nullptr);
 }
 
 }  // namespace scm

@@ -326,6 +326,8 @@ long long scatman_footprint_bytes(const scatman_config *c) {
         b += round_2mib(npix * 8);                                    // q_z table
     } else if (!tc) {
         b += round_2mib(64 * npix * cx);        // partial fields (upper bound on splits)
+    } else {
+        b += round_2mib(256LL * 128 * 4 * 8);   // last wave's partial fields (< 256 SMs, <= 4 parts)
     }
     b += round_2mib(nvox * cx);                 // adjoint field (backward)
     if (tc) {
