@@ -147,28 +147,45 @@ int grad_voxel_blocks(const GridParams &gp) {
     return (int)(b < 608 ? b : 608);
 }
 
-// Soft occupancy of one voxel with its surface radius and clip state, in the
-// same arithmetic as the forward voxeliser's soft branch.
+// Soft occupancy of one voxel with its surface radius and clip state: the
+// forward voxeliser's soft branch in FP64; in FP32 with FP32 body coordinates
+// (the occupancy is smooth, so this moves chi by ~1e-7, far inside the FP32
+// gradient's tolerance, and keeps FP64 off the per-voxel path).
 template <typename R>
 __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz, R &chi,
                                            R &rs, int &clip, R &ux, R &uy, R &uz) {
-    double px, py, pz;
-    if (sp.kind == SCATMAN_SPHERE) {
-        px = (ix - 0.5 * (gp.nx - 1)) * gp.voxel - sp.cx;
-        py = (iy - 0.5 * (gp.ny - 1)) * gp.voxel - sp.cy;
-        pz = (iz - 0.5 * (gp.nz - 1)) * gp.voxel - sp.cz;
+    R px, py, pz;
+    if constexpr (sizeof(R) == 8) {
+        if (sp.kind == SCATMAN_SPHERE) {
+            px = (ix - 0.5 * (gp.nx - 1)) * gp.voxel - sp.cx;
+            py = (iy - 0.5 * (gp.ny - 1)) * gp.voxel - sp.cy;
+            pz = (iz - 0.5 * (gp.nz - 1)) * gp.voxel - sp.cz;
+        } else {
+            body_coords(sp, gp, ix, iy, iz, px, py, pz);
+        }
     } else {
-        body_coords(sp, gp, ix, iy, iz, px, py, pz);
+        const float vox = (float)gp.voxel;
+        const float dx = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
+        const float dy = ((float)iy - 0.5f * (float)(gp.ny - 1)) * vox - sp.cyf;
+        const float dz = ((float)iz - 0.5f * (float)(gp.nz - 1)) * vox - sp.czf;
+        if (sp.kind == SCATMAN_SPHERE) {
+            px = dx;
+            py = dy;
+            pz = dz;
+        } else {
+            px = sp.Rf[0] * dx + sp.Rf[3] * dy + sp.Rf[6] * dz;
+            py = sp.Rf[1] * dx + sp.Rf[4] * dy + sp.Rf[7] * dz;
+            pz = sp.Rf[2] * dx + sp.Rf[5] * dy + sp.Rf[8] * dz;
+        }
     }
-    const double p2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
-    const R rr = (R)sqrt(p2);
+    const R rr = sqrt(px * px + py * py + pz * pz);
     ux = (R)0;
     uy = (R)0;
     uz = (R)1;
     if (rr > (R)0) {
-        ux = (R)px / rr;
-        uy = (R)py / rr;
-        uz = (R)pz / rr;
+        ux = px / rr;
+        uy = py / rr;
+        uz = pz / rr;
     }
     clip = 0;
     if (sp.kind == SCATMAN_SPHERE) {
@@ -179,23 +196,25 @@ __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridPara
         const R ic = sizeof(R) == 4 ? (R)sp.inv_cf : (R)(1.0 / sp.c);
         rs = (R)1 / sqrt(ux * ux * ia * ia + uy * uy * ib * ib + uz * uz * ic * ic);
     } else {
-        R raw = sh_radius_unclipped<R>(sp, (R)px, (R)py, (R)pz, rr);
+        const ShTab<R> tb(sp);
+        R raw = sh_radius_unclipped<R>(sp, px, py, pz, rr);
         rs = raw;
-        if (raw < (R)sp.rmin) {
-            rs = (R)sp.rmin;
+        if (raw < tb.rmin) {
+            rs = tb.rmin;
             clip = -1;
-        } else if (raw > (R)sp.rmax) {
-            rs = (R)sp.rmax;
+        } else if (raw > tb.rmax) {
+            rs = tb.rmax;
             clip = 1;
         }
     }
-    chi = (R)1 / ((R)1 + exp(-(rs - rr) * (R)sp.inv_w));
+    const R inv_w = sizeof(R) == 4 ? (R)sp.inv_w_f : (R)sp.inv_w;
+    chi = (R)1 / ((R)1 + exp(-(rs - rr) * inv_w));
 }
 
 // kRun: voxels per lane along z (nz <= 32 kRun), a compile-time bound so the
 // per-lane runs stay in registers.
 template <typename R, int kRun>
-__global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp, GridParams gp,
+__global__ void __launch_bounds__(kGradThreads, 2) grad_voxel_kernel(ShapeParams sp, GridParams gp,
                                                                   const typename Cx<R>::T *__restrict__ S,
                                                                   double *__restrict__ partials) {
     using C = typename Cx<R>::T;
@@ -221,6 +240,12 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
     nm1.x = (R)(-d);
     nm1.y = (R)b;
     const R kdz = (R)(gp.k0 * gp.voxel);
+    // per-voxel constants converted once (FP64 stays off the voxel loop)
+    const R inv_w = sizeof(R) == 4 ? (R)sp.inv_w_f : (R)sp.inv_w;
+    const R R0 = (R)sp.R0, inv_R0 = (R)(1.0 / sp.R0);
+    const R inv_a3 = sp.kind == SCATMAN_ELLIPSOID ? (R)(1.0 / (sp.a * sp.a * sp.a)) : (R)0;
+    const R inv_b3 = sp.kind == SCATMAN_ELLIPSOID ? (R)(1.0 / (sp.b * sp.b * sp.b)) : (R)0;
+    const R inv_c3 = sp.kind == SCATMAN_ELLIPSOID ? (R)(1.0 / (sp.c * sp.c * sp.c)) : (R)0;
     const long long ncols = (long long)gp.nx * gp.ny;
     const long long wstride = (long long)gridDim.x * (kGradThreads / 32);
     for (long long col = (long long)blockIdx.x * (kGradThreads / 32) + warp; col < ncols; col += wstride) {
@@ -297,7 +322,7 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
                 C t1 = cmul(Rv[k], T[k]);
                 C t2 = cmul(nm1, suffix);
                 const R re_chibar = t1.x - kdz * t2.y;
-                const R coef = re_chibar * chi[k] * ((R)1 - chi[k]) * (R)sp.inv_w;
+                const R coef = re_chibar * chi[k] * ((R)1 - chi[k]) * inv_w;
                 C sv;
                 sv.x = chi[k] * T[k].x;
                 sv.y = chi[k] * T[k].y;
@@ -308,18 +333,18 @@ __global__ void __launch_bounds__(kGradThreads) grad_voxel_kernel(ShapeParams sp
                     acc[0] += coef;
                 } else if (sp.kind == SCATMAN_ELLIPSOID) {
                     const R r3 = rs[k] * rs[k] * rs[k];
-                    acc[0] += coef * r3 * ux[k] * ux[k] / (R)(sp.a * sp.a * sp.a);
-                    acc[1] += coef * r3 * uy[k] * uy[k] / (R)(sp.b * sp.b * sp.b);
-                    acc[2] += coef * r3 * uz[k] * uz[k] / (R)(sp.c * sp.c * sp.c);
+                    acc[0] += coef * r3 * ux[k] * ux[k] * inv_a3;
+                    acc[1] += coef * r3 * uy[k] * uy[k] * inv_b3;
+                    acc[2] += coef * r3 * uz[k] * uz[k] * inv_c3;
                 } else if (clip[k] == 0) {
-                    w0 = coef * (R)sp.R0;
+                    w0 = coef * R0;
                     ct = uz[k];
                     st = sqrt(ux[k] * ux[k] + uy[k] * uy[k]);
                     if (st > (R)0) {
                         cph = ux[k] / st;
                         sph = uy[k] / st;
                     }
-                    acc[0] += coef * rs[k] / (R)sp.R0;
+                    acc[0] += coef * rs[k] * inv_R0;
                 } else if (clip[k] < 0) {
                     acc[0] += coef * (R)0.1;
                 }

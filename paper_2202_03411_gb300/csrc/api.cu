@@ -64,6 +64,9 @@ void finish_shape_params(ShapeParams *sp) {
     sp->cyf = (float)sp->cy;
     sp->czf = (float)sp->cz;
     sp->r2f = (float)(sp->r * sp->r);
+    sp->R0f = (float)sp->R0;
+    sp->rminf = (float)sp->rmin;
+    sp->rmaxf = (float)sp->rmax;
     sp->inv_af = sp->a > 0 ? (float)(1.0 / sp->a) : 0.f;
     sp->inv_bf = sp->b > 0 ? (float)(1.0 / sp->b) : 0.f;
     sp->inv_cf = sp->c > 0 ? (float)(1.0 / sp->c) : 0.f;

@@ -41,6 +41,7 @@ struct ShapeParams {
     float Rf[9];                    // the rotation and the offsets in FP32 (fast path)
     float cxf, cyf, czf;
     float r2f, inv_af, inv_bf, inv_cf;   // r^2 and 1/a, 1/b, 1/c in FP32
+    float R0f, rminf, rmaxf;             // harmonics radius scale and clip in FP32
     double alm[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1)];
     float almf[(SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1)];
     // normalised associated-Legendre recurrence coefficients, index l(l+1)/2 + m

@@ -9,11 +9,16 @@ namespace scm {
 template <typename T> struct ShTab;
 template <> struct ShTab<float> {
     const float *a, *b, *d, *e, *alm;
-    __device__ explicit ShTab(const ShapeParams &sp) : a(sp.sh_af), b(sp.sh_bf), d(sp.sh_df), e(sp.sh_ef), alm(sp.almf) {}
+    float R0, rmin, rmax;
+    __device__ explicit ShTab(const ShapeParams &sp)
+        : a(sp.sh_af), b(sp.sh_bf), d(sp.sh_df), e(sp.sh_ef), alm(sp.almf), R0(sp.R0f), rmin(sp.rminf),
+          rmax(sp.rmaxf) {}
 };
 template <> struct ShTab<double> {
     const double *a, *b, *d, *e, *alm;
-    __device__ explicit ShTab(const ShapeParams &sp) : a(sp.sh_a), b(sp.sh_b), d(sp.sh_d), e(sp.sh_e), alm(sp.alm) {}
+    double R0, rmin, rmax;
+    __device__ explicit ShTab(const ShapeParams &sp)
+        : a(sp.sh_a), b(sp.sh_b), d(sp.sh_d), e(sp.sh_e), alm(sp.alm), R0(sp.R0), rmin(sp.rmin), rmax(sp.rmax) {}
 };
 
 // ---------------------------------------------------------------------------
@@ -90,15 +95,16 @@ __device__ __forceinline__ T sh_radius_unclipped(const ShapeParams &sp, T px, T 
     real_sh_all<T>(tb, sp.lmax, ct, st, cphi, sphi, [&](int idx, T y) {
         if (idx > 0) sum += tb.alm[idx] * y;
     });
-    return (T)sp.R0 * ((T)1 + sum);
+    return tb.R0 * ((T)1 + sum);
 }
 
 // The same radius clipped to [rmin, rmax].
 template <typename T>
 __device__ __forceinline__ T sh_radius(const ShapeParams &sp, T px, T py, T pz, T rr) {
     T r = sh_radius_unclipped<T>(sp, px, py, pz, rr);
-    r = r < (T)sp.rmin ? (T)sp.rmin : r;
-    r = r > (T)sp.rmax ? (T)sp.rmax : r;
+    const ShTab<T> tb(sp);
+    r = r < tb.rmin ? tb.rmin : r;
+    r = r > tb.rmax ? tb.rmax : r;
     return r;
 }
 

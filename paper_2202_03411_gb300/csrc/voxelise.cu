@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
 #pragma unroll 1
         for (int st = 0; st < steps; ++st) {
             const int iz = 32 * st + lane;
-            double c = 0.0;
+            Re c = (Re)0;                       // FP32 in the FP32 modes: no FP64 on the common path
             if (iz < nz) {
                 bool decided = false;
                 if (band) {
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
                     const float d = sqrtf(r2xy + zo * zo);
                     const float m = 1e-3f * vox + 1e-5f * d;
                     if (d + m < sp.band_lo) {
-                        c = 1.0;
+                        c = (Re)1;
                         decided = true;
                     } else if (d - m > sp.band_hi) {
                         decided = true;
@@ -109,9 +109,9 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
                 if (!decided) {
                     if (varn) {
                         const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
-                        c = (cell >= 0 && sp.vmap[cell] != 0) ? 1.0 : 0.0;
+                        c = (cell >= 0 && sp.vmap[cell] != 0) ? (Re)1 : (Re)0;
                     } else {
-                        c = occupancy<kFp64, kMaps>(sp, gp, ix, iy, iz);
+                        c = (Re)occupancy<kFp64, kMaps>(sp, gp, ix, iy, iz);
                     }
                 }
                 if (kFp64) srow[iz].x = c;                                // exact copy until pass 2
