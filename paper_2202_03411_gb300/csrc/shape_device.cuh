@@ -33,13 +33,19 @@ template <> struct ShTab<double> {
 // come precomputed in the shape parameters.
 // f(index = l*l+l+m, Y) is called for every (l, m) with l <= L.
 // ---------------------------------------------------------------------------
+// The loops are unrolled to the largest degree with an early exit at L, so
+// every table index and callback index is a compile-time constant (the
+// coefficients become constant-bank operands) while the arithmetic and its
+// order are those of the plain loops.
 template <typename T, typename F>
 __device__ __forceinline__ void real_sh_all(const ShTab<T> &tb, int L, T ct, T st, T cphi, T sphi, F &&f) {
     const T kInvSqrt4Pi = (T)0.28209479177387814347;
     const T kSqrt2 = (T)1.41421356237309504880;
     T pmm = kInvSqrt4Pi;
     T cm = (T)1, sm = (T)0;
-    for (int m = 0; m <= L; ++m) {
+#pragma unroll
+    for (int m = 0; m <= SCATMAN_MAX_LMAX; ++m) {
+        if (m > L) break;
         if (m > 0) {
             pmm = tb.d[m] * st * pmm;
             T c2 = cm * cphi - sm * sphi;
@@ -50,8 +56,9 @@ __device__ __forceinline__ void real_sh_all(const ShTab<T> &tb, int L, T ct, T s
         const T wc = m == 0 ? (T)1 : kSqrt2 * cm;
         const T ws = kSqrt2 * sm;
         T p2 = (T)0, p1 = pmm;
-        const int base = m * (m + 1) / 2;
-        for (int l = m; l <= L; ++l) {
+#pragma unroll
+        for (int l = m; l <= SCATMAN_MAX_LMAX; ++l) {
+            if (l > L) break;
             T p;
             if (l == m) {
                 p = pmm;
@@ -72,7 +79,6 @@ __device__ __forceinline__ void real_sh_all(const ShTab<T> &tb, int L, T ct, T s
                 f(l * l + l - m, p * ws);
             }
         }
-        (void)base;
     }
 }
 
