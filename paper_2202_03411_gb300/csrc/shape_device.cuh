@@ -253,12 +253,12 @@ __device__ __forceinline__ int vmap_cell(const ShapeParams &sp, const GridParams
 // the signed distance to the surface along the ray from the centre.
 // kMaps: compiled for the map kinds (radii and volume maps); the parametric
 // kinds' instantiation carries none of their code.
-template <bool kFp64, bool kMaps = false>
-__device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz) {
+template <bool kFp64, bool kMaps = false, typename OccT = typename std::conditional<kFp64, double, float>::type>
+__device__ __forceinline__ OccT occupancy(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz) {
     if (kMaps && sp.kind == SCATMAN_VOLUMEMAP) {
         // binary in both modes: a volume map has no surface radius
         const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
-        return (cell >= 0 && sp.vmap[cell] != 0) ? 1.0 : 0.0;
+        return (cell >= 0 && sp.vmap[cell] != 0) ? (OccT)1 : (OccT)0;
     }
     if (!sp.soft) {
         if (!kFp64) {
@@ -269,7 +269,7 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
             if (sp.kind == SCATMAN_SPHERE) {
                 const float r2 = sp.r2f;
                 const float m = r2 - (dx * dx + dy * dy + dz * dz);
-                if (fabsf(m) > 1e-4f * r2 + 1e-6f) return m > 0.f ? 1.0 : 0.0;
+                if (fabsf(m) > 1e-4f * r2 + 1e-6f) return m > 0.f ? (OccT)1 : (OccT)0;
             } else {
                 const float px = sp.Rf[0] * dx + sp.Rf[3] * dy + sp.Rf[6] * dz;
                 const float py = sp.Rf[1] * dx + sp.Rf[4] * dy + sp.Rf[7] * dz;
@@ -277,7 +277,7 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
                 if (sp.kind == SCATMAN_ELLIPSOID) {
                     const float u = px * sp.inv_af, v = py * sp.inv_bf, w = pz * sp.inv_cf;
                     const float m = 1.f - (u * u + v * v + w * w);
-                    if (fabsf(m) > 1e-4f) return m > 0.f ? 1.0 : 0.0;
+                    if (fabsf(m) > 1e-4f) return m > 0.f ? (OccT)1 : (OccT)0;
                 } else if (kMaps && sp.kind == SCATMAN_RADIALMAP) {
                     const float rr = sqrtf(px * px + py * py + pz * pz);
                     const float rs = rmap_radius_f(sp, px, py, pz);
@@ -286,16 +286,16 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
                     // centre) times the map's steepest slope, plus rounding
                     const float margin = 4e-3f * vox + 1e-6f * (fabsf(rs) + rr) +
                                          sp.rm_slope * (2e-6f + 2e-5f / fmaxf(rr, vox));
-                    if (fabsf(m) > margin) return m > 0.f ? 1.0 : 0.0;
+                    if (fabsf(m) > margin) return m > 0.f ? (OccT)1 : (OccT)0;
                 } else {
                     const float rr = sqrtf(px * px + py * py + pz * pz);
                     const float rs = sh_radius<float>(sp, px, py, pz, rr);
                     const float m = rs - rr;
-                    if (fabsf(m) > 4e-3f * vox) return m > 0.f ? 1.0 : 0.0;
+                    if (fabsf(m) > 4e-3f * vox) return m > 0.f ? (OccT)1 : (OccT)0;
                 }
             }
         }
-        return occupancy_binary_fp64(sp, gp, ix, iy, iz);
+        return (OccT)occupancy_binary_fp64(sp, gp, ix, iy, iz);
     }
     double px, py, pz;
     if (sp.kind == SCATMAN_SPHERE) {
@@ -320,7 +320,7 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
         } else {
             rs = sh_radius<double>(sp, px, py, pz, rr);
         }
-        return 1.0 / (1.0 + exp(-(rs - rr) * sp.inv_w));
+        return (OccT)(1.0 / (1.0 + exp(-(rs - rr) * sp.inv_w)));
     }
     float rf = (float)rr, rs;
     if (sp.kind == SCATMAN_SPHERE) {
@@ -335,7 +335,7 @@ __device__ __forceinline__ double occupancy(const ShapeParams &sp, const GridPar
     } else {
         rs = sh_radius<float>(sp, (float)px, (float)py, (float)pz, rf);
     }
-    return (double)(1.0f / (1.0f + __expf(-(rs - rf) * sp.inv_w_f)));
+    return (OccT)(1.0f / (1.0f + __expf(-(rs - rf) * sp.inv_w_f)));
 }
 
 }  // namespace scm
