@@ -164,7 +164,7 @@ __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridPara
             body_coords(sp, gp, ix, iy, iz, px, py, pz);
         }
     } else {
-        const float vox = (float)gp.voxel;
+        const float vox = gp.voxf;
         const float dx = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
         const float dy = ((float)iy - 0.5f * (float)(gp.ny - 1)) * vox - sp.cyf;
         const float dz = ((float)iz - 0.5f * (float)(gp.nz - 1)) * vox - sp.czf;

@@ -533,7 +533,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     if (rc) return rc;
     set_radius_band(s, &sp);
 
-    GridParams gp{c.nx, c.ny, c.nz, c.voxel, h->k0, s->delta, s->beta};
+    const GridParams gp = make_grid(c.nx, c.ny, c.nz, c.voxel, h->k0, s->delta, s->beta);
     SliceOut so;
     so.layout = h->precision == SCATMAN_FP64 ? kLayoutC64
                 : !h->tensor_core ? kLayoutC32
@@ -792,7 +792,7 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
         if ((rc = alloc_dev(h, &h->d_S, nvox * (f64 ? sizeof(double2) : sizeof(float2)), "adjoint field")))
             return rc;
     }
-    GridParams gp{c.nx, c.ny, c.nz, c.voxel, h->k0, h->shape.delta, h->shape.beta};
+    const GridParams gp = make_grid(c.nx, c.ny, c.nz, c.voxel, h->k0, h->shape.delta, h->shape.beta);
     const int ng = grad_param_count(h->sp);
     const int nvb = grad_voxel_blocks(gp), npb = grad_pixel_blocks(h->n_pix);
     const size_t need = (size_t)nvb * (ng + 2) + (size_t)npb;
@@ -1024,7 +1024,7 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
     if (s->kind == SCATMAN_SPHHARM)
         for (int k = 0; k < (s->lmax + 1) * (s->lmax + 1); ++k) sp.alm[k] = s->alm[k];
     finish_shape_params(&sp);
-    GridParams gp{c.nx, c.ny, c.nz, c.voxel, k0, s->delta, s->beta};
+    const GridParams gp = make_grid(c.nx, c.ny, c.nz, c.voxel, k0, s->delta, s->beta);
     SliceOut so;
     so.layout = kLayoutC32;
     so.Nxp = so.Nyp = so.Kp = 0;

@@ -95,7 +95,13 @@ struct GridParams {
     double voxel;
     double k0;
     double delta, beta;
+    float voxf;                     // voxel in FP32 (set by make_grid)
 };
+
+inline GridParams make_grid(int nx, int ny, int nz, double voxel, double k0, double delta, double beta) {
+    GridParams g{nx, ny, nz, voxel, k0, delta, beta, (float)voxel};
+    return g;
+}
 
 // Where the voxeliser writes s = chi*T.
 enum SliceLayout { kLayoutC64 = 0, kLayoutC32 = 1, kLayoutTcF16 = 2, kLayoutTcBF16 = 3 };

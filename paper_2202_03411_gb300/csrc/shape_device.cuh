@@ -218,7 +218,7 @@ static __device__ __noinline__ double occupancy_binary_fp64(const ShapeParams &s
 template <bool kFp64>
 __device__ __forceinline__ int vmap_cell(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz) {
     if (!kFp64) {
-        const float vox = (float)gp.voxel;
+        const float vox = gp.voxf;
         const float dx = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
         const float dy = ((float)iy - 0.5f * (float)(gp.ny - 1)) * vox - sp.cyf;
         const float dz = ((float)iz - 0.5f * (float)(gp.nz - 1)) * vox - sp.czf;
@@ -253,7 +253,10 @@ __device__ __forceinline__ int vmap_cell(const ShapeParams &sp, const GridParams
 // the signed distance to the surface along the ray from the centre.
 // kMaps: compiled for the map kinds (radii and volume maps); the parametric
 // kinds' instantiation carries none of their code.
-template <bool kFp64, bool kMaps = false, typename OccT = typename std::conditional<kFp64, double, float>::type>
+// kDefer (FP32 modes): a binary voxel the FP32 test cannot settle returns -1
+// instead of taking the FP64 path here, so the caller can batch those voxels.
+template <bool kFp64, bool kMaps = false, bool kDefer = false,
+          typename OccT = typename std::conditional<kFp64, double, float>::type>
 __device__ __forceinline__ OccT occupancy(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz) {
     if (kMaps && sp.kind == SCATMAN_VOLUMEMAP) {
         // binary in both modes: a volume map has no surface radius
@@ -262,7 +265,7 @@ __device__ __forceinline__ OccT occupancy(const ShapeParams &sp, const GridParam
     }
     if (!sp.soft) {
         if (!kFp64) {
-            const float vox = (float)gp.voxel;
+            const float vox = gp.voxf;
             const float dx = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
             const float dy = ((float)iy - 0.5f * (float)(gp.ny - 1)) * vox - sp.cyf;
             const float dz = ((float)iz - 0.5f * (float)(gp.nz - 1)) * vox - sp.czf;
@@ -295,6 +298,7 @@ __device__ __forceinline__ OccT occupancy(const ShapeParams &sp, const GridParam
                 }
             }
         }
+        if (kDefer && !kFp64) return (OccT)-1;
         return (OccT)occupancy_binary_fp64(sp, gp, ix, iy, iz);
     }
     double px, py, pz;

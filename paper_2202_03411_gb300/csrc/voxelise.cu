@@ -46,18 +46,33 @@ cudaError_t launch_detector_q(int det_nx, int det_ny, double theta_max_deg, doub
 constexpr int kLinesPerCta = 32;
 constexpr int kVoxThreads = 256;
 constexpr int kMaxRun = 8;          // z values per lane: nz <= 256
+constexpr int kVoxQueue = 512;      // binary voxels per CTA whose FP64 decision is batched
 
 // s_j = chi_j T_j with T_j = exp(i k0 dz (n-1) C_j) = e^{-k0 dz beta C} e^{-i k0 dz delta C}.
 // A warp takes one (x, y) line at a time; its lanes take 32 consecutive z per
 // step, so neighbouring lanes hold neighbouring voxels (and binary shapes can
 // skip the surface radius where the whole step is clearly inside or outside).
-// Pass 1 renders chi into shared memory; pass 2 forms the exclusive prefix
-// C_j with a warp scan per step plus the running total of earlier steps, then
-// T_j and s_j.  Tiles are [line][z] with a padded row, so both the z-walk and
-// the line-fastest output loop are free of bank conflicts.
+// Pass 1 renders chi into shared memory for all of the CTA's lines; in the
+// FP32 modes the few binary voxels too close to the surface for the FP32 test
+// are queued and decided in FP64 afterwards by whole warps (a lone lane in
+// the FP64 path would hold its warp for the full FP64 radius).  Pass 2 forms
+// the exclusive prefix C_j with a warp scan per step plus the running total
+// of earlier steps, then T_j and s_j.  Tiles are [line][z] with a padded row,
+// so both the z-walk and the line-fastest output loop are free of bank
+// conflicts.
+// Per-launch constants of the scan, formed on the host in FP64 and handed
+// over in both precisions (no FP64 arithmetic in the kernel's prologue).
+struct VoxConst {
+    double att, ph, kdz, inv_scale;         // k0 dz beta, k0 dz delta, k0 dz, 1 / nscale
+    float att_f, ph_f, kdz_f, inv_scale_f;
+};
+template <typename T> __device__ __forceinline__ T vc_pick(double d, float f);
+template <> __device__ __forceinline__ double vc_pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float vc_pick<float>(double, float f) { return f; }
+
 template <bool kFp64, typename ScanT, bool kMaps>
 __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapeParams sp, GridParams gp,
-                                                                    SliceOut out) {
+                                                                    SliceOut out, VoxConst vc) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int nz = gp.nz;
     const int zs = nz + 1;                                                    // padded row
@@ -65,19 +80,23 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
     using Re = typename std::conditional<kFp64, double, float>::type;
     Cx *s_tile = reinterpret_cast<Cx *>(smem);                                // [32][zs]
     float *chi_tile = reinterpret_cast<float *>(smem + sizeof(Cx) * zs * kLinesPerCta);
+    int *queue = reinterpret_cast<int *>(chi_tile + (size_t)zs * kLinesPerCta);   // (line << 16) | z
+    __shared__ int s_qn;
+    if (threadIdx.x == 0) s_qn = 0;
+    __syncthreads();
 
     const int ix = blockIdx.x;
     const int y0 = blockIdx.y * kLinesPerCta;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int steps = (nz + 31) / 32;
-    const ScanT a_att = (ScanT)(gp.k0 * gp.voxel * gp.beta);     // attenuation per unit C
-    const ScanT a_ph = (ScanT)(gp.k0 * gp.voxel * gp.delta);     // phase per unit C
+    const ScanT a_att = vc_pick<ScanT>(vc.att, vc.att_f);         // attenuation per unit C
+    const ScanT a_ph = vc_pick<ScanT>(vc.ph, vc.ph_f);             // phase per unit C
     const bool varn = kMaps && sp.varn != 0;                      // per-cell index of a volume map
-    const ScanT kdz = (ScanT)(gp.k0 * gp.voxel);
-    const Re inv_scale = (Re)(1.0 / sp.nscale);
+    const ScanT kdz = vc_pick<ScanT>(vc.kdz, vc.kdz_f);
+    const Re inv_scale = vc_pick<Re>(vc.inv_scale, vc.inv_scale_f);
     // radius band of a binary harmonics or radii-map shape: inside below lo, outside above hi
     const bool band = !sp.soft && sp.band_hi > 0.f;
-    const float vox = (float)gp.voxel;
+    const float vox = gp.voxf;
     const float xo = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
 
     for (int yl = warp; yl < kLinesPerCta; yl += kVoxThreads / 32) {
@@ -111,14 +130,39 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
                         const int cell = vmap_cell<kFp64>(sp, gp, ix, iy, iz);
                         c = (cell >= 0 && sp.vmap[cell] != 0) ? (Re)1 : (Re)0;
                     } else {
-                        c = (Re)occupancy<kFp64, kMaps>(sp, gp, ix, iy, iz);
+                        c = (Re)occupancy<kFp64, kMaps, true>(sp, gp, ix, iy, iz);
+                        if (!kFp64 && c < (Re)0) {
+                            // too close to the surface for FP32: queue it (inline when full)
+                            const int slot = atomicAdd(&s_qn, 1);
+                            if (slot < kVoxQueue)
+                                queue[slot] = (yl << 16) | iz;
+                            else
+                                c = (Re)occupancy_binary_fp64(sp, gp, ix, iy, iz);
+                        }
                     }
                 }
                 if (kFp64) srow[iz].x = c;                                // exact copy until pass 2
                 crow[iz] = (float)c;
             }
         }
-        __syncwarp();
+    }
+    __syncthreads();
+    if (!kFp64) {
+        // the queued voxels' FP64 decisions, one voxel per thread
+        const int qn = min(s_qn, kVoxQueue);
+        for (int k = threadIdx.x; k < qn; k += kVoxThreads) {
+            const int e = queue[k];
+            const int yl = e >> 16, iz = e & 0xffff;
+            chi_tile[(size_t)yl * zs + iz] = (float)occupancy_binary_fp64(sp, gp, ix, y0 + yl, iz);
+        }
+        __syncthreads();
+    }
+
+    for (int yl = warp; yl < kLinesPerCta; yl += kVoxThreads / 32) {
+        const int iy = y0 + yl;
+        if (iy >= gp.ny) break;
+        Cx *srow = s_tile + (size_t)yl * zs;
+        float *crow = chi_tile + (size_t)yl * zs;
         // pass 2: exclusive prefix along z, transmission, slice value
         ScanT carry = (ScanT)0, carry_d = (ScanT)0, carry_b = (ScanT)0;
 #pragma unroll 1
@@ -250,17 +294,26 @@ cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const S
     if (out.bounds) bounds_init_kernel<<<(4 * gp.nz + 255) / 256, 256, 0, st>>>(out.bounds, gp.nz);
     dim3 grid(gp.nx, (gp.ny + kLinesPerCta - 1) / kLinesPerCta);
     size_t cx = fp64_mode ? sizeof(double2) : sizeof(float2);
-    size_t smem = (cx + sizeof(float)) * (size_t)(gp.nz + 1) * kLinesPerCta;
+    size_t smem = (cx + sizeof(float)) * (size_t)(gp.nz + 1) * kLinesPerCta + kVoxQueue * sizeof(int);
     // per-function attribute shared by all threads: set it to the largest size
     // (nz = 256) so a concurrent launch from another thread is never rejected
-    const int smem_max = (int)((cx + sizeof(float)) * (32 * kMaxRun + 1) * kLinesPerCta);
+    const int smem_max = (int)((cx + sizeof(float)) * (32 * kMaxRun + 1) * kLinesPerCta + kVoxQueue * sizeof(int));
     const bool maps = sp.kind == SCATMAN_RADIALMAP || sp.kind == SCATMAN_VOLUMEMAP;
     auto k = fp64_mode   ? (maps ? voxelise_scan_kernel<true, double, true> : voxelise_scan_kernel<true, double, false>)
              : scan_fp64 ? (maps ? voxelise_scan_kernel<false, double, true> : voxelise_scan_kernel<false, double, false>)
                          : (maps ? voxelise_scan_kernel<false, float, true> : voxelise_scan_kernel<false, float, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
     if (e != cudaSuccess) return e;
-    k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out);
+    VoxConst vc;
+    vc.att = gp.k0 * gp.voxel * gp.beta;
+    vc.ph = gp.k0 * gp.voxel * gp.delta;
+    vc.kdz = gp.k0 * gp.voxel;
+    vc.inv_scale = sp.nscale != 0.0 ? 1.0 / sp.nscale : 0.0;
+    vc.att_f = (float)vc.att;
+    vc.ph_f = (float)vc.ph;
+    vc.kdz_f = (float)vc.kdz;
+    vc.inv_scale_f = (float)vc.inv_scale;
+    k<<<grid, kVoxThreads, smem, st>>>(sp, gp, out, vc);
     return cudaGetLastError();
 }
 
