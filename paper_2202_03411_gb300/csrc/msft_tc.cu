@@ -26,6 +26,13 @@
 // TMA producer, warps 9 and 10 issue the MMAs of alternate slices (warp 9
 // owns the tensor memory).  The roles
 // meet only at mbarriers, so the producer runs ahead across pixel tiles.
+// Work comes in units of one pixel tile and a range of its occupied slices:
+// whole tiles, except that the last partial wave's tiles are cut into up to
+// four slice ranges whose partial fields tc_tail_sum_kernel adds, so that
+// wave fills the SMs.  The same kernel in store mode is the uniform-q
+// detector's y-sum: its rows are detector rows, every tile is cut into
+// slice ranges (slices are independent there) and the epilogue writes the
+// accumulators as 16-bit operand planes instead of reducing them.
 // Every wait is bounded: on time-out the kernel sets a bit in the error word,
 // releases its tensor memory and returns.
 #include "internal.cuh"
