@@ -2,15 +2,19 @@
 // GPU (continuous admission under a device-memory budget).
 //
 // Threads: one scheduler thread owns admission; each slot owns a host thread
-// and a CUDA stream and runs its requests one after another.  A request is
-// admitted when a slot is idle and the bytes that slot must hold for it fit
-// under the budget.  Slots keep the handle (and fit buffers) of their last
-// geometry; idle slots' handles are evicted when the budget needs room.
-// Requests therefore overlap on the device as far as slots and memory allow,
-// and new arrivals are taken in as soon as either frees up.
+// and a CUDA stream and runs its requests one after another.  Handles (with a
+// fit's buffers) live in a server-wide cache keyed by geometry: a request
+// takes an idle handle of its geometry when there is one, else the slot
+// creates one, and after the request the handle goes back to the cache, so
+// a steady mix of geometries runs without device allocations (which stall
+// every stream).  A request is admitted when a slot is idle and, if it needs
+// a new handle, the handle's bytes fit under the budget after evicting idle
+// handles, least recently used first.  Requests therefore overlap on the
+// device as far as slots and memory allow, and new arrivals are taken in as
+// soon as either frees up.
 //
-// Accounting: `reserved` is the sum over slots of `held`, the bytes a slot
-// holds or has been promised for its current geometry.
+// Accounting: `reserved` is the sum of the bytes of every handle in existence
+// (idle, in use, or promised to a slot that is creating it).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -39,6 +43,17 @@ struct GeomKey {
     bool operator==(const GeomKey &o) const { return !(*this < o) && !(o < *this); }
 };
 
+// A handle and its fit buffers for one geometry.
+struct Cached {
+    GeomKey key;
+    scatman_handle *h = nullptr;
+    float *d_target = nullptr;
+    void *d_w = nullptr;
+    double *d_loss = nullptr;
+    long long bytes = 0;            // accounted bytes
+    unsigned long long last_use = 0;
+};
+
 struct Req {
     long long ticket = 0;
     scatman_config cfg;
@@ -54,6 +69,7 @@ struct Req {
     Clock::time_point t_submit, t_done;
     bool done = false;
     int status = SCATMAN_OK;
+    std::unique_ptr<Cached> handle; // from the cache, or null: the slot creates one of `need` bytes
 };
 
 struct Slot {
@@ -61,13 +77,6 @@ struct Slot {
     cudaStream_t stream = nullptr;
     std::thread thr;
     std::shared_ptr<Req> job;       // set by the scheduler, cleared by the slot
-    long long held = 0;             // bytes accounted to this slot
-    bool has_cache = false;         // a handle for `key` exists
-    GeomKey key{};
-    scatman_handle *h = nullptr;
-    float *d_target = nullptr;
-    void *d_w = nullptr;
-    double *d_loss = nullptr;
 };
 
 static long long round_2mib(long long b) {
@@ -85,6 +94,8 @@ struct scatman_server {
     std::deque<std::shared_ptr<scm::Req>> queue;
     std::map<long long, std::shared_ptr<scm::Req>> reqs;
     std::vector<std::unique_ptr<scm::Slot>> slots;
+    std::vector<std::unique_ptr<scm::Cached>> idle;   // handles not in use
+    unsigned long long use_clock = 0;
     std::thread sched;
     bool stopping = false;
     bool sched_done = false;
@@ -109,66 +120,69 @@ static long long slot_bytes(const scatman_config &c, int precision, double width
     return fp + round_2mib(npix * 4) + round_2mib(npix * elem) + round_2mib(256 * 8);
 }
 
-static void free_cache(Slot &s) {
-    if (s.h) scatman_destroy(s.h);
-    if (s.d_target) cudaFree(s.d_target);
-    if (s.d_w) cudaFree(s.d_w);
-    if (s.d_loss) cudaFree(s.d_loss);
-    s.h = nullptr;
-    s.d_target = nullptr;
-    s.d_w = nullptr;
-    s.d_loss = nullptr;
-    s.has_cache = false;
+static void free_cached(Cached &c) {
+    if (c.h) scatman_destroy(c.h);
+    if (c.d_target) cudaFree(c.d_target);
+    if (c.d_w) cudaFree(c.d_w);
+    if (c.d_loss) cudaFree(c.d_loss);
+    c.h = nullptr;
+    c.d_target = nullptr;
+    c.d_w = nullptr;
+    c.d_loss = nullptr;
 }
 
-// Runs one request on the slot's stream; returns the request's status.
-static int run_request(const scatman_server_config &scfg, Slot &s, Req &r) {
-    const int prec = scfg.precision;
-    const bool f64 = prec == SCATMAN_FP64;
-    if (!s.has_cache || !(s.key == r.key)) {
-        free_cache(s);
-        scatman_config c = r.cfg;
-        c.precision = prec;
-        c.soft = 1;
-        c.soft_width = scfg.soft_width;
-        c.q_list = nullptr;
-        c.n_q = 0;
-        int rc = scatman_create(&c, s.stream, &s.h);
-        if (rc) {
-            s.h = nullptr;
-            return rc;
-        }
-        const long long n = s.h->n_pix;
-        if (cudaMalloc((void **)&s.d_target, n * sizeof(float)) != cudaSuccess ||
-            cudaMalloc(&s.d_w, n * (f64 ? 8 : 4)) != cudaSuccess ||
-            cudaMalloc((void **)&s.d_loss, 256 * sizeof(double)) != cudaSuccess) {
-            free_cache(s);
-            return SCATMAN_ERR_OOM;
-        }
-        s.has_cache = true;
-        s.key = r.key;
+// A new handle and fit buffers for the request's geometry on the slot's stream.
+static int create_cached(const scatman_server_config &scfg, Slot &s, const Req &r, Cached &c) {
+    const bool f64 = scfg.precision == SCATMAN_FP64;
+    scatman_config cfg = r.cfg;
+    cfg.precision = scfg.precision;
+    cfg.soft = 1;
+    cfg.soft_width = scfg.soft_width;
+    cfg.q_list = nullptr;
+    cfg.n_q = 0;
+    c.key = r.key;
+    int rc = scatman_create(&cfg, s.stream, &c.h);
+    if (rc) {
+        c.h = nullptr;
+        return rc;
     }
-    scatman_handle *h = s.h;
+    const long long n = c.h->n_pix;
+    if (cudaMalloc((void **)&c.d_target, n * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&c.d_w, n * (f64 ? 8 : 4)) != cudaSuccess ||
+        cudaMalloc((void **)&c.d_loss, 256 * sizeof(double)) != cudaSuccess) {
+        free_cached(c);
+        return SCATMAN_ERR_OOM;
+    }
+    return SCATMAN_OK;
+}
+
+// Runs one request on the slot's stream with handle `c`; returns the status.
+static int run_request(const scatman_server_config &scfg, Slot &s, Req &r, Cached &c) {
+    const bool f64 = scfg.precision == SCATMAN_FP64;
+    scatman_handle *h = c.h;
+    // a cached handle may come from another slot: its work is finished, and
+    // the handle was created on a caller-owned stream, so it can move
+    h->stream = s.stream;
     const long long n = h->n_pix;
     r.shape.alm = r.alm.empty() ? nullptr : r.alm.data();
     int rc = scatman_voxelise(h, &r.shape);
     if (rc) return rc;
     rc = scatman_forward(h, h->d_I, nullptr);
     if (rc) return rc;
-    if (cudaMemcpyAsync(s.d_target, r.target.data(), n * sizeof(float), cudaMemcpyHostToDevice, s.stream) !=
+    if (cudaMemcpyAsync(c.d_target, r.target.data(), n * sizeof(float), cudaMemcpyHostToDevice, s.stream) !=
         cudaSuccess)
         return SCATMAN_ERR_CUDA;
     const int nb = l2_residual_blocks(n);
-    if (launch_l2_residual(f64, h->d_I, s.d_target, n, s.d_w, s.d_loss, nb, s.stream) != cudaSuccess)
+    if (launch_l2_residual(f64, h->d_I, c.d_target, n, c.d_w, c.d_loss, nb, s.stream) != cudaSuccess)
         return SCATMAN_ERR_CUDA;
     std::vector<double> grad;
     if (r.want_gradient) {
         grad.resize(scatman_param_count(h));
-        rc = scatman_backward(h, s.d_w, grad.data());
+        rc = scatman_backward(h, c.d_w, grad.data());
         if (rc) return rc;
     }
     std::vector<double> loss_part(nb);
-    if (cudaMemcpyAsync(loss_part.data(), s.d_loss, nb * sizeof(double), cudaMemcpyDeviceToHost, s.stream) !=
+    if (cudaMemcpyAsync(loss_part.data(), c.d_loss, nb * sizeof(double), cudaMemcpyDeviceToHost, s.stream) !=
         cudaSuccess)
         return SCATMAN_ERR_CUDA;
     std::vector<double> Id;
@@ -200,13 +214,23 @@ static void slot_main(scatman_server *srv, Slot *s) {
         srv->cv.wait(lk, [&] { return s->job != nullptr || srv->sched_done; });
         if (!s->job) break;
         std::shared_ptr<Req> r = s->job;
+        std::unique_ptr<Cached> c = std::move(r->handle);
+        const long long promised = r->need;
         lk.unlock();
-        const int st = run_request(srv->cfg, *s, *r);
-        if (st != SCATMAN_OK) free_cache(*s);          // never keep a handle in an unknown state
+        int st = SCATMAN_OK;
+        if (!c) {
+            c = std::make_unique<Cached>();
+            c->bytes = promised;
+            st = create_cached(srv->cfg, *s, *r, *c);
+        }
+        if (st == SCATMAN_OK) st = run_request(srv->cfg, *s, *r, *c);
+        if (st != SCATMAN_OK) free_cached(*c);          // never keep a handle in an unknown state
         lk.lock();
-        if (!s->has_cache) {
-            srv->reserved -= s->held;
-            s->held = 0;
+        if (st == SCATMAN_OK) {
+            c->last_use = ++srv->use_clock;
+            srv->idle.push_back(std::move(c));
+        } else {
+            srv->reserved -= c->bytes;
         }
         r->status = st;
         r->t_done = Clock::now();
@@ -235,30 +259,30 @@ static void sched_main(scatman_server *srv) {
         if (srv->queue.empty()) break;                   // stopping and drained
         std::shared_ptr<Req> r = srv->queue.front();
         Slot *pick = nullptr;
-        for (auto &s : srv->slots)                       // an idle slot that already holds this geometry
-            if (!s->job && s->has_cache && s->key == r->key) { pick = s.get(); break; }
-        long long delta = 0;
-        if (!pick) {
-            for (auto &s : srv->slots)                   // else an empty idle slot
-                if (!s->job && s->held == 0) { pick = s.get(); break; }
-            if (!pick)
-                for (auto &s : srv->slots)               // else the idle slot holding the most bytes
-                    if (!s->job && (!pick || s->held > pick->held)) pick = s.get();
-            delta = r->need - pick->held;
-            if (srv->reserved + delta > budget) {
-                // make room: release other idle slots' handles, largest first
-                std::vector<Slot *> idle;
-                for (auto &s : srv->slots)
-                    if (!s->job && s.get() != pick && s->held > 0) idle.push_back(s.get());
-                std::sort(idle.begin(), idle.end(), [](Slot *a, Slot *b) { return a->held > b->held; });
-                for (Slot *s : idle) {
-                    if (srv->reserved + delta <= budget) break;
-                    free_cache(*s);
-                    srv->reserved -= s->held;
-                    s->held = 0;
+        for (auto &s : srv->slots)
+            if (!s->job) { pick = s.get(); break; }
+        // an idle handle of this geometry, most recently used first
+        int best = -1;
+        for (int i = 0; i < (int)srv->idle.size(); ++i)
+            if (srv->idle[i]->key == r->key && (best < 0 || srv->idle[i]->last_use > srv->idle[best]->last_use))
+                best = i;
+        if (best >= 0) {
+            r->handle = std::move(srv->idle[best]);
+            srv->idle.erase(srv->idle.begin() + best);
+        } else {
+            if (srv->reserved + r->need > budget) {
+                // make room: release idle handles, least recently used first
+                std::sort(srv->idle.begin(), srv->idle.end(),
+                          [](const std::unique_ptr<Cached> &a, const std::unique_ptr<Cached> &b) {
+                              return a->last_use > b->last_use;
+                          });
+                while (!srv->idle.empty() && srv->reserved + r->need > budget) {
+                    free_cached(*srv->idle.back());
+                    srv->reserved -= srv->idle.back()->bytes;
+                    srv->idle.pop_back();
                 }
             }
-            if (srv->reserved + delta > budget) {
+            if (srv->reserved + r->need > budget) {
                 bool any_busy = false;
                 for (auto &s : srv->slots) any_busy |= (s->job != nullptr);
                 if (!any_busy) {                          // cannot fit even alone
@@ -273,8 +297,7 @@ static void sched_main(scatman_server *srv) {
                 srv->cv.wait(lk);                        // wait for a completion and retry
                 continue;
             }
-            srv->reserved += delta;
-            pick->held = r->need;
+            srv->reserved += r->need;                    // the slot creates the handle
         }
         srv->queue.pop_front();
         pick->job = r;
@@ -445,10 +468,9 @@ void scatman_server_destroy(scatman_server *srv) {
     if (srv->sched.joinable()) srv->sched.join();
     for (auto &s : srv->slots)
         if (s->thr.joinable()) s->thr.join();
-    for (auto &s : srv->slots) {
-        free_cache(*s);
-        cudaStreamDestroy(s->stream);
-    }
+    for (auto &c : srv->idle) free_cached(*c);
+    srv->idle.clear();
+    for (auto &s : srv->slots) cudaStreamDestroy(s->stream);
     delete srv;
 }
 
