@@ -15,8 +15,8 @@
 // copied into each stage with one bulk copy; the x-phase operand L depends on
 // the slice and the weights, so eight generator warps build it in shared
 // memory (phase recurrences, FP16 with |L| <= 1), rows x < nx only (padding
-// rows feed output rows that are never written back), while one MMA warp
-// consumes the previous stages.  Per-pixel constants (q split into FP32 pairs,
+// rows feed output rows that are never written back), in teams of two that
+// take successive chunks, while one MMA warp consumes the finished stages.  Per-pixel constants (q split into FP32 pairs,
 // one-voxel rotations) come from a table built once per handle, so the
 // generators do no FP64 work.  A CTA owns two slices (two TMEM accumulators
 // sharing every R tile) and a contiguous range of pixels; the pixel ranges'
@@ -27,6 +27,7 @@
 namespace scm {
 
 constexpr int kAdjGenWarps = 8;             // build the x-phase operand, then the epilogue
+constexpr int kAdjGenTeams = kAdjGenWarps / 2;   // two warps (half the rows each) build one chunk
 constexpr int kAdjLoadWarp = kAdjGenWarps;  // bulk-copies the y-phase operand
 constexpr int kAdjMmaWarp = kAdjGenWarps + 1;
 constexpr int kAdjThreads = (kAdjGenWarps + 2) * 32;
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(smem_u32(&full[s]), kAdjGenWarps);
+            mbar_init(smem_u32(&full[s]), 2);
             mbar_init(smem_u32(&bfull[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
@@ -210,11 +211,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         __syncwarp();
     } else {
         // ---------------- generator warps: the x-phase operand ----------------
+        // Teams of two warps take whole chunks in turn (chunk c: team c % 4),
+        // each warp half of the rows, so a lane's per-chunk set-up (weights,
+        // start phases) serves half the rows instead of an eighth.
         const float inv_g = 1.0f / fmaxf(__uint_as_float(*P.gmax_bits), 1e-30f);
         const int i = lane;                      // pixel within the chunk
+        const int team = warp >> 1;
         // rows r0 .. r1 - 1 of both slices' L tiles (x < nx only)
-        const int ra = (P.nx + kAdjGenWarps - 1) / kAdjGenWarps;
-        const int r0 = warp * ra, r1 = min(P.nx, r0 + ra);
+        const int ra = (P.nx + 1) / 2;
+        const int r0 = (warp & 1) * ra, r1 = min(P.nx, r0 + ra);
         const float vox = (float)P.voxel;
         const float x0 = ((float)r0 - 0.5f * (float)(P.nx - 1)) * vox;
         const float zj = ((float)j0 - 0.5f * (P.nz - 1)) * vox;
@@ -237,12 +242,12 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
                 ta_n = tb_n = tc_n = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         };
-        load_pixel(0);
-        for (int c = 0; c < n_chunks; ++c) {
+        load_pixel(team);
+        for (int c = team; c < n_chunks; c += kAdjGenTeams) {
             const float2 a_c = a_n;
             const float w_c = w_n;
             const float4 ta = ta_n, tb = tb_n, tcv = tc_n;
-            load_pixel(c + 1);
+            load_pixel(c + kAdjGenTeams);
             const uint32_t s = c % NS, ph = (c / NS) & 1;
             if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutEpilogue)) break;
             uint8_t *sA0 = base + s * stage_bytes;
