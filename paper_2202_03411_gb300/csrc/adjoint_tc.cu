@@ -27,7 +27,6 @@
 namespace scm {
 
 constexpr int kAdjGenWarps = 8;             // build the x-phase operand, then the epilogue
-constexpr int kAdjGenTeams = kAdjGenWarps / 2;   // two warps (half the rows each) build one chunk
 constexpr int kAdjLoadWarp = kAdjGenWarps;  // bulk-copies the y-phase operand
 constexpr int kAdjMmaWarp = kAdjGenWarps + 1;
 constexpr int kAdjThreads = (kAdjGenWarps + 2) * 32;
@@ -41,6 +40,7 @@ struct AdjParams {
     const float4 *tab;          // per pixel: (qxh, qxl, qyh, qyl), (qzh, qzl, e^{+i qx dv}), (e^{+i qy dv}, e^{+i qz dv})
     const uint8_t *rtile;       // per 32-pixel chunk: the y-phase operand tile (2 Nyp rows x 128 bytes)
     int stages;
+    int teams;                  // generator teams (1, 2 or 4; never more than stages)
     const float2 *A;            // forward field (FP32)
     const float *w;             // dL/dI
     const unsigned *gmax_bits;  // max |w A| as float bits
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(smem_u32(&full[s]), 2);
+            mbar_init(smem_u32(&full[s]), kAdjGenWarps / P.teams);
             mbar_init(smem_u32(&bfull[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
@@ -211,15 +211,19 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         __syncwarp();
     } else {
         // ---------------- generator warps: the x-phase operand ----------------
-        // Teams of two warps take whole chunks in turn (chunk c: team c % 4),
-        // each warp half of the rows, so a lane's per-chunk set-up (weights,
-        // start phases) serves half the rows instead of an eighth.
+        // Teams of warps take whole chunks in turn (chunk c: team c % teams),
+        // each warp a share of the rows, so a lane's per-chunk set-up (weights,
+        // start phases) serves more rows.  A team's next chunk reuses a stage
+        // only after the chunk `stages` earlier has been consumed, which with
+        // teams <= stages keeps every stage barrier within one phase of its
+        // waiters (the parity waits need that).
         const float inv_g = 1.0f / fmaxf(__uint_as_float(*P.gmax_bits), 1e-30f);
         const int i = lane;                      // pixel within the chunk
-        const int team = warp >> 1;
+        const int per_team = kAdjGenWarps / P.teams;
+        const int team = warp / per_team;
         // rows r0 .. r1 - 1 of both slices' L tiles (x < nx only)
-        const int ra = (P.nx + 1) / 2;
-        const int r0 = (warp & 1) * ra, r1 = min(P.nx, r0 + ra);
+        const int ra = (P.nx + per_team - 1) / per_team;
+        const int r0 = (warp % per_team) * ra, r1 = min(P.nx, r0 + ra);
         const float vox = (float)P.voxel;
         const float x0 = ((float)r0 - 0.5f * (float)(P.nx - 1)) * vox;
         const float zj = ((float)j0 - 0.5f * (P.nz - 1)) * vox;
@@ -243,11 +247,11 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
             }
         };
         load_pixel(team);
-        for (int c = team; c < n_chunks; c += kAdjGenTeams) {
+        for (int c = team; c < n_chunks; c += P.teams) {
             const float2 a_c = a_n;
             const float w_c = w_n;
             const float4 ta = ta_n, tb = tb_n, tcv = tc_n;
-            load_pixel(c + kAdjGenTeams);
+            load_pixel(c + P.teams);
             const uint32_t s = c % NS, ph = (c / NS) & 1;
             if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag, P.err, kErrTimeoutEpilogue)) break;
             uint8_t *sA0 = base + s * stage_bytes;
@@ -403,6 +407,7 @@ cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab
     P.Nyp = adj_nyp(ny);
     if (!adjoint_tc_supported(nx, ny)) return cudaErrorInvalidValue;
     P.stages = adj_stages(P.Nyp);
+    P.teams = P.stages >= 4 ? 4 : P.stages >= 2 ? 2 : 1;
     const long long chunks = (n_pix + kAdjChunk - 1) / kAdjChunk;
     P.pix_per_split = (int)((chunks + splits - 1) / splits) * kAdjChunk;
     P.voxel = voxel;

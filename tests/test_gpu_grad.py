@@ -138,3 +138,21 @@ def test_gradient_full_size_harmonics_96(prec, full_size_case):
     ref = oracle.gradient(s, g, 2 * (I_gpu - target), A, width=width)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err < GTOL[prec], err
+
+
+@pytest.mark.parametrize("ny", [72, 128])
+def test_gradient_tensor_core_adjoint_stage_counts(ny):
+    """The tensor-core adjoint at y extents whose operand stages leave four
+    (ny = 72) and three (ny = 128) pipeline stages, so both generator team
+    layouts run, with enough pixels for many chunks per team."""
+    from workloads import ELLIPSOID
+    g = Geometry(20, ny, 16, 1.0, 5.0, 45.0, 48, 40)
+    s = Shape(ELLIPSOID, a=6.0, b=0.4 * ny, c=5.5, delta=0.03, beta=0.004, latitude=10, longitude=80, rotation=30)
+    width = 0.6
+    t = perturbed(s, np.random.default_rng(9), rel=0.05)
+    target = oracle.forward(t, g, soft=True, width=width)[0]
+    _, A = oracle.forward(s, g, soft=True, width=width)
+    _, got, I_gpu = _gpu_grad(g, s, target, "tc_bf16_split", width)
+    ref = oracle.gradient(s, g, 2 * (I_gpu - target), A, width=width)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < GTOL["tc_bf16_split"], (ny, err)
