@@ -691,7 +691,10 @@ def main():
         fp32["rel_l2_I_vs_fp64_oracle"] = err_fp32
     serving = None
     if args.short_serving > 0 and extras:
-        serving = serving_run(args.short_serving, args.serving_slots, args.precision, fractions=(0.8,))
+        try:
+            serving = serving_run(args.short_serving, args.serving_slots, args.precision, fractions=(0.8,))
+        except Exception as e:          # the main line is still printed
+            serving = {"error": f"{type(e).__name__}: {e}"}
 
     pat_sorted = sorted(pat_ms)
     p50 = pat_sorted[len(pat_sorted) // 2]

@@ -95,9 +95,11 @@ def footprint_bytes(geometry, precision) -> int:
 
 
 def run_stream(server: Server, requests: List, targets: List[np.ndarray], time_scale: float = 1.0,
-               want_I: bool = False):
+               want_I: bool = False, wait_timeout_s: float = 120.0):
     """Submits request i at requests[i].arrival_s * time_scale (seconds after
-    start) and waits for all.  Returns (results, latencies_s, wall_s)."""
+    start) and waits for all; a request that has not finished `wait_timeout_s`
+    after its turn to be collected raises ScatmanError (SCATMAN_ERR_TIMEOUT)
+    instead of blocking forever.  Returns (results, latencies_s, status, wall_s)."""
     n = len(requests)
     tickets: List[Optional[int]] = [None] * n
     results: List[Optional[dict]] = [None] * n
@@ -123,7 +125,7 @@ def run_stream(server: Server, requests: List, targets: List[np.ndarray], time_s
             time.sleep(1e-4)
         if tickets[i] is None:
             break
-        status[i], lat[i] = server.wait(tickets[i])
+        status[i], lat[i] = server.wait(tickets[i], timeout_s=wait_timeout_s)
     th.join()
     wall = time.perf_counter() - t0
     if errors:
