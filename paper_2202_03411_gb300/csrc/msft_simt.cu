@@ -53,6 +53,20 @@ __global__ void __launch_bounds__(kSimtThreads) msft_simt_kernel(const typename 
     C wx[kPPT];
 #pragma unroll
     for (int pp = 0; pp < kPPT; ++pp) wx[pp] = expmi<R>(qx[pp], voxel);
+    // FP32: q as float pairs and FP32 coordinates, so the phase anchors do no
+    // FP64 work (FP64 runs at a small fraction of the FP32 rate here)
+    float qxh[kPPT], qxl[kPPT], qyh[kPPT], qyl[kPPT], qzh[kPPT], qzl[kPPT];
+#pragma unroll
+    for (int pp = 0; pp < kPPT; ++pp) {
+        qxh[pp] = (float)qx[pp];
+        qxl[pp] = (float)(qx[pp] - (double)qxh[pp]);
+        qyh[pp] = (float)qy[pp];
+        qyl[pp] = (float)(qy[pp] - (double)qyh[pp]);
+        qzh[pp] = (float)qz[pp];
+        qzl[pp] = (float)(qz[pp] - (double)qzh[pp]);
+    }
+    const float vf = (float)voxel;
+    const float xoff = 0.5f * (float)(nx - 1), yoff = 0.5f * (float)(ny - 1), zoff = 0.5f * (float)(nz - 1);
 
     C acc[kPPT];
 #pragma unroll
@@ -66,7 +80,11 @@ __global__ void __launch_bounds__(kSimtThreads) msft_simt_kernel(const typename 
             const double yc = (y0 + k - 0.5 * (ny - 1)) * voxel;
 #pragma unroll
             for (int pp = 0; pp < kPPT; ++pp) {
-                C e = expmi<R>(qy[pp], yc);
+                C e;
+                if constexpr (sizeof(R) == 4)
+                    e = expmi_fs(qyh[pp], qyl[pp], ((float)(y0 + k) - yoff) * vf);
+                else
+                    e = expmi<R>(qy[pp], yc);
                 py[pp][k].x = in ? e.x : (R)0;
                 py[pp][k].y = in ? e.y : (R)0;
             }
@@ -101,15 +119,24 @@ __global__ void __launch_bounds__(kSimtThreads) msft_simt_kernel(const typename 
                         acc[pp].x += accz[pp].x;
                         acc[pp].y += accz[pp].y;
                         accz[pp].x = accz[pp].y = (R)0;
-                        Z[pp] = expmi<R>(qz[pp], (z - 0.5 * (nz - 1)) * voxel);
+                        if constexpr (sizeof(R) == 4)
+                            Z[pp] = expmi_fs(qzh[pp], qzl[pp], ((float)z - zoff) * vf);
+                        else
+                            Z[pp] = expmi<R>(qz[pp], (z - 0.5 * (nz - 1)) * voxel);
                     }
                     zcur = z;
                 }
                 const bool anchor = (x % 16 == 0) || (cl == 0) || (col == col_begin);
 #pragma unroll
                 for (int pp = 0; pp < kPPT; ++pp) {
-                    if (anchor) ph[pp] = cmul(Z[pp], expmi<R>(qx[pp], (x - 0.5 * (nx - 1)) * voxel));
-                    else ph[pp] = cmul(ph[pp], wx[pp]);
+                    if (anchor) {
+                        if constexpr (sizeof(R) == 4)
+                            ph[pp] = cmul(Z[pp], expmi_fs(qxh[pp], qxl[pp], ((float)x - xoff) * vf));
+                        else
+                            ph[pp] = cmul(Z[pp], expmi<R>(qx[pp], (x - 0.5 * (nx - 1)) * voxel));
+                    } else {
+                        ph[pp] = cmul(ph[pp], wx[pp]);
+                    }
                 }
                 C g[kPPT];
 #pragma unroll
