@@ -218,7 +218,8 @@ cudaError_t launch_msft_uniform(bool fp64, const void *s, int nx, int ny, int nz
                                 const float2 *qz, void *H, void *A, void *I, cudaStream_t st);
 // Uniform-q detector on the tensor cores (msft_tc.cu in store mode for U1,
 // msft_uniform_tc.cu for the x/z contraction).
-// Operand geometry: Kx = nx padded to 64, Jp = nz padded to 16, Rg rows per group.
+// Operand geometry: Kx = nx padded to its K block (16, 32 or 64), Jp = nz padded
+// to 16, Rg rows per group.
 void uq_tc_geometry(int nx, int nz, int *Kx, int *Jp, int *Rg);
 size_t uq_tc_h_bytes(int nx, int nz, int det_ny);
 int uq_tc_slots(int nx, int nz, bool split);
@@ -257,10 +258,11 @@ cudaError_t launch_uq_y_tc_mma(const TcMaps &maps, const double *qrow, int det_n
 // Real flops one contraction launch issues for the given per-slice boxes.
 double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
 bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why);
-// A 3D tiled tensor map over 16-bit elements with the 128-byte swizzle
-// (dims innermost first; strides of dims 1 and 2 in bytes).
+// A 3D tiled tensor map over 16-bit elements with a 32-, 64- or 128-byte
+// swizzle (dims innermost first; strides of dims 1 and 2 in bytes; the box's
+// inner extent in bytes equals the swizzle width).
 bool encode_tmap_3d_16bit(CUtensorMap *map, void *base, const uint64_t dims[3], const uint64_t strides[2],
-                          const uint32_t box[3], bool bf16, std::string *why);
+                          const uint32_t box[3], bool bf16, std::string *why, int swizzle_bytes);
 // Ideal detector (detector.cu): expected photons and Poisson counts per pixel.
 cudaError_t launch_photon_counts(const void *I, bool fp64, long long n, int det_nx, int det_ny, bool uniform,
                                  double theta_max_deg, double wavelength, double voxel, double photon_density,

@@ -668,7 +668,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapFloatOOBfill);
 
 bool encode_tmap_3d_16bit(CUtensorMap *map, void *base, const uint64_t dims[3], const uint64_t strides[2],
-                          const uint32_t box[3], bool bf16, std::string *why) {
+                          const uint32_t box[3], bool bf16, std::string *why, int swizzle_bytes) {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
         void *ptr = nullptr;
@@ -686,8 +686,11 @@ bool encode_tmap_3d_16bit(CUtensorMap *map, void *base, const uint64_t dims[3], 
     cuuint64_t st[2] = {strides[0], strides[1]};
     cuuint32_t bx[3] = {box[0], box[1], box[2]};
     cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapSwizzle sw = swizzle_bytes == 32   ? CU_TENSOR_MAP_SWIZZLE_32B
+                                  : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                        : CU_TENSOR_MAP_SWIZZLE_128B;
     CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, base, d, st, bx,
-                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         *why = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
@@ -709,7 +712,7 @@ bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16,
         const uint64_t dims[3] = {(uint64_t)Kp, (uint64_t)Nxp, (uint64_t)kPlanes * nz};
         const uint64_t strides[2] = {(uint64_t)Kp * 2, (uint64_t)Nxp * Kp * 2};
         const uint32_t box[3] = {(uint32_t)kBK, (uint32_t)(16 * k), (uint32_t)kPlanes};
-        if (!encode_tmap_3d_16bit(&maps->m[k - 1], base, dims, strides, box, bf16, why)) return false;
+        if (!encode_tmap_3d_16bit(&maps->m[k - 1], base, dims, strides, box, bf16, why, 128)) return false;
     }
     return true;
 }

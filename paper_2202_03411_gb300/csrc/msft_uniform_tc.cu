@@ -35,12 +35,14 @@ struct UqParams {
     const float2 *qz;           // per pixel (q_z hi, lo); hi = NaN marker off the Ewald sphere
     int det_nx, det_ny;
     int nx, nz;
-    int Kx, Jp, Jg;             // x padded to 64, z padded to 16, Rg Jp
+    int Kx, Jp, Jg;             // x padded to the K block, z padded to 16, Rg Jp
+    int kbe, rb;                // K block: 16 / 32 / 64 elements in rows of rb = 32 / 64 / 128 bytes
     int n_groups;               // ceil(det_ny / Rg)
-    int nkb;                    // Kx / 64
+    int nkb;                    // Kx / kbe
     int n_ut;                   // pixel tiles of 128 columns u
     int slots;
-    uint32_t stage_bytes;       // one 64-x block of a group: 3 Jg rows of 128 bytes
+    uint32_t box_bytes;         // one K block of a group: 3 Jg rows of rb bytes
+    uint32_t stage_bytes;       // box_bytes rounded up to 1024 (every stage swizzle-aligned)
     int split, bf16;
     uint32_t idesc;             // N = 2 Jg
     uint32_t tmem_cols;
@@ -76,6 +78,29 @@ __device__ __forceinline__ void uq_range(const UqParams &P, long long &lo, long 
     hi = total * (blockIdx.x + 1) / gridDim.x;
 }
 
+// Operand tiles in K blocks of kbe elements: rows of rb bytes with the
+// matching swizzle (128, 64 or 32 bytes: the 16-byte chunk index XOR row
+// bits, as TMA writes them and the MMA descriptors read them), so a small x
+// extent pads to 16 or 32 instead of 64.
+__device__ __forceinline__ uint32_t uq_chunk_offset(const UqParams &P, int m, int k) {
+    const int kb = k / P.kbe, c = (k % P.kbe) >> 3;
+    const int sw = P.rb == 128 ? (m & 7) : P.rb == 64 ? ((m >> 1) & 3) : ((m >> 2) & 1);
+    return (uint32_t)(kb * kTileRows * P.rb + m * P.rb + ((c ^ sw) << 4));
+}
+__device__ __forceinline__ uint32_t uq_k_offset(const UqParams &P, int k) {
+    return (uint32_t)((k / P.kbe) * kTileRows * P.rb + (k % P.kbe) * 2);
+}
+// K-major shared-memory descriptor: 8-row groups rb x 8 bytes apart, layout
+// 2 / 4 / 6 = 128 / 64 / 32-byte swizzle.
+__device__ __forceinline__ uint64_t uq_desc(uint32_t saddr, int rb) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)((8 * rb) >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(rb == 128 ? 2 : rb == 64 ? 4 : 6) << 61;
+    return d;
+}
+
 // Phase operand E[m, k] = [cos(q_x x_k) | -sin(q_x x_k)] of pixel column
 // u = u0 + m (zero beyond nx and beyond the detector), hi and lo parts: one
 // reduced sincos per 8 x and FP32 rotations by 1..4 voxels.
@@ -103,8 +128,8 @@ __device__ __forceinline__ void build_uq_phase(const UqParams &P, int u0, uint8_
             split_pair(in0 ? phs[e].x : 0.f, in1 ? phs[e + 1].x : 0.f, P.bf16, &re_hi[e >> 1], &re_lo[e >> 1]);
             split_pair(in0 ? phs[e].y : 0.f, in1 ? phs[e + 1].y : 0.f, P.bf16, &im_hi[e >> 1], &im_lo[e >> 1]);
         }
-        const uint32_t o_re = a_chunk_offset(m, 8 * x8);
-        const uint32_t o_im = a_chunk_offset(m, P.Kx + 8 * x8);
+        const uint32_t o_re = uq_chunk_offset(P, m, 8 * x8);
+        const uint32_t o_im = uq_chunk_offset(P, m, P.Kx + 8 * x8);
         *reinterpret_cast<uint4 *>(sA_hi + o_re) = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
         *reinterpret_cast<uint4 *>(sA_hi + o_im) = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
         if (P.split) {
@@ -118,7 +143,7 @@ template <int kR>
 __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_constant__ CUtensorMap map, const UqParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const uint32_t a_bytes = (uint32_t)(2 * P.nkb) * kTileKBlockBytes;         // [Er | Ei] over K = 2 Kx
+    const uint32_t a_bytes = (uint32_t)(2 * P.nkb * kTileRows * P.rb);        // [Er | Ei] over K = 2 Kx
     uint8_t *sA_hi = base;
     uint8_t *sA_lo = base + a_bytes;
     uint8_t *stages = base + (P.split ? 2 : 1) * a_bytes;
@@ -173,8 +198,8 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
                     }
                     if (elect_one()) {
                         const uint32_t fb = smem_u32(&full[s]);
-                        mbar_arrive_expect_tx(fb, P.stage_bytes);
-                        tma_load_3d(smem_u32(stages + (size_t)s * P.stage_bytes), &map, fb, kb * kTileKBlock, 0, 3 * g);
+                        mbar_arrive_expect_tx(fb, P.box_bytes);
+                        tma_load_3d(smem_u32(stages + (size_t)s * P.stage_bytes), &map, fb, kb * P.kbe, 0, 3 * g);
                     }
                     __syncwarp();
                     ++prod_it;
@@ -183,8 +208,8 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
         }
     } else if (warp == kUqMmaWarp) {
         // ---------------- MMA issuer (warp-wide loop, one elected lane issues) ----------------
-        const uint64_t ahi0 = sw128_desc(smem_u32(sA_hi)), alo0 = sw128_desc(smem_u32(sA_lo));
-        const uint64_t st0 = sw128_desc(smem_u32(stages));
+        const uint64_t ahi0 = uq_desc(smem_u32(sA_hi), P.rb), alo0 = uq_desc(smem_u32(sA_lo), P.rb);
+        const uint64_t st0 = uq_desc(smem_u32(stages), P.rb);
         uint32_t it = 0, acc_it = 0, tl = 0;
         bool ok = true;
         long long idx, hi;
@@ -210,11 +235,13 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
                     }
                     tc_fence_after();
                     const uint64_t w2 = st0 + (uint64_t)(((size_t)s * P.stage_bytes) >> 4);    // rows [0, 2 Jg): [-Hi | Hr]
-                    const uint64_t w1 = w2 + (uint64_t)(((uint32_t)P.Jg * 128u) >> 4);         // rows [Jg, 3 Jg): [Hr | Hi]
+                    const uint64_t w1 = w2 + (uint64_t)(((uint32_t)P.Jg * (uint32_t)P.rb) >> 4); // rows [Jg, 3 Jg): [Hr | Hi]
+                    const int ksteps = P.kbe >> 4;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        const int x0 = kTileKBlock * kb + 16 * kk;
-                        const uint64_t off_r = a_k_offset(x0) >> 4, off_i = a_k_offset(P.Kx + x0) >> 4;
+                        if (kk >= ksteps) break;
+                        const int x0 = P.kbe * kb + 16 * kk;
+                        const uint64_t off_r = uq_k_offset(P, x0) >> 4, off_i = uq_k_offset(P, P.Kx + x0) >> 4;
                         const uint64_t b1 = w1 + (uint64_t)(kk * 2), b2 = w2 + (uint64_t)(kk * 2);
                         const uint32_t acc0 = first ? 0u : 1u;
                         if (elect_one()) {
@@ -340,11 +367,17 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
 }
 
 // ---- host side ----------------------------------------------------------------------
-static size_t uq_a_bytes(int Kx, bool split) { return (size_t)(split ? 2 : 1) * 2 * (Kx / 64) * kTileKBlockBytes; }
+// [Er | Ei] (and its low part): 128 rows x 2 Kx elements of 2 bytes.
+static size_t uq_a_bytes(int Kx, bool split) { return (size_t)(split ? 2 : 1) * kTileRows * 2 * Kx * 2; }
 static size_t uq_fixed_bytes() { return 1024 + 256; }
 
+// K block of the x contraction: 16, 32 or 64 x (32-, 64- or 128-byte rows).
+static int uq_kblock(int nx) { return nx <= 16 ? 16 : nx <= 32 ? 32 : 64; }
+static size_t uq_stage_bytes(int Jg, int kbe) { return ((size_t)3 * Jg * kbe * 2 + 1023) / 1024 * 1024; }
+
 void uq_tc_geometry(int nx, int nz, int *Kx, int *Jp, int *Rg) {
-    *Kx = (nx + 63) / 64 * 64;
+    const int kbe = uq_kblock(nx);
+    *Kx = (nx + kbe - 1) / kbe * kbe;
     *Jp = (nz + 15) / 16 * 16;
     int r = 1;
     while (r < 8 && 2 * r * *Jp <= 128) r <<= 1;
@@ -356,7 +389,7 @@ int uq_tc_slots(int nx, int nz, bool split) {
     int Kx, Jp, Rg;
     uq_tc_geometry(nx, nz, &Kx, &Jp, &Rg);
     if (Kx > 128 || Jp > 128) return 0;
-    const size_t stage = (size_t)3 * Rg * Jp * 128;
+    const size_t stage = uq_stage_bytes(Rg * Jp, uq_kblock(nx));
     const size_t used = uq_a_bytes(Kx, split) + uq_fixed_bytes();
     if (used + 2 * stage > (size_t)kUqMaxSmem) return 0;
     const size_t n = ((size_t)kUqMaxSmem - used) / stage;
@@ -369,8 +402,9 @@ bool encode_tmap_uq(CUtensorMap *map, void *H, int nx, int nz, int det_ny, bool 
     const int Jg = Rg * Jp, n_groups = (det_ny + Rg - 1) / Rg;
     const uint64_t dims[3] = {(uint64_t)Kx, (uint64_t)Jg, (uint64_t)3 * n_groups};
     const uint64_t strides[2] = {(uint64_t)Kx * 2, (uint64_t)Jg * Kx * 2};
-    const uint32_t box[3] = {(uint32_t)kTileKBlock, (uint32_t)Jg, 3u};
-    return encode_tmap_3d_16bit(map, H, dims, strides, box, bf16, why);
+    const int kbe = uq_kblock(nx);
+    const uint32_t box[3] = {(uint32_t)kbe, (uint32_t)Jg, 3u};
+    return encode_tmap_3d_16bit(map, H, dims, strides, box, bf16, why, kbe * 2);
 }
 
 // Bytes of the y-contracted 16-bit operand: every row group, three planes.
@@ -403,10 +437,13 @@ cudaError_t launch_uq_tc(const CUtensorMap &map, const float2 *qz, int nx, int n
     P.nz = nz;
     P.Jg = Rg * P.Jp;
     P.n_groups = (det_ny + Rg - 1) / Rg;
-    P.nkb = P.Kx / 64;
+    P.kbe = uq_kblock(nx);
+    P.rb = 2 * P.kbe;
+    P.nkb = P.Kx / P.kbe;
     P.slots = uq_tc_slots(nx, nz, split);
     if (P.slots < 2) return cudaErrorInvalidValue;
-    P.stage_bytes = (uint32_t)(3 * P.Jg * 128);
+    P.box_bytes = (uint32_t)(3 * P.Jg * P.rb);
+    P.stage_bytes = (uint32_t)uq_stage_bytes(P.Jg, P.kbe);
     P.n_ut = (det_nx + kTileRows - 1) / kTileRows;
     const long long total = (long long)P.n_ut * P.n_groups;
     P.split = split ? 1 : 0;
