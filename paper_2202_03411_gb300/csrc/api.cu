@@ -277,9 +277,8 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
         return fail(rc);
     if (h->uniform_tc) {
         const size_t hb = uq_tc_h_bytes(c.nx, c.nz, c.det_ny);
+        // (zeroed by each forward before the y-sum writes its occupied part)
         if ((rc = alloc_dev(h, &h->d_H, hb, "y-contracted slices"))) return fail(rc);
-        // padding rows (z >= nz) and columns (x >= nx) stay zero for good
-        if ((rc = check_cuda(h, cudaMemsetAsync(h->d_H, 0, hb, h->stream), "memset"))) return fail(rc);
     } else if (h->uniform_q) {
         if ((rc = alloc_dev(h, &h->d_H, (size_t)c.det_ny * nvox / c.ny * cx, "y-contracted slices"))) return fail(rc);
     } else if (h->tensor_core) {
