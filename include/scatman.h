@@ -95,8 +95,11 @@ enum {
  *                  k0 * voxel * nz * max(delta, beta) > 5)
  *  detector        SCATMAN_DETECTOR_FLAT (0) or SCATMAN_DETECTOR_UNIFORM_Q; the
  *                  uniform-q detector runs the separable transverse sum (q_x
- *                  depends on the pixel column only, q_y on the row only) in
- *                  SCATMAN_FP32 or SCATMAN_FP64, nz <= 128
+ *                  depends on the pixel column only, q_y on the row only),
+ *                  nz <= 128: on the CUDA cores in SCATMAN_FP32 / SCATMAN_FP64,
+ *                  on the tensor cores in the four TC modes (y-sum with FP16
+ *                  operands, x/z sum in the mode's type; nx <= 128 and, with
+ *                  split phases, ny <= 128 as for the flat detector)
  */
 typedef struct {
     int nx, ny, nz;
