@@ -36,7 +36,7 @@ struct UqParams {
     int det_nx, det_ny;
     int nx, nz;
     int Kx, Jp, Jg;             // x padded to the K block, z padded to 16, Rg Jp
-    int kbe, rb;                // K block: 16 / 32 / 64 elements in rows of rb = 32 / 64 / 128 bytes
+    int kbe, rb, kbs;           // K block: 16 / 32 / 64 elements (2^kbs) in rows of rb = 32 / 64 / 128 bytes
     int n_groups;               // ceil(det_ny / Rg)
     int nkb;                    // Kx / kbe
     int n_ut;                   // pixel tiles of 128 columns u
@@ -83,12 +83,9 @@ __device__ __forceinline__ void uq_range(const UqParams &P, long long &lo, long 
 // bits, as TMA writes them and the MMA descriptors read them), so a small x
 // extent pads to 16 or 32 instead of 64.
 __device__ __forceinline__ uint32_t uq_chunk_offset(const UqParams &P, int m, int k) {
-    const int kb = k / P.kbe, c = (k % P.kbe) >> 3;
+    const int kb = k >> P.kbs, c = (k & (P.kbe - 1)) >> 3;
     const int sw = P.rb == 128 ? (m & 7) : P.rb == 64 ? ((m >> 1) & 3) : ((m >> 2) & 1);
     return (uint32_t)(kb * kTileRows * P.rb + m * P.rb + ((c ^ sw) << 4));
-}
-__device__ __forceinline__ uint32_t uq_k_offset(const UqParams &P, int k) {
-    return (uint32_t)((k / P.kbe) * kTileRows * P.rb + (k % P.kbe) * 2);
 }
 // K-major shared-memory descriptor: 8-row groups rb x 8 bytes apart, layout
 // 2 / 4 / 6 = 128 / 64 / 32-byte swizzle.
@@ -237,11 +234,13 @@ __global__ void __launch_bounds__(kUqThreads, 1) uq_tc_kernel(const __grid_const
                     const uint64_t w2 = st0 + (uint64_t)(((size_t)s * P.stage_bytes) >> 4);    // rows [0, 2 Jg): [-Hi | Hr]
                     const uint64_t w1 = w2 + (uint64_t)(((uint32_t)P.Jg * (uint32_t)P.rb) >> 4); // rows [Jg, 3 Jg): [Hr | Hi]
                     const int ksteps = P.kbe >> 4;
+                    // K block kb of [Er] and block nkb + kb of [Ei]; 32 bytes per K step
+                    const uint64_t blk_r = (uint64_t)(((uint32_t)kb * kTileRows * (uint32_t)P.rb) >> 4);
+                    const uint64_t blk_i = (uint64_t)(((uint32_t)(P.nkb + kb) * kTileRows * (uint32_t)P.rb) >> 4);
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         if (kk >= ksteps) break;
-                        const int x0 = P.kbe * kb + 16 * kk;
-                        const uint64_t off_r = uq_k_offset(P, x0) >> 4, off_i = uq_k_offset(P, P.Kx + x0) >> 4;
+                        const uint64_t off_r = blk_r + (uint64_t)(2 * kk), off_i = blk_i + (uint64_t)(2 * kk);
                         const uint64_t b1 = w1 + (uint64_t)(kk * 2), b2 = w2 + (uint64_t)(kk * 2);
                         const uint32_t acc0 = first ? 0u : 1u;
                         if (elect_one()) {
@@ -439,6 +438,7 @@ cudaError_t launch_uq_tc(const CUtensorMap &map, const float2 *qz, int nx, int n
     P.n_groups = (det_ny + Rg - 1) / Rg;
     P.kbe = uq_kblock(nx);
     P.rb = 2 * P.kbe;
+    P.kbs = P.kbe == 16 ? 4 : P.kbe == 32 ? 5 : 6;
     P.nkb = P.Kx / P.kbe;
     P.slots = uq_tc_slots(nx, nz, split);
     if (P.slots < 2) return cudaErrorInvalidValue;
