@@ -89,3 +89,24 @@ def test_footprint_is_a_host_calculation(lib):
     assert footprint_bytes(big, "tc_bf16_split") > 512 * 512 * 2 * 128 * 4
     # the largest serving request fits many times into a 120 GB budget
     assert footprint_bytes(big, "tc_bf16_split") < (120 << 30) // 100
+
+
+def test_footprint_counts_the_uniform_q_buffers(lib):
+    """The uniform-q detector's y-contracted operand and q_z table are part of
+    the estimate: the tensor-core planes grow with the detector rows and with
+    the padded z extent, the FP32 slices with rows x nx x nz."""
+    from paper_2202_03411_gb300.serving import footprint_bytes
+    from workloads import DETECTOR_UNIFORM_Q
+    g = Geometry(56, 56, 56, 1.0, 1.0, 30.0, 2048, 2048, DETECTOR_UNIFORM_Q)
+    flat = Geometry(56, 56, 56, 1.0, 1.0, 30.0, 2048, 2048)
+    # tensor cores: 2048 rows x 3 planes x 64 padded z x 64 padded x x 2 bytes = 48 MiB of planes,
+    # plus an 8-byte q_z per pixel (32 MiB), on top of the flat detector's buffers
+    extra = footprint_bytes(g, "tc_bf16_split") - footprint_bytes(flat, "tc_bf16_split")
+    assert extra >= (48 << 20) + (32 << 20) - (4 << 20)
+    # FP32: q (96 MiB), 2048 rows x 56 x 56 complex slices (49 MiB) and the q_z table
+    # (32 MiB); no split partial fields (the flat detector's 2 GiB)
+    n = 2048 * 2048
+    assert footprint_bytes(g, "fp32") >= 24 * n + 2048 * 56 * 56 * 8 + 8 * n
+    assert footprint_bytes(g, "fp32") < footprint_bytes(flat, "fp32")
+    g_small = Geometry(56, 56, 56, 1.0, 1.0, 30.0, 256, 256, DETECTOR_UNIFORM_Q)
+    assert 0 < footprint_bytes(g_small, "fp32") < footprint_bytes(g, "fp32")
