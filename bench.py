@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=0,
                     help="run the serving mix with this many requests and print its own JSON line")
-    ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--serving-slots", type=int, default=4)
     ap.add_argument("--fit-step", type=int, default=0,
                     help="time this many forward+gradient fit steps of the 96^3 l<=6 workload and print a JSON line")
     ap.add_argument("--short-serving", type=int, default=240,
