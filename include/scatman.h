@@ -49,7 +49,8 @@ typedef enum {
     SCATMAN_ERR_TIMEOUT = -4,     /* a kernel gave up a bounded wait; results invalid */
     SCATMAN_ERR_ADMISSION = -5,   /* serving: request exceeds the memory budget */
     SCATMAN_ERR_STATE = -6,       /* call out of order (e.g. forward before voxelise) */
-    SCATMAN_ERR_UNSUPPORTED = -7  /* no device of compute capability 10.3 */
+    SCATMAN_ERR_UNSUPPORTED = -7, /* no device of compute capability 10.3 */
+    SCATMAN_ERR_CANCELLED = -8    /* serving: the request was cancelled before it was admitted */
 } scatman_status;
 
 /* Arithmetic of the Fourier contraction (Eq. 9's per-slice sum). */
@@ -258,6 +259,27 @@ SCATMAN_API int scatman_photon_counts(scatman_handle *h, double photon_density, 
  */
 SCATMAN_API int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams);
 
+/*
+ * Failure-path hooks (no counterpart in the paper; they let tests reach the
+ * error paths without faulting a GPU).
+ *
+ * scatman_set_wait_limit: every wait of the handle's tensor-core kernels on
+ * another warp's work gives up after `seconds` (default and maximum 2 s;
+ * seconds <= 0 restores the default) instead of 2 s.  A kernel that gives up
+ * sets its error bit, waits (with the full limit) for its own TMA copies and
+ * MMAs in flight, frees its tensor memory and returns; scatman_sync then
+ * reports ERR_TIMEOUT and the results of that call are invalid.  The handle
+ * stays usable.  Synchronises the stream.  Errors: ERR_ARG (NaN), ERR_CUDA.
+ *
+ * scatman_debug_fail_allocation: process-wide; with after >= 0 the device
+ * allocation that follows `after` more successful ones (in any handle or
+ * server of the process) fails once as if the device were out of memory
+ * (the call that made it returns ERR_OOM and releases what it had
+ * allocated); after < 0 disarms it.
+ */
+SCATMAN_API int scatman_set_wait_limit(scatman_handle *h, double seconds);
+SCATMAN_API void scatman_debug_fail_allocation(long long after);
+
 /* Number of gradient entries for the current shape (0 before voxelise). */
 SCATMAN_API int scatman_param_count(const scatman_handle *h);
 
@@ -338,6 +360,7 @@ typedef struct {
     long long submitted, completed, failed;
     long long bytes_reserved, bytes_reserved_peak;
     int inflight, inflight_peak;
+    long long cancelled;
 } scatman_server_stats;
 
 /* Creates the server on the current device.  Errors: ERR_ARG, ERR_CUDA,
@@ -355,6 +378,12 @@ SCATMAN_API int scatman_server_submit(scatman_server *srv, const scatman_request
  * request's own status and *latency_s to submit-to-completion time. */
 SCATMAN_API int scatman_server_wait(scatman_server *srv, long long ticket, double timeout_s, int *status,
                                     double *latency_s);
+
+/* Cancels a request that is still queued: it will not run, and
+ * scatman_server_wait reports it with status ERR_CANCELLED.  Returns OK, or
+ * ERR_STATE once the request has been admitted (it then runs to completion),
+ * ERR_ARG for an unknown ticket. */
+SCATMAN_API int scatman_server_cancel(scatman_server *srv, long long ticket);
 
 SCATMAN_API int scatman_server_stats_get(scatman_server *srv, scatman_server_stats *out);
 

@@ -15,10 +15,11 @@ SCATMAN_ERR_TIMEOUT = -4
 SCATMAN_ERR_ADMISSION = -5
 SCATMAN_ERR_STATE = -6
 SCATMAN_ERR_UNSUPPORTED = -7
+SCATMAN_ERR_CANCELLED = -8
 
 STATUS_NAMES = {
     0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT", -5: "ERR_ADMISSION",
-    -6: "ERR_STATE", -7: "ERR_UNSUPPORTED",
+    -6: "ERR_STATE", -7: "ERR_UNSUPPORTED", -8: "ERR_CANCELLED",
 }
 
 SCATMAN_FP64 = 0
@@ -34,6 +35,9 @@ PRECISIONS = {
 }
 
 SCATMAN_MAX_LMAX = 12
+
+SCATMAN_SPHERE, SCATMAN_ELLIPSOID, SCATMAN_SPHHARM, SCATMAN_RADIALMAP, SCATMAN_VOLUMEMAP = 0, 1, 2, 3, 4
+SCATMAN_DETECTOR_FLAT, SCATMAN_DETECTOR_UNIFORM_Q = 0, 1
 
 _D = ctypes.POINTER(ctypes.c_double)
 
@@ -77,7 +81,7 @@ class scatman_request(ctypes.Structure):
 class scatman_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
                 ("bytes_reserved", ctypes.c_longlong), ("bytes_reserved_peak", ctypes.c_longlong),
-                ("inflight", ctypes.c_int), ("inflight_peak", ctypes.c_int)]
+                ("inflight", ctypes.c_int), ("inflight_peak", ctypes.c_int), ("cancelled", ctypes.c_longlong)]
 
 
 # name -> (restype, argtypes); every symbol include/scatman.h declares
@@ -110,6 +114,9 @@ SIGNATURES = {
     "scatman_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "scatman_server_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(scatman_server_stats)]),
+    "scatman_server_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
+    "scatman_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "scatman_debug_fail_allocation": (None, [ctypes.c_longlong]),
     "scatman_server_destroy": (None, [ctypes.c_void_p]),
     "scatman_footprint_bytes": (ctypes.c_longlong, [ctypes.POINTER(scatman_config)]),
     "scatman_forward_noalloc": (ctypes.c_int, [ctypes.POINTER(scatman_config), ctypes.POINTER(scatman_shape),

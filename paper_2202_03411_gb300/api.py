@@ -14,6 +14,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import scatman_config, scatman_shape
+from .types import alm_array
 
 
 class ScatmanError(RuntimeError):
@@ -28,6 +29,37 @@ def _check(code: int, handle: Optional["Handle"] = None, what: str = ""):
         if handle is not None and handle.ptr:
             msg = _lib.load().scatman_last_error(handle.ptr).decode()
         raise ScatmanError(code, f"{what}: {msg}" if what else msg)
+
+
+def _device_ptr(t, dtypes, n: int, what: str) -> ctypes.c_void_p:
+    """Data pointer of a CUDA tensor after checking that the library may write
+    (or read) n elements of one of `dtypes` there: a wrong type, a host
+    tensor, a strided view or a short buffer raises ValueError instead of
+    reaching a kernel."""
+    if t is None:
+        return ctypes.c_void_p(None)
+    names = tuple(str(d).replace("torch.", "") for d in dtypes)
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if str(t.dtype).replace("torch.", "") not in names:
+        raise ValueError(f"{what} must have dtype {' or '.join(names)}, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.numel() < n:
+        raise ValueError(f"{what} holds {t.numel()} elements; {n} are needed")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype_name: str, n: int, what: str) -> int:
+    """Address of a host array (numpy or CPU tensor) that receives n elements."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype_name) or not a.flags["C_CONTIGUOUS"] or a.size < n:
+            raise ValueError(f"{what} must be a contiguous {dtype_name} array of at least {n} elements")
+        return a.ctypes.data
+    if getattr(a, "is_cuda", True) or str(a.dtype).replace("torch.", "") != dtype_name or \
+            not a.is_contiguous() or a.numel() < n:
+        raise ValueError(f"{what} must be a contiguous CPU {dtype_name} tensor of at least {n} elements")
+    return a.data_ptr()
 
 
 class Handle:
@@ -85,7 +117,7 @@ def make_shape(shape):
     st.kind = shape.kind
     st.r, st.a, st.b, st.c, st.R0 = shape.r, shape.a, shape.b, shape.c, shape.R0
     st.lmax = shape.lmax
-    alm = shape.alm_array()
+    alm = alm_array(shape)
     st.alm = alm.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     st.delta, st.beta = shape.delta, shape.beta
     st.latitude, st.longitude, st.rotation = shape.latitude, shape.longitude, shape.rotation
@@ -140,14 +172,16 @@ def scatman_voxelise(h: Handle, shape) -> None:
 
 def scatman_forward(h: Handle, I, A=None) -> None:
     """I, A: CUDA tensors (float64/complex128 in FP64 mode, float32/complex64 otherwise)."""
-    _check(_lib.load().scatman_forward(h.ptr, ctypes.c_void_p(I.data_ptr()),
-                                       ctypes.c_void_p(A.data_ptr() if A is not None else None)), h, "forward")
+    n = scatman_n_pix(h)
+    pi = _device_ptr(I, ["float64"] if h.fp64 else ["float32"], n, "I")
+    pa = _device_ptr(A, ["complex128"] if h.fp64 else ["complex64"], n, "A")
+    _check(_lib.load().scatman_forward(h.ptr, pi, pa), h, "forward")
 
 
 def scatman_acquire(h: Handle, shape, I_host) -> None:
     """I_host: numpy array or pinned CPU tensor of n_pix elements."""
     st, alm = make_shape(shape)
-    ptr = I_host.ctypes.data if isinstance(I_host, np.ndarray) else I_host.data_ptr()
+    ptr = _host_ptr(I_host, "float64" if h.fp64 else "float32", scatman_n_pix(h), "I_host")
     _check(_lib.load().scatman_acquire(h.ptr, ctypes.byref(st), ctypes.c_void_p(ptr)), h, "acquire")
 
 
@@ -162,7 +196,8 @@ def scatman_acquire_batch(h: Handle, shapes, I_host) -> None:
         arr[i] = st
         keep.append(k)
     rows = [I_host[i] for i in range(n)]
-    ptrs = (ctypes.c_void_p * max(n, 1))(*[r.ctypes.data if isinstance(r, np.ndarray) else r.data_ptr() for r in rows])
+    dt, npx = ("float64" if h.fp64 else "float32"), scatman_n_pix(h)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[_host_ptr(r, dt, npx, f"I_host[{i}]") for i, r in enumerate(rows)])
     _check(_lib.load().scatman_acquire_batch(h.ptr, arr, n, ptrs), h, "acquire_batch")
 
 
@@ -170,8 +205,8 @@ def scatman_backward(h: Handle, dLdI) -> np.ndarray:
     lib = _lib.load()
     n = lib.scatman_param_count(h.ptr)
     out = np.zeros(n, dtype=np.float64)
-    _check(lib.scatman_backward(h.ptr, ctypes.c_void_p(dLdI.data_ptr()),
-                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), h, "backward")
+    pd = _device_ptr(dLdI, ["float64"] if h.fp64 else ["float32"], scatman_n_pix(h), "dLdI")
+    _check(lib.scatman_backward(h.ptr, pd, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), h, "backward")
     return out
 
 
@@ -181,10 +216,11 @@ def scatman_photon_counts(h: Handle, photon_density: float, seed: int, I, want_l
     (float64 and int64); either may be skipped (None)."""
     import torch
     n = scatman_n_pix(h)
+    pi = _device_ptr(I, ["float64"] if h.fp64 else ["float32"], n, "I")
     lam = torch.empty(n, dtype=torch.float64, device=I.device) if want_lambda else None
     cnt = torch.empty(n, dtype=torch.int64, device=I.device) if want_counts else None
     _check(_lib.load().scatman_photon_counts(
-        h.ptr, float(photon_density), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.c_void_p(I.data_ptr()),
+        h.ptr, float(photon_density), int(seed) & 0xFFFFFFFFFFFFFFFF, pi,
         ctypes.c_void_p(lam.data_ptr() if lam is not None else None),
         ctypes.c_void_p(cnt.data_ptr() if cnt is not None else None)), h, "photon counts")
     return lam, cnt
@@ -237,6 +273,18 @@ def scatman_contraction_flops(h: Handle):
     return a.value, b.value
 
 
+def scatman_set_wait_limit(h: Handle, seconds: float) -> None:
+    """Failure-path hook: the handle's tensor-core kernels give up their waits
+    on other warps after `seconds` (<= 0: the default 2 s)."""
+    _check(_lib.load().scatman_set_wait_limit(h.ptr, float(seconds)), h, "set_wait_limit")
+
+
+def scatman_debug_fail_allocation(after: int) -> None:
+    """Failure-path hook: the device allocation after `after` more successful
+    ones fails once (process-wide); a negative value disarms it."""
+    _lib.load().scatman_debug_fail_allocation(int(after))
+
+
 def scatman_destroy(h: Handle) -> None:
     h.close()
 
@@ -253,15 +301,19 @@ def scatman_forward_noalloc(geometry, shape, I, A=None, soft: bool = False, soft
                             scan_fp64: bool = False, q_list: Optional[np.ndarray] = None,
                             stream: Optional[int] = None) -> None:
     """scatman_forward_noalloc: the FP32 forward for callers that cannot
-    allocate device memory; I (and A) are float32 (complex64) CUDA tensors."""
+    allocate device memory (an application whose memory pool already holds
+    nearly all of the GPU, or a loop that must not take the device-wide
+    synchronisation of an allocation).  I (and A) are float32 (complex64) CUDA
+    tensors of at least n_pix elements; the flat detector or a q_list only."""
     lib = _lib.load()
     cfg, keep = make_config(geometry, "fp32", soft, soft_width, scan_fp64, q_list)
     st, alm = make_shape(shape)
+    n = int(q_list.shape[0]) if q_list is not None else geometry.det_nx * geometry.det_ny
+    pi = _device_ptr(I, ["float32"], n, "I")
+    pa = _device_ptr(A, ["complex64"], n, "A")
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
-    code = lib.scatman_forward_noalloc(ctypes.byref(cfg), ctypes.byref(st), ctypes.c_void_p(stream),
-                                       ctypes.c_void_p(I.data_ptr()),
-                                       ctypes.c_void_p(A.data_ptr() if A is not None else None))
+    code = lib.scatman_forward_noalloc(ctypes.byref(cfg), ctypes.byref(st), ctypes.c_void_p(stream), pi, pa)
     if code != 0:
         raise ScatmanError(code, "scatman_forward_noalloc: " + lib.scatman_last_error(None).decode())

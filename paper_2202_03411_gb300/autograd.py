@@ -12,11 +12,13 @@ field of its last forward call, so give each in-flight fit its own handle.
 """
 from __future__ import annotations
 
+import copy
+
 import numpy as np
 import torch
 
 from . import api
-from workloads import ELLIPSOID, SPHERE, Shape
+from .types import ELLIPSOID, SPHERE, Shape, alm_array
 
 
 def params_of(shape: Shape) -> np.ndarray:
@@ -25,13 +27,13 @@ def params_of(shape: Shape) -> np.ndarray:
     elif shape.kind == ELLIPSOID:
         v = [shape.a, shape.b, shape.c]
     else:
-        v = list(shape.alm_array()[1:]) + [shape.R0]
+        v = list(alm_array(shape)[1:]) + [shape.R0]
     return np.array(v + [shape.delta, shape.beta], dtype=np.float64)
 
 
 def shape_with(template: Shape, params) -> Shape:
     p = np.asarray(params, dtype=np.float64)
-    s = template.copy()
+    s = copy.deepcopy(template)
     if s.kind == SPHERE:
         s.r = float(p[0])
     elif s.kind == ELLIPSOID:

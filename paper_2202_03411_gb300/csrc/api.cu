@@ -2,6 +2,7 @@
 // argument checks, buffer ownership and dispatch to the kernels.
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <new>
 
 #include "internal.cuh"
@@ -94,6 +95,29 @@ void finish_shape_params(ShapeParams *sp) {
 
 }  // namespace scm
 
+namespace scm {
+
+// Allocation-failure injection for tests: when armed with n >= 0, the
+// allocation after n more successful ones fails (once), as if the device were
+// out of memory.  Process-wide; -1 disarms it.
+static std::atomic<long long> g_fail_countdown{-1};
+
+cudaError_t device_malloc(void **p, size_t bytes) {
+    long long c = g_fail_countdown.load();
+    while (c >= 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) {
+            if (c == 0) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+}  // namespace scm
+
 using namespace scm;
 
 extern "C" {
@@ -120,7 +144,7 @@ int scatman_param_count(const scatman_handle *h) {
 
 static int alloc_dev(scatman_handle *h, void **p, size_t bytes, const char *what) {
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = scm::device_malloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
         return check_cuda(h, e, what);
@@ -170,6 +194,76 @@ void scatman_destroy(scatman_handle *h) {
     delete h;
 }
 
+// Checks shared by scatman_create and scatman_forward_noalloc: grid, lengths,
+// occupancy width, and the q set (explicit list or detector).  Sets *n_pix.
+static bool check_config(const scatman_config &c, long long *n_pix, std::string *why) {
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.nz > 256 || c.nx > 4096 || c.ny > 4096) {
+        *why = "grid sizes must be >= 1, nx and ny <= 4096 and nz <= 256";
+        return false;
+    }
+    if (!(c.voxel > 0) || !(c.wavelength > 0)) {
+        *why = "voxel and wavelength must be positive";
+        return false;
+    }
+    if (c.soft && !(c.soft_width > 0)) {
+        *why = "soft occupancy needs soft_width > 0";
+        return false;
+    }
+    if (c.q_list) {
+        if (c.n_q < 1) {
+            *why = "n_q must be >= 1 with q_list";
+            return false;
+        }
+        *n_pix = c.n_q;
+    } else {
+        if (c.det_nx < 1 || c.det_ny < 1) {
+            *why = "detector size must be >= 1";
+            return false;
+        }
+        if (!(c.theta_max_deg > 0 && c.theta_max_deg < 90)) {
+            *why = "theta_max_deg must lie in (0, 90)";
+            return false;
+        }
+        *n_pix = (long long)c.det_nx * c.det_ny;
+    }
+    if (c.detector != SCATMAN_DETECTOR_FLAT && c.detector != SCATMAN_DETECTOR_UNIFORM_Q) {
+        *why = "unknown detector";
+        return false;
+    }
+    return true;
+}
+
+// Checks of a sphere, ellipsoid or harmonics shape (map shapes add their own).
+static bool check_param_shape(const scatman_shape *s, std::string *why) {
+    if (s->kind == SCATMAN_SPHERE && !(s->r > 0)) {
+        *why = "sphere radius must be > 0";
+        return false;
+    }
+    if (s->kind == SCATMAN_ELLIPSOID && !(s->a > 0 && s->b > 0 && s->c > 0)) {
+        *why = "ellipsoid semi-axes must be > 0";
+        return false;
+    }
+    if (s->kind == SCATMAN_SPHHARM) {
+        if (!(s->R0 > 0)) {
+            *why = "R0 must be > 0";
+            return false;
+        }
+        if (s->lmax < 0 || s->lmax > SCATMAN_MAX_LMAX) {
+            *why = "lmax out of range";
+            return false;
+        }
+        if (s->lmax > 0 && !s->alm) {
+            *why = "alm is NULL";
+            return false;
+        }
+    }
+    if (!std::isfinite(s->delta) || !std::isfinite(s->beta)) {
+        *why = "delta and beta must be finite";
+        return false;
+    }
+    return true;
+}
+
 int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle **out) {
     if (!out) return SCATMAN_ERR_ARG;
     *out = nullptr;
@@ -186,25 +280,12 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
         return code;
     };
     const scatman_config &c = *cfg;
-    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.nz > 256 || c.nx > 4096 || c.ny > 4096)
-        return fail(set_error(h, SCATMAN_ERR_ARG, "grid sizes must be >= 1 and nz <= 256"));
-    if (!(c.voxel > 0) || !(c.wavelength > 0))
-        return fail(set_error(h, SCATMAN_ERR_ARG, "voxel and wavelength must be positive"));
+    {
+        std::string why;
+        if (!check_config(c, &h->n_pix, &why)) return fail(set_error(h, SCATMAN_ERR_ARG, why));
+    }
     if (c.precision < SCATMAN_FP64 || c.precision > SCATMAN_TC_BF16)
         return fail(set_error(h, SCATMAN_ERR_ARG, "unknown precision"));
-    if (c.soft && !(c.soft_width > 0))
-        return fail(set_error(h, SCATMAN_ERR_ARG, "soft occupancy needs soft_width > 0"));
-    if (cfg->q_list) {
-        if (cfg->n_q < 1) return fail(set_error(h, SCATMAN_ERR_ARG, "n_q must be >= 1 with q_list"));
-        h->n_pix = cfg->n_q;
-    } else {
-        if (c.det_nx < 1 || c.det_ny < 1) return fail(set_error(h, SCATMAN_ERR_ARG, "detector size must be >= 1"));
-        if (!(c.theta_max_deg > 0 && c.theta_max_deg < 90))
-            return fail(set_error(h, SCATMAN_ERR_ARG, "theta_max_deg must lie in (0, 90)"));
-        h->n_pix = (long long)c.det_nx * c.det_ny;
-    }
-    if (c.detector != SCATMAN_DETECTOR_FLAT && c.detector != SCATMAN_DETECTOR_UNIFORM_Q)
-        return fail(set_error(h, SCATMAN_ERR_ARG, "unknown detector"));
     h->uniform_q = c.detector == SCATMAN_DETECTOR_UNIFORM_Q && !cfg->q_list;
     if (h->uniform_q && c.nz > 128)
         return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector supports nz <= 128"));
@@ -257,8 +338,9 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     int rc;
     if ((rc = alloc_dev(h, (void **)&h->d_q, npix * 3 * sizeof(double), "q buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, (void **)&h->d_chi, nvox * sizeof(float), "occupancy buffer"))) return fail(rc);
-    if (h->tensor_core &&
-        (rc = alloc_dev(h, (void **)&h->d_bounds, (6 * (size_t)c.nz + 2) * sizeof(int), "slice bounds")))
+    // per-slice occupied boxes (every mode skips the empty parts of each
+    // slice), then the tensor-core kernel's occupied-slice list
+    if ((rc = alloc_dev(h, (void **)&h->d_bounds, (6 * (size_t)c.nz + 2) * sizeof(int), "slice bounds")))
         return fail(rc);
     if (h->tensor_core) {
         h->s_bytes = h->b_rows * (size_t)h->Kp * 2;
@@ -269,7 +351,7 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     const size_t cx = f64 ? sizeof(double2) : sizeof(float2);
     if ((rc = alloc_dev(h, &h->d_A, npix * cx, "field buffer"))) return fail(rc);
     if ((rc = alloc_dev(h, &h->d_I, npix * (f64 ? 8 : 4), "intensity buffer"))) return fail(rc);
-    if ((rc = alloc_dev(h, (void **)&h->d_err, sizeof(int), "error word"))) return fail(rc);
+    if ((rc = alloc_dev(h, (void **)&h->d_err, kStatusBytes, "status block"))) return fail(rc);
     if (h->uniform_q && (rc = alloc_dev(h, (void **)&h->d_uq_qz, npix * sizeof(float2), "q_z table")))
         return fail(rc);
     if (h->uniform_tc &&
@@ -288,7 +370,7 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
         h->splits = simt_splits(h->n_pix, c.nx, c.nz, h->sm_count);
         if ((rc = alloc_dev(h, &h->d_partial, (size_t)h->splits * npix * cx, "partial fields"))) return fail(rc);
     }
-    if ((rc = check_cuda(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "memset"))) return fail(rc);
+    if ((rc = check_cuda(h, cudaMemsetAsync(h->d_err, 0, kStatusBytes, h->stream), "memset"))) return fail(rc);
     if ((rc = check_cuda(h, cudaMemsetAsync(h->d_s, 0, h->s_bytes, h->stream), "memset"))) return fail(rc);
 
     if (cfg->q_list) {
@@ -485,16 +567,10 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
                 for (long long k = 0; k < ncell; ++k)
                     if (!std::isfinite(arr[k])) return set_error(h, SCATMAN_ERR_ARG, "map index values must be finite");
     }
-    if (s->kind == SCATMAN_SPHERE && !(s->r > 0)) return set_error(h, SCATMAN_ERR_ARG, "sphere radius must be > 0");
-    if (s->kind == SCATMAN_ELLIPSOID && !(s->a > 0 && s->b > 0 && s->c > 0))
-        return set_error(h, SCATMAN_ERR_ARG, "ellipsoid semi-axes must be > 0");
-    if (s->kind == SCATMAN_SPHHARM) {
-        if (!(s->R0 > 0)) return set_error(h, SCATMAN_ERR_ARG, "R0 must be > 0");
-        if (s->lmax < 0 || s->lmax > SCATMAN_MAX_LMAX) return set_error(h, SCATMAN_ERR_ARG, "lmax out of range");
-        if (s->lmax > 0 && !s->alm) return set_error(h, SCATMAN_ERR_ARG, "alm is NULL");
+    {
+        std::string why;
+        if (!check_param_shape(s, &why)) return set_error(h, SCATMAN_ERR_ARG, why);
     }
-    if (!std::isfinite(s->delta) || !std::isfinite(s->beta))
-        return set_error(h, SCATMAN_ERR_ARG, "delta and beta must be finite");
 
     h->shape = *s;
     // the map arrays are borrowed for this call only
@@ -592,7 +668,7 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
                            (float *)I_dev, h->d_err, h->sm_count, h->stream, h->d_tail);
     } else {
         e = launch_msft_simt(h->precision == SCATMAN_FP64, h->d_s, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
-                             str_re, str_im, h->d_A, I_dev, h->d_partial, h->splits, h->stream);
+                             str_re, str_im, h->d_A, I_dev, h->d_partial, h->splits, h->stream, h->d_bounds);
     }
     int rc = check_cuda(h, e, "forward");
     if (rc) return rc;
@@ -619,6 +695,22 @@ int scatman_sync(scatman_handle *h) {
                          "a kernel gave up a bounded wait (error bits " + std::to_string(err) + ")");
     }
     return SCATMAN_OK;
+}
+
+void scatman_debug_fail_allocation(long long after) { scm::g_fail_countdown.store(after < 0 ? -1 : after); }
+
+int scatman_set_wait_limit(scatman_handle *h, double seconds) {
+    if (!h) return SCATMAN_ERR_ARG;
+    if (!std::isfinite(seconds)) return set_error(h, SCATMAN_ERR_ARG, "the wait limit must be finite");
+    unsigned long long ns = 0;
+    if (seconds > 0) {
+        const double v = seconds * 1e9;
+        ns = v < 1.0 ? 1ull : v >= (double)scm::kWaitLimitMaxNs ? 0ull : (unsigned long long)v;
+    }
+    int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (rc) return rc;
+    return check_cuda(h, cudaMemcpy(reinterpret_cast<char *>(h->d_err) + 8, &ns, sizeof(ns), cudaMemcpyHostToDevice),
+                      "wait limit");
 }
 
 int scatman_acquire(scatman_handle *h, const scatman_shape *shape, void *I_host) {
@@ -740,17 +832,17 @@ int scatman_contraction_flops(scatman_handle *h, double *issued, double *dense) 
         *issued = uq_tc_issued_flops(c.nx, c.nz, c.det_nx, c.det_ny, h->split);
         return SCATMAN_OK;
     }
-    if (!h->tensor_core) {
-        *dense = 8.0 * dense_pairs;
-        *issued = *dense;
-        return SCATMAN_OK;
-    }
     std::vector<int> b(4 * (size_t)c.nz);
     int rc = check_cuda(h, cudaMemcpyAsync(b.data(), h->d_bounds, b.size() * sizeof(int), cudaMemcpyDeviceToHost,
                                            h->stream),
                         "bounds download");
     if (rc) return rc;
     if ((rc = scatman_sync(h))) return rc;
+    if (!h->tensor_core) {
+        *dense = 8.0 * dense_pairs;
+        *issued = h->uniform_q ? *dense : simt_issued_flops(b.data(), c.nz, c.ny, h->n_pix, h->precision == SCATMAN_FP64);
+        return SCATMAN_OK;
+    }
     *dense = 8.0 * dense_pairs * (h->split ? 2.0 : 1.0);
     *issued = tc_issued_flops(b.data(), c.nz, h->Nxp, h->Nyp, h->n_pix, h->split);
     return SCATMAN_OK;
@@ -932,29 +1024,15 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
     if (!cfg || !s || !I_dev) return fail(SCATMAN_ERR_ARG, "NULL argument");
     const scatman_config &c = *cfg;
     if (c.precision != SCATMAN_FP32) return fail(SCATMAN_ERR_ARG, "the no-allocation forward runs in SCATMAN_FP32 only");
-    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.nz > 256)
-        return fail(SCATMAN_ERR_ARG, "grid sizes must be >= 1 and nz <= 256");
-    if (!(c.voxel > 0) || !(c.wavelength > 0)) return fail(SCATMAN_ERR_ARG, "voxel and wavelength must be positive");
-    if (c.soft && !(c.soft_width > 0)) return fail(SCATMAN_ERR_ARG, "soft occupancy needs soft_width > 0");
-    long long n_pix;
-    if (c.q_list) {
-        if (c.n_q < 1) return fail(SCATMAN_ERR_ARG, "n_q must be >= 1 with q_list");
-        n_pix = c.n_q;
-    } else {
-        if (c.det_nx < 1 || c.det_ny < 1) return fail(SCATMAN_ERR_ARG, "detector size must be >= 1");
-        if (!(c.theta_max_deg > 0 && c.theta_max_deg < 90))
-            return fail(SCATMAN_ERR_ARG, "theta_max_deg must lie in (0, 90)");
-        n_pix = (long long)c.det_nx * c.det_ny;
-    }
+    long long n_pix = 0;
+    std::string why;
+    if (!check_config(c, &n_pix, &why)) return fail(SCATMAN_ERR_ARG, why);
+    // the flat detector's q (or the caller's q_list) only: the uniform-q
+    // detector needs its own q table and a masked field
+    if (c.detector != SCATMAN_DETECTOR_FLAT && !c.q_list)
+        return fail(SCATMAN_ERR_ARG, "the no-allocation forward supports the flat detector or a q_list only");
     if (s->kind < SCATMAN_SPHERE || s->kind > SCATMAN_SPHHARM) return fail(SCATMAN_ERR_ARG, "unknown shape kind");
-    if (s->kind == SCATMAN_SPHERE && !(s->r > 0)) return fail(SCATMAN_ERR_ARG, "sphere radius must be > 0");
-    if (s->kind == SCATMAN_ELLIPSOID && !(s->a > 0 && s->b > 0 && s->c > 0))
-        return fail(SCATMAN_ERR_ARG, "ellipsoid semi-axes must be > 0");
-    if (s->kind == SCATMAN_SPHHARM) {
-        if (!(s->R0 > 0)) return fail(SCATMAN_ERR_ARG, "R0 must be > 0");
-        if (s->lmax < 0 || s->lmax > SCATMAN_MAX_LMAX) return fail(SCATMAN_ERR_ARG, "lmax out of range");
-        if (s->lmax > 0 && !s->alm) return fail(SCATMAN_ERR_ARG, "alm is NULL");
-    }
+    if (!check_param_shape(s, &why)) return fail(SCATMAN_ERR_ARG, why);
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(SCATMAN_ERR_UNSUPPORTED, "no CUDA device");
@@ -980,7 +1058,6 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
         return fail(SCATMAN_ERR_ARG, "problem needs " + std::to_string(need) + " bytes of scratch; the no-allocation "
                                      "forward holds " + std::to_string(kNoAllocScratchBytes) + " bytes");
     void *base = nullptr;
-    std::string why;
     int rc = noalloc_scratch(dev, &base, &why);
     if (rc) return fail(rc, why);
     unsigned char *b = (unsigned char *)base;
@@ -1020,9 +1097,10 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
     sp.cx = s->cx;
     sp.cy = s->cy;
     sp.cz = s->cz;
-    if (s->kind == SCATMAN_SPHHARM)
+    if (s->kind == SCATMAN_SPHHARM && s->lmax > 0)        // alm may be NULL at lmax = 0
         for (int k = 0; k < (s->lmax + 1) * (s->lmax + 1); ++k) sp.alm[k] = s->alm[k];
     finish_shape_params(&sp);
+    set_radius_band(s, &sp);
     const GridParams gp = make_grid(c.nx, c.ny, c.nz, c.voxel, k0, s->delta, s->beta);
     SliceOut so;
     so.layout = kLayoutC32;
@@ -1036,7 +1114,7 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
     if (e != cudaSuccess) return fail(SCATMAN_ERR_CUDA, std::string("voxelise: ") + cudaGetErrorString(e));
     const double d = s->delta, bb = s->beta;
     e = launch_msft_simt(false, d_s, d_q, n_pix, c.nx, c.ny, c.nz, c.voxel, -2.0 * d + d * d - bb * bb,
-                         2.0 * bb - 2.0 * d * bb, d_A, I_dev, d_part, splits, st);
+                         2.0 * bb - 2.0 * d * bb, d_A, I_dev, d_part, splits, st, nullptr);
     if (e != cudaSuccess) return fail(SCATMAN_ERR_CUDA, std::string("forward: ") + cudaGetErrorString(e));
     return SCATMAN_OK;
 }

@@ -16,6 +16,16 @@ namespace scm {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// Device allocation used by every buffer of the library; a test hook
+// (scatman_debug_fail_allocation) can make one of them fail on the host.
+cudaError_t device_malloc(void **p, size_t bytes);
+
+// Status block of a handle on the device (kStatusBytes): the error word (int,
+// byte 0) that kernels set, and at byte 8 an optional shorter limit in ns for
+// the kernels' work waits (unsigned long long; 0 = the default).
+constexpr size_t kStatusBytes = 16;
+constexpr unsigned long long kWaitLimitMaxNs = 2000000000ull;   // every bounded wait: 2 s at most
+
 // Bits of the device error word written by kernels.
 enum : int {
     kErrTimeoutProducer = 1,
@@ -232,9 +242,12 @@ cudaError_t launch_uq_tc(const CUtensorMap &map, const float2 *qz, int nx, int n
                          bool bf16, float2 *A, float *I, int *err, int sm_count, cudaStream_t st);
 // CUDA-core contraction (msft_simt.cu).
 int simt_splits(long long n_pix, int nx, int nz, int sm_count);
+// bounds: the voxeliser's per-slice occupied boxes (4 nz ints), or NULL for a dense sum.
 cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long long n_pix, int nx, int ny,
                              int nz, double voxel, double str_re, double str_im, void *A, void *I,
-                             void *partial, int splits, cudaStream_t st);
+                             void *partial, int splits, cudaStream_t st, const int *bounds);
+// Real flops the CUDA-core contraction executes with box skipping (host copy of the bounds).
+double simt_issued_flops(const int *bounds, int nz, int ny, long long n_pix, bool fp64);
 // Tensor-core contraction (msft_tc.cu).
 size_t tc_ring_bytes(int Nyp, int Nxp, bool split);
 // tail_part: scratch of tc_tail_part_bytes for the partial fields of the last

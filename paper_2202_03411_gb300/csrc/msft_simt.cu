@@ -5,9 +5,12 @@
 // of a group of (z, x) columns are staged in shared memory and read as
 // broadcasts.  Per column the y-sum G = sum_y e^{-i q_y y} s is formed with
 // complex FMAs and accumulated with the column phase e^{-i (q_x x + q_z z)}
-// (re-anchored every 16 columns, stepped in between).  The (z, x) columns can
-// be split across blocks; partial fields are summed in a fixed order by a
-// second kernel, so the result does not depend on scheduling.
+// (re-anchored every 16 columns and after a skipped column, stepped in
+// between).  With the voxeliser's per-slice occupied boxes, columns outside
+// their slice's x range and y chunks outside its y range are skipped (their
+// slice values are zero).  The (z, x) columns can be split across blocks;
+// partial fields are summed in a fixed order by a second kernel, so the
+// result does not depend on scheduling.
 #include "internal.cuh"
 
 namespace scm {
@@ -30,9 +33,11 @@ __global__ void __launch_bounds__(kSimtThreads) msft_simt_kernel(const typename 
                                                                  const double *__restrict__ q, long long n_pix,
                                                                  int nx, int ny, int nz, double voxel,
                                                                  int cols_per_split,
+                                                                 const int *__restrict__ bounds,
                                                                  typename Cplx<R>::T *__restrict__ partial) {
     using C = typename Cplx<R>::T;
     __shared__ C tile[kCols][YC];
+    __shared__ int s_live[kCols];         // per staged column: 1 if its slice is occupied there in this y chunk
     const long long pix0 = (long long)blockIdx.x * (kSimtThreads * kPPT) + threadIdx.x;
     const int ncol = nx * nz;
     const int col_begin = blockIdx.y * cols_per_split;
@@ -96,21 +101,33 @@ __global__ void __launch_bounds__(kSimtThreads) msft_simt_kernel(const typename 
             ph[pp].x = (R)1;
             ph[pp].y = (R)0;
         }
-        int zcur = -1;
+        int zcur = -1, xprev = -2;
         C Z[kPPT];
         for (int c0 = col_begin; c0 < col_end; c0 += kCols) {
+            __syncthreads();
+            for (int cl = threadIdx.x; cl < kCols; cl += kSimtThreads) {
+                const int col = c0 + cl;
+                bool live = col < col_end;
+                if (live && bounds) {
+                    const int z = col / nx, x = col - z * nx;
+                    live = x >= bounds[z] && x < bounds[nz + z] && y0 < bounds[3 * nz + z] &&
+                           y0 + YC > bounds[2 * nz + z];
+                }
+                s_live[cl] = live ? 1 : 0;
+            }
             __syncthreads();
             for (int it = threadIdx.x; it < kCols * YC; it += kSimtThreads) {
                 const int cl = it / YC, k = it % YC;
                 const int col = c0 + cl;
                 C v;
                 v.x = v.y = (R)0;
-                if (col < col_end && y0 + k < ny) v = s[(size_t)col * ny + y0 + k];
+                if (s_live[cl] && y0 + k < ny) v = s[(size_t)col * ny + y0 + k];
                 tile[cl][k] = v;
             }
             __syncthreads();
             const int nc = min(kCols, col_end - c0);
             for (int cl = 0; cl < nc; ++cl) {
+                if (!s_live[cl]) continue;             // block-uniform: no divergence
                 const int col = c0 + cl;
                 const int z = col / nx, x = col - z * nx;
                 if (z != zcur) {
@@ -125,8 +142,10 @@ __global__ void __launch_bounds__(kSimtThreads) msft_simt_kernel(const typename 
                             Z[pp] = expmi<R>(qz[pp], (z - 0.5 * (nz - 1)) * voxel);
                     }
                     zcur = z;
+                    xprev = -2;
                 }
-                const bool anchor = (x % 16 == 0) || (cl == 0) || (col == col_begin);
+                const bool anchor = (x % 16 == 0) || (x != xprev + 1);
+                xprev = x;
 #pragma unroll
                 for (int pp = 0; pp < kPPT; ++pp) {
                     if (anchor) {
@@ -197,6 +216,19 @@ __global__ void msft_reduce_kernel(const typename Cplx<R>::T *__restrict__ parti
     I[p] = a.x * a.x + a.y * a.y;
 }
 
+double simt_issued_flops(const int *bounds, int nz, int ny, long long n_pix, bool fp64) {
+    const int yc = fp64 ? 8 : 16;       // the y chunk of the FP64 / FP32 kernel
+    double cols_y = 0.0;
+    for (int z = 0; z < nz; ++z) {
+        const int xlo = bounds[z], xhi = bounds[nz + z], ylo = bounds[2 * nz + z], yhi = bounds[3 * nz + z];
+        if (xlo >= xhi || ylo >= yhi) continue;
+        int chunks = 0;
+        for (int y0 = 0; y0 < ny; y0 += yc) chunks += (y0 < yhi && y0 + yc > ylo) ? 1 : 0;
+        cols_y += (double)(xhi - xlo) * chunks * yc;
+    }
+    return 8.0 * cols_y * (double)n_pix;
+}
+
 int simt_splits(long long n_pix, int nx, int nz, int sm_count) {
     long long pblocks = (n_pix + kSimtThreads * kPPT - 1) / (kSimtThreads * kPPT);
     int ncol_groups = (nx * nz + kCols - 1) / kCols;
@@ -209,7 +241,7 @@ int simt_splits(long long n_pix, int nx, int nz, int sm_count) {
 
 cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long long n_pix, int nx, int ny, int nz,
                              double voxel, double str_re, double str_im, void *A, void *I, void *partial,
-                             int splits, cudaStream_t st) {
+                             int splits, cudaStream_t st, const int *bounds) {
     long long pblocks = (n_pix + kSimtThreads * kPPT - 1) / (kSimtThreads * kPPT);
     int ncol = nx * nz;
     int groups = (ncol + kCols - 1) / kCols;
@@ -220,12 +252,12 @@ cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long lon
     unsigned rblocks = (unsigned)((n_pix + rthreads - 1) / rthreads);
     if (fp64) {
         msft_simt_kernel<double, 8><<<grid, kSimtThreads, 0, st>>>(
-            (const double2 *)s, q, n_pix, nx, ny, nz, voxel, per, (double2 *)partial);
+            (const double2 *)s, q, n_pix, nx, ny, nz, voxel, per, bounds, (double2 *)partial);
         msft_reduce_kernel<double><<<rblocks, rthreads, 0, st>>>((const double2 *)partial, used, n_pix, str_re,
                                                                  str_im, (double2 *)A, (double *)I);
     } else {
         msft_simt_kernel<float, 16><<<grid, kSimtThreads, 0, st>>>(
-            (const float2 *)s, q, n_pix, nx, ny, nz, voxel, per, (float2 *)partial);
+            (const float2 *)s, q, n_pix, nx, ny, nz, voxel, per, bounds, (float2 *)partial);
         msft_reduce_kernel<float><<<rblocks, rthreads, 0, st>>>((const float2 *)partial, used, n_pix,
                                                                 (float)str_re, (float)str_im, (float2 *)A,
                                                                 (float *)I);

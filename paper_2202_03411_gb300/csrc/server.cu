@@ -147,9 +147,9 @@ static int create_cached(const scatman_server_config &scfg, Slot &s, const Req &
         return rc;
     }
     const long long n = c.h->n_pix;
-    if (cudaMalloc((void **)&c.d_target, n * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&c.d_w, n * (f64 ? 8 : 4)) != cudaSuccess ||
-        cudaMalloc((void **)&c.d_loss, 256 * sizeof(double)) != cudaSuccess) {
+    if (device_malloc((void **)&c.d_target, n * sizeof(float)) != cudaSuccess ||
+        device_malloc(&c.d_w, n * (f64 ? 8 : 4)) != cudaSuccess ||
+        device_malloc((void **)&c.d_loss, 256 * sizeof(double)) != cudaSuccess) {
         free_cached(c);
         return SCATMAN_ERR_OOM;
     }
@@ -335,7 +335,7 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     }
     long long b = 0;
     b += round_2mib(npix * 24);                 // q
-    if (tc) b += round_2mib(24LL * c->nz + 8);  // slice bounds and occupied-slice list
+    b += round_2mib(24LL * c->nz + 8);          // slice bounds and occupied-slice list
     b += round_2mib(nvox * 4);                  // occupancy
     b += round_2mib(s_bytes);                   // slices
     b += round_2mib(npix * cx);                 // field cache
@@ -447,6 +447,23 @@ int scatman_server_wait(scatman_server *srv, long long ticket, double timeout_s,
     if (status) *status = r->status;
     if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
     srv->reqs.erase(it);
+    return SCATMAN_OK;
+}
+
+int scatman_server_cancel(scatman_server *srv, long long ticket) {
+    if (!srv) return SCATMAN_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return SCATMAN_ERR_ARG;
+    std::shared_ptr<Req> r = it->second;
+    auto q = std::find(srv->queue.begin(), srv->queue.end(), r);
+    if (q == srv->queue.end()) return SCATMAN_ERR_STATE;     // admitted, running or finished
+    srv->queue.erase(q);
+    r->status = SCATMAN_ERR_CANCELLED;
+    r->t_done = Clock::now();
+    r->done = true;
+    ++srv->stats.cancelled;
+    srv->cv.notify_all();
     return SCATMAN_OK;
 }
 

@@ -5,7 +5,7 @@
 
 namespace scm {
 
-constexpr unsigned long long kTimeoutNs = 2000000000ull;   // bounded waits: 2 s
+constexpr unsigned long long kTimeoutNs = kWaitLimitMaxNs;   // bounded waits: 2 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -35,16 +35,26 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// Time limit of a wait.  `err` is the handle's status block: the error bits,
+// then at byte 8 an optional shorter limit in ns for the work waits (0: the
+// default).  Drain waits, which keep a CTA alive until its own TMA and MMA
+// work has landed, always take the full limit.
+__device__ __forceinline__ unsigned long long wait_limit_ns(const int *err, int code) {
+    if (code == kErrTimeoutDrain) return kTimeoutNs;
+    const unsigned long long v = *reinterpret_cast<const volatile unsigned long long *>(err + 2);
+    return v == 0 || v > kTimeoutNs ? kTimeoutNs : v;
+}
 // Bounded wait on a phase parity (slow path, out of line).  Returns false when
 // the wait gave up (time limit, or another role already gave up).
 static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag,
                                                    int *err, int code) {
     const unsigned long long t0 = global_ns();
+    const unsigned long long limit = wait_limit_ns(err, code);
     while (true) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (global_ns() - t0 > kTimeoutNs) {
+        if (global_ns() - t0 > limit) {
             atomicOr(err, code);
             *abort_flag = 1;
             return false;

@@ -16,6 +16,7 @@ import numpy as np
 
 from . import _lib
 from .api import ScatmanError, make_config, make_shape
+from .types import n_params
 
 
 class Server:
@@ -46,7 +47,7 @@ class Server:
         tgt = np.ascontiguousarray(target, dtype=np.float32)
         req.target = tgt.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         req.want_gradient = int(want_gradient)
-        res = {"loss": np.zeros(1), "grad": np.zeros(shape.n_params()),
+        res = {"loss": np.zeros(1), "grad": np.zeros(n_params(shape)),
                "I": np.zeros(geometry.n_pix, dtype=np.float32) if want_I else None}
         req.grad_out = res["grad"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         req.loss_out = res["loss"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -71,6 +72,16 @@ class Server:
         with self._lock:
             self._live.pop(ticket, None)
         return st.value, lat.value
+
+    def cancel(self, ticket: int) -> bool:
+        """Cancels a queued request: True if it will not run (its wait then
+        reports ERR_CANCELLED), False if it was already admitted."""
+        code = _lib.load().scatman_server_cancel(self.ptr, ticket)
+        if code == _lib.SCATMAN_ERR_STATE:
+            return False
+        if code != 0:
+            raise ScatmanError(code, "scatman_server_cancel")
+        return True
 
     def stats(self) -> dict:
         s = _lib.scatman_server_stats()

@@ -110,3 +110,51 @@ def test_footprint_counts_the_uniform_q_buffers(lib):
     assert footprint_bytes(g, "fp32") < footprint_bytes(flat, "fp32")
     g_small = Geometry(56, 56, 56, 1.0, 1.0, 30.0, 256, 256, DETECTOR_UNIFORM_Q)
     assert 0 < footprint_bytes(g_small, "fp32") < footprint_bytes(g, "fp32")
+
+
+def test_noalloc_host_checks(lib):
+    """Checks that answer before any device is touched (no GPU needed)."""
+    from paper_2202_03411_gb300.api import make_shape
+    from workloads import SPHERE, Shape
+    st, keep = make_shape(Shape(SPHERE, r=4.0, delta=0.01, beta=0.001))
+    fake = ctypes.c_void_p(16)          # never dereferenced: the calls fail their argument checks first
+    for g, frag in ((Geometry(16, 16, 16, 1.0, 8.0, 30.0, 8, 8, 1), "flat detector"),
+                    (Geometry(16, 5000, 16, 1.0, 8.0, 30.0, 8, 8), "4096"),
+                    (Geometry(16, 16, 16, 1.0, 8.0, 30.0, 8, 8, 7), "detector")):
+        cfg, _ = make_config(g, "fp32")
+        assert lib.scatman_forward_noalloc(ctypes.byref(cfg), ctypes.byref(st), None, fake, None) == \
+            _lib.SCATMAN_ERR_ARG
+        assert frag in lib.scatman_last_error(None).decode()
+    cfg, _ = make_config(Geometry(16, 16, 16, 1.0, 8.0, 30.0, 8, 8), "tc_bf16_split")
+    assert lib.scatman_forward_noalloc(ctypes.byref(cfg), ctypes.byref(st), None, fake, None) == \
+        _lib.SCATMAN_ERR_ARG
+
+
+def test_failure_hooks_reject_null(lib):
+    assert lib.scatman_set_wait_limit(None, 1.0) == _lib.SCATMAN_ERR_ARG
+    assert lib.scatman_server_cancel(None, 1) == _lib.SCATMAN_ERR_ARG
+    lib.scatman_debug_fail_allocation(-1)
+
+
+class _FakeTensor:
+    def __init__(self, is_cuda=True, dtype="torch.float32", contiguous=True, n=100):
+        self.is_cuda, self.dtype, self._c, self._n = is_cuda, dtype, contiguous, n
+
+    def is_contiguous(self):
+        return self._c
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):
+        return 4096
+
+
+def test_binding_checks_output_buffers_before_any_kernel():
+    from paper_2202_03411_gb300.api import _device_ptr
+    assert _device_ptr(_FakeTensor(), ["float32"], 100, "I").value == 4096
+    assert _device_ptr(None, ["float32"], 100, "A").value is None
+    for bad in (_FakeTensor(is_cuda=False), _FakeTensor(dtype="torch.float64"), _FakeTensor(contiguous=False),
+                _FakeTensor(n=99)):
+        with pytest.raises(ValueError):
+            _device_ptr(bad, ["float32"], 100, "I")

@@ -34,13 +34,11 @@ def _pattern(g, prec):
     return h, I
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tc_bf16_split"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tc_bf16_split", "tc_f16_split"])
 @pytest.mark.parametrize("detector", [0, 1])
 @pytest.mark.parametrize("density", [1e-2, 50.0, 1e5])
 def test_photon_counts_match_oracle(prec, detector, density):
     import paper_2202_03411_gb300 as sm
-    if detector == 1 and prec.startswith("tc"):
-        pytest.skip("the uniform-q detector runs in the CUDA-core modes")
     g = Geometry(24, 24, 24, 1.0, 8.0, 40.0, 96, 80, detector)
     h, I = _pattern(g, prec)
     lam, cnt = sm.scatman_photon_counts(h, density, 12345, I)

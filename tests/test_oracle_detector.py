@@ -28,6 +28,28 @@ def _lambda_field(lams, g=G):
     return target / (amp * amp * dom)                 # photon density 1
 
 
+# Known-answer vectors of Philox-4x32-10 published with the generator by its
+# authors (Salmon, Moraes, Dror and Shaw, "Parallel random numbers: as easy as
+# 1, 2, 3", SC'11; the Random123 distribution's known-answer test list):
+# (counter words 0-3, key words 0-1) -> output words 0-3.
+PHILOX_KAT = [
+    ((0x00000000, 0x00000000, 0x00000000, 0x00000000), (0x00000000, 0x00000000),
+     (0x6627e8d5, 0xe169c58d, 0xbc57ac4c, 0x9b00dbd8)),
+    ((0xffffffff, 0xffffffff, 0xffffffff, 0xffffffff), (0xffffffff, 0xffffffff),
+     (0x408f276d, 0x41c83b0e, 0xa20bc7c6, 0x6d5451fd)),
+    ((0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344), (0xa4093822, 0x299f31d0),
+     (0xd16cfe09, 0x94fdcceb, 0x5001e420, 0x24126ea1)),
+]
+
+
+@pytest.mark.parametrize("counter,key,expected", PHILOX_KAT)
+def test_philox_known_answers(counter, key, expected):
+    """A wrong round count, multiplier, Weyl key increment or word order fails
+    at least one of the three published vectors."""
+    got = [int(v) for v in oracle.philox(counter, key)]
+    assert got == list(expected), [hex(v) for v in got]
+
+
 def test_philox_uniform_and_avalanche():
     rng = np.random.default_rng(0)
     words = np.array([oracle.philox([i, 0, 0, 0], [123, 456]) for i in range(4000)]).ravel()
