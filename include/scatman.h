@@ -271,6 +271,14 @@ SCATMAN_API int scatman_backward(scatman_handle *h, const void *dLdI_dev, double
  * reports ERR_TIMEOUT and the results of that call are invalid.  The handle
  * stays usable.  Synchronises the stream.  Errors: ERR_ARG (NaN), ERR_CUDA.
  *
+ * scatman_debug_stall: with on != 0, the MMA warps of the handle's
+ * tensor-core contraction and adjoint kernels first wait on a barrier that no
+ * thread arrives at, so that wait runs out after the wait limit and the
+ * kernel takes its abort path exactly as after a real stall (the other warps
+ * stop at their next wait, in-flight TMA copies and MMAs are drained, tensor
+ * memory is freed); the call then reports ERR_TIMEOUT.  on = 0 restores
+ * normal operation.  Synchronises the stream.  Errors: ERR_ARG, ERR_CUDA.
+ *
  * scatman_debug_fail_allocation: process-wide; with after >= 0 the device
  * allocation that follows `after` more successful ones (in any handle or
  * server of the process) fails once as if the device were out of memory
@@ -278,6 +286,7 @@ SCATMAN_API int scatman_backward(scatman_handle *h, const void *dLdI_dev, double
  * allocated); after < 0 disarms it.
  */
 SCATMAN_API int scatman_set_wait_limit(scatman_handle *h, double seconds);
+SCATMAN_API int scatman_debug_stall(scatman_handle *h, int on);
 SCATMAN_API void scatman_debug_fail_allocation(long long after);
 
 /* Number of gradient entries for the current shape (0 before voxelise). */

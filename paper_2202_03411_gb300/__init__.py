@@ -10,7 +10,7 @@ from .api import (Handle, ScatmanError, scatman_acquire, scatman_acquire_batch, 
                   scatman_create, scatman_destroy,
                   scatman_device_bytes, scatman_elem_size, scatman_forward, scatman_forward_noalloc, scatman_get_occupancy,
                   scatman_get_q, scatman_get_slices, scatman_last_error, scatman_n_pix, scatman_param_count,
-                  scatman_photon_counts, scatman_set_wait_limit, scatman_debug_fail_allocation, scatman_sync,
+                  scatman_photon_counts, scatman_set_wait_limit, scatman_debug_fail_allocation, scatman_debug_stall, scatman_sync,
                   scatman_version, scatman_voxelise)
 from .types import Geometry, Shape
 
@@ -18,6 +18,6 @@ __all__ = [
     "Handle", "ScatmanError", "scatman_acquire", "scatman_acquire_batch", "scatman_backward", "scatman_contraction_flops", "scatman_create", "scatman_destroy",
     "scatman_device_bytes", "scatman_elem_size", "scatman_forward", "scatman_forward_noalloc", "scatman_get_occupancy", "scatman_get_q",
     "scatman_get_slices", "scatman_last_error", "scatman_n_pix", "scatman_param_count", "scatman_photon_counts",
-    "scatman_sync", "scatman_set_wait_limit", "scatman_debug_fail_allocation", "Geometry", "Shape", "types",
+    "scatman_sync", "scatman_set_wait_limit", "scatman_debug_fail_allocation", "scatman_debug_stall", "Geometry", "Shape", "types",
     "scatman_version", "scatman_voxelise",
 ]

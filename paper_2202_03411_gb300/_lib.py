@@ -116,6 +116,7 @@ SIGNATURES = {
     "scatman_server_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(scatman_server_stats)]),
     "scatman_server_cancel": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_longlong]),
     "scatman_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double]),
+    "scatman_debug_stall": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "scatman_debug_fail_allocation": (None, [ctypes.c_longlong]),
     "scatman_server_destroy": (None, [ctypes.c_void_p]),
     "scatman_footprint_bytes": (ctypes.c_longlong, [ctypes.POINTER(scatman_config)]),

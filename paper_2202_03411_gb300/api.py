@@ -279,6 +279,12 @@ def scatman_set_wait_limit(h: Handle, seconds: float) -> None:
     _check(_lib.load().scatman_set_wait_limit(h.ptr, float(seconds)), h, "set_wait_limit")
 
 
+def scatman_debug_stall(h: Handle, on: bool) -> None:
+    """Failure-path hook: the handle's tensor-core MMA warps first wait on a
+    barrier nothing arrives at, so the kernels take their time-out path."""
+    _check(_lib.load().scatman_debug_stall(h.ptr, int(bool(on))), h, "debug_stall")
+
+
 def scatman_debug_fail_allocation(after: int) -> None:
     """Failure-path hook: the device allocation after `after` more successful
     ones fails once (process-wide); a negative value disarms it."""

@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
     uint64_t *bfull = bars + kAdjMaxStages;         // y-phase operand copied (bytes)
     uint64_t *empty = bars + 2 * kAdjMaxStages;
     uint64_t *done = bars + 3 * kAdjMaxStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *never = done + 1;                     // no thread arrives here (the failure-path test waits on it)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(never + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
             mbar_init(smem_u32(&empty[s]), 1);
         }
         mbar_init(smem_u32(done), 1);
+        mbar_init(smem_u32(never), 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -166,7 +168,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         // warp-wide loop; one elected lane issues the MMAs and commits
         const uint32_t d0 = tmem_base, d1 = tmem_base + (uint32_t)Nn;
         const uint64_t desc0 = sw128_desc(smem_u32(base));
-        for (int c = 0; c < n_chunks; ++c) {
+        const bool stalled =
+            stall_requested(P.err) && !warp_wait(smem_u32(never), 0, abort_flag, P.err, kErrTimeoutMma);
+        for (int c = 0; c < (stalled ? 0 : n_chunks); ++c) {
             const uint32_t s = c % NS, ph = (c / NS) & 1;
             if (!warp_wait(smem_u32(&full[s]), ph, abort_flag, P.err, kErrTimeoutMma)) break;
             if (!warp_wait(smem_u32(&bfull[s]), ph, abort_flag, P.err, kErrTimeoutMma)) break;

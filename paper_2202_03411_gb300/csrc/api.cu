@@ -713,6 +713,15 @@ int scatman_set_wait_limit(scatman_handle *h, double seconds) {
                       "wait limit");
 }
 
+int scatman_debug_stall(scatman_handle *h, int on) {
+    if (!h) return SCATMAN_ERR_ARG;
+    int rc = check_cuda(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+    if (rc) return rc;
+    const int v = on ? 1 : 0;
+    return check_cuda(h, cudaMemcpy(reinterpret_cast<char *>(h->d_err) + 4, &v, sizeof(v), cudaMemcpyHostToDevice),
+                      "stall flag");
+}
+
 int scatman_acquire(scatman_handle *h, const scatman_shape *shape, void *I_host) {
     if (!h || !shape || !I_host) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
     int rc = scatman_voxelise(h, shape);

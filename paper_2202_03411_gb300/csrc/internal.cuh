@@ -21,8 +21,11 @@ constexpr double kPi = 3.14159265358979323846;
 cudaError_t device_malloc(void **p, size_t bytes);
 
 // Status block of a handle on the device (kStatusBytes): the error word (int,
-// byte 0) that kernels set, and at byte 8 an optional shorter limit in ns for
-// the kernels' work waits (unsigned long long; 0 = the default).
+// byte 0) that kernels set; a test flag (int, byte 4) that makes the
+// tensor-core kernels' MMA warps first wait on a barrier nothing arrives at,
+// so that wait runs out and takes the abort path; and at byte 8 an optional
+// shorter limit in ns for the kernels' work waits (unsigned long long; 0 =
+// the default).
 constexpr size_t kStatusBytes = 16;
 constexpr unsigned long long kWaitLimitMaxNs = 2000000000ull;   // every bounded wait: 2 s at most
 

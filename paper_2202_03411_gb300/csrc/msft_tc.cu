@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t *tempty = tfull + 2;
     uint64_t *drain = tempty + 2;
     uint64_t *a_full = drain + 1;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_full + 1);
+    uint64_t *never = a_full + 1;              // no thread arrives here (the failure-path test waits on it)
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(never + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -259,6 +260,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         mbar_init(smem_u32(drain), 2);
         mbar_init(smem_u32(a_full), kEpiThreads);
+        mbar_init(smem_u32(never), 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -336,6 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         uint32_t head_off = 0;
         uint32_t tl = 0;
         const int n_occ = (int)__ldg(&P.list[0].x);
+        if (stall_requested(P.err) && !warp_wait(smem_u32(never), 0, abort_flag, P.err, kErrTimeoutMma)) ok = false;
         for (int u = blockIdx.x; u < P.num_units && ok; u += gridDim.x, ++tl) {
             if (!warp_wait(smem_u32(a_full), tl & 1, abort_flag, P.err, kErrTimeoutMma)) break;
             tc_fence_after();

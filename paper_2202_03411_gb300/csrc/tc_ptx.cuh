@@ -44,6 +44,10 @@ __device__ __forceinline__ unsigned long long wait_limit_ns(const int *err, int 
     const unsigned long long v = *reinterpret_cast<const volatile unsigned long long *>(err + 2);
     return v == 0 || v > kTimeoutNs ? kTimeoutNs : v;
 }
+// The status block's test flag: wait once on a barrier that never completes.
+__device__ __forceinline__ bool stall_requested(const int *err) {
+    return *reinterpret_cast<const volatile int *>(err + 1) != 0;
+}
 // Bounded wait on a phase parity (slow path, out of line).  Returns false when
 // the wait gave up (time limit, or another role already gave up).
 static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag,

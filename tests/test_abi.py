@@ -132,6 +132,7 @@ def test_noalloc_host_checks(lib):
 
 def test_failure_hooks_reject_null(lib):
     assert lib.scatman_set_wait_limit(None, 1.0) == _lib.SCATMAN_ERR_ARG
+    assert lib.scatman_debug_stall(None, 1) == _lib.SCATMAN_ERR_ARG
     assert lib.scatman_server_cancel(None, 1) == _lib.SCATMAN_ERR_ARG
     lib.scatman_debug_fail_allocation(-1)
 

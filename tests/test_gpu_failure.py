@@ -1,10 +1,12 @@
 """Failure paths on the GPU, reached without faulting it.
 
-* Bounded waits: a handle's wait limit is shortened to 1 ns, so the tensor-core
-  kernels' waits on other warps give up (each kernel then drains its own TMA
-  copies and MMAs with the full limit, frees its tensor memory and returns);
-  the call reports ERR_TIMEOUT and the same handle, with the limit restored,
-  computes the right answer again.
+* Bounded waits: with the handle's test flag set, the tensor-core kernels' MMA
+  warps first wait on a barrier that nothing arrives at (a flag nothing sets);
+  with the wait limit shortened to 10 ms that wait runs out, the kernel takes
+  its abort path (the other warps stop at their next wait, the TMA copies and
+  MMAs in flight are drained with the full limit, tensor memory is freed) and
+  the call reports ERR_TIMEOUT.  The same handle, with the flag cleared and
+  the limit restored, computes the right answer again.
 * Allocation failure injected on the host (scatman_debug_fail_allocation):
   scatman_create returns ERR_OOM at every point of its allocation sequence and
   releases what it had; the server reports ERR_OOM for the request whose
@@ -40,11 +42,13 @@ def test_forward_wait_timeout_is_reported_and_the_handle_recovers():
     h = sm.scatman_create(g, "tc_bf16_split")
     I = torch.empty(g.n_pix, dtype=torch.float32, device="cuda")
     sm.scatman_voxelise(h, s)
-    sm.scatman_set_wait_limit(h, 1e-9)
+    sm.scatman_set_wait_limit(h, 0.01)
+    sm.scatman_debug_stall(h, True)
     sm.scatman_forward(h, I)
     with pytest.raises(sm.ScatmanError) as e:
         sm.scatman_sync(h)
     assert e.value.code == -4                       # ERR_TIMEOUT
+    sm.scatman_debug_stall(h, False)
     sm.scatman_set_wait_limit(h, 0.0)               # the default limit again
     sm.scatman_forward(h, I)
     sm.scatman_sync(h)
@@ -74,10 +78,12 @@ def test_backward_wait_timeout_is_reported_and_the_handle_recovers():
     sm.scatman_sync(h)
     w = torch.ones_like(I)
     ref = sm.scatman_backward(h, w)
-    sm.scatman_set_wait_limit(h, 1e-9)
+    sm.scatman_set_wait_limit(h, 0.01)
+    sm.scatman_debug_stall(h, True)
     with pytest.raises(sm.ScatmanError) as e:
         sm.scatman_backward(h, w)
     assert e.value.code == -4
+    sm.scatman_debug_stall(h, False)
     sm.scatman_set_wait_limit(h, -1.0)
     again = sm.scatman_backward(h, w)
     assert np.array_equal(again, ref)               # fixed reduction orders: bit for bit
