@@ -319,8 +319,8 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
         h->Kp = h->Nyp;                       // K extent of one slice-operand row
         if (h->Nxp > 128)
             return fail(set_error(h, SCATMAN_ERR_ARG, "tensor-core modes support nx <= 128"));
-        if (tc_ring_bytes(h->Nyp, h->Nxp, h->split) == 0)
-            return fail(set_error(h, SCATMAN_ERR_ARG, "ny too large for the tensor-core phase tile"));
+        if (!tc_grid_ok(h->Nxp, h->Nyp, h->split))
+            return fail(set_error(h, SCATMAN_ERR_ARG, "ny too large for the tensor-core phase operand"));
         h->b_rows = (size_t)c.nz * 3 * h->Nxp;   // planes -Im, Re, Im of every slice
     }
 
@@ -340,7 +340,7 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     if ((rc = alloc_dev(h, (void **)&h->d_chi, nvox * sizeof(float), "occupancy buffer"))) return fail(rc);
     // per-slice occupied boxes (every mode skips the empty parts of each
     // slice), then the tensor-core kernel's occupied-slice list
-    if ((rc = alloc_dev(h, (void **)&h->d_bounds, (6 * (size_t)c.nz + 2) * sizeof(int), "slice bounds")))
+    if ((rc = alloc_dev(h, (void **)&h->d_bounds, slice_geom_ints(c.nz) * sizeof(int), "slice geometry")))
         return fail(rc);
     if (h->tensor_core) {
         h->s_bytes = h->b_rows * (size_t)h->Kp * 2;
@@ -619,6 +619,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     so.s = h->d_s;
     so.chi = h->d_chi;
     so.bounds = h->d_bounds;
+    so.chunk_y = h->tensor_core ? geom_chunk_y(h->d_bounds, c.nz) : nullptr;
     double strength = std::fmax(std::fabs(s->delta), std::fabs(s->beta));
     if (sp.varn) strength = std::fmax(strength, h->map_index_max);
     h->scan_fp64 = c.scan_fp64 || (h->k0 * c.voxel * c.nz * strength > 5.0);
@@ -651,8 +652,7 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
         if (e == cudaSuccess) {
             const UqStore store{(uint16_t *)h->d_H, h->uq_Jp, h->uq_Rg, h->uq_Kx, h->bf16};
             e = launch_uq_y_tc_mma(h->tmap_B, h->d_uq_qrow, c.det_ny, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, c.voxel,
-                                   h->split, h->s_bf16, h->d_bounds, (uint2 *)(h->d_bounds + 4 * c.nz), store,
-                                   h->d_err, h->sm_count, h->stream);
+                                   h->split, h->s_bf16, h->d_bounds, store, h->d_err, h->sm_count, h->stream);
         }
         if (e == cudaSuccess)
             e = launch_uq_tc(h->tmap_H, h->d_uq_qz, c.nx, c.nz, c.det_nx, c.det_ny, c.theta_max_deg, h->k0, c.voxel,
@@ -664,7 +664,7 @@ int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
                                 h->stream);
     } else if (h->tensor_core) {
         e = launch_msft_tc(h->tmap_B, h->d_q, h->n_pix, c.nx, c.ny, c.nz, h->Nxp, h->Nyp, c.voxel, str_re,
-                           str_im, h->split, h->bf16, h->d_bounds, (uint2 *)(h->d_bounds + 4 * c.nz), (float2 *)h->d_A,
+                           str_im, h->split, h->bf16, h->d_bounds, (float2 *)h->d_A,
                            (float *)I_dev, h->d_err, h->sm_count, h->stream, h->d_tail);
     } else {
         e = launch_msft_simt(h->precision == SCATMAN_FP64, h->d_s, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
@@ -841,10 +841,10 @@ int scatman_contraction_flops(scatman_handle *h, double *issued, double *dense) 
         *issued = uq_tc_issued_flops(c.nx, c.nz, c.det_nx, c.det_ny, h->split);
         return SCATMAN_OK;
     }
-    std::vector<int> b(4 * (size_t)c.nz);
+    std::vector<int> b((4 + 2 * (size_t)kGeomChunks) * c.nz);
     int rc = check_cuda(h, cudaMemcpyAsync(b.data(), h->d_bounds, b.size() * sizeof(int), cudaMemcpyDeviceToHost,
                                            h->stream),
-                        "bounds download");
+                        "slice geometry download");
     if (rc) return rc;
     if ((rc = scatman_sync(h))) return rc;
     if (!h->tensor_core) {
@@ -1117,6 +1117,7 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
     so.s = d_s;
     so.chi = d_chi;
     so.bounds = nullptr;
+    so.chunk_y = nullptr;
     const double strength = std::fmax(std::fabs(s->delta), std::fabs(s->beta));
     const bool scan_fp64 = c.scan_fp64 || (k0 * c.voxel * c.nz * strength > 5.0);
     e = launch_voxelise(sp, gp, so, scan_fp64, false, st);

@@ -119,12 +119,28 @@ inline GridParams make_grid(int nx, int ny, int nz, double voxel, double k0, dou
 // Where the voxeliser writes s = chi*T.
 enum SliceLayout { kLayoutC64 = 0, kLayoutC32 = 1, kLayoutTcF16 = 2, kLayoutTcBF16 = 3 };
 
-// Tensor maps of the tensor-core slice operand, one per span width of 16k
-// rows (k = 1 .. kTcMaxChunks).
-constexpr int kTcMaxChunks = 8;
+// Tensor maps of the tensor-core slice operand, one per span width of 8k
+// rows (k = 1 .. kTcMaxChunks): a box of 64 y x 8k rows x the three planes.
+constexpr int kTcMaxChunks = 16;
 struct TcMaps {
     CUtensorMap m[kTcMaxChunks];
 };
+
+// Per-slice geometry the voxeliser records for the contractions, in one
+// device buffer of slice_geom_ints(nz) ints:
+//   [0, 4 nz)            occupied box of every slice [x_lo | x_hi | y_lo | y_hi]
+//   [4 nz, 36 nz)        occupied y range of every 8-column chunk of every slice,
+//                        [y_lo | y_hi] x [nz][kGeomChunks] (tensor-core grids, nx <= 128)
+//   then                 the tensor-core kernel's work-unit list (uint2, kMaxUnitsPerSlice nz + 1)
+constexpr int kGeomChunks = 16;
+constexpr int kMaxUnitsPerSlice = 4;
+inline size_t slice_geom_ints(int nz) {
+    return 4 * (size_t)nz + 2 * (size_t)kGeomChunks * nz + 2 * ((size_t)kMaxUnitsPerSlice * nz + 1);
+}
+inline int *geom_chunk_y(int *g, int nz) { return g + 4 * (size_t)nz; }
+inline uint2 *geom_units(int *g, int nz) {
+    return reinterpret_cast<uint2 *>(g + 4 * (size_t)nz + 2 * (size_t)kGeomChunks * nz);
+}
 
 struct SliceOut {
     int layout;
@@ -132,6 +148,7 @@ struct SliceOut {
     void *s;                        // C64: double2[nvox]; C32: float2[nvox]; TC: 16-bit [nz*3*Nxp][Kp]
     float *chi;                     // occupancy [z][x][y]
     int *bounds;                    // per slice [x_lo | x_hi | y_lo | y_hi] of chi != 0 (nz each), or null
+    int *chunk_y;                   // per slice and 8-column chunk [y_lo | y_hi] (see above), or null
 };
 
 }  // namespace scm
@@ -251,13 +268,15 @@ cudaError_t launch_msft_simt(bool fp64, const void *s, const double *q, long lon
                              void *partial, int splits, cudaStream_t st, const int *bounds);
 // Real flops the CUDA-core contraction executes with box skipping (host copy of the bounds).
 double simt_issued_flops(const int *bounds, int nz, int ny, long long n_pix, bool fp64);
-// Tensor-core contraction (msft_tc.cu).
-size_t tc_ring_bytes(int Nyp, int Nxp, bool split);
-// tail_part: scratch of tc_tail_part_bytes for the partial fields of the last
-// partial wave's tiles (null: every tile whole).
+// Tensor-core contraction (msft_tc.cu).  Whether a padded grid fits its
+// tensor-memory layout (phase operand and two accumulators) and unit masks.
+bool tc_grid_ok(int Nxp, int Nyp, bool split);
+// geom: the slice-geometry buffer (slice_geom_ints); tail_part: scratch of
+// tc_tail_part_bytes for the partial fields of the last partial wave's tiles
+// (null: every tile whole).
 cudaError_t launch_msft_tc(const TcMaps &maps, const double *q, long long n_pix, int nx, int ny, int nz,
                            int Nxp, int Nyp, double voxel, double str_re, double str_im, bool split,
-                           bool bf16, const int *bounds, uint2 *list, float2 *A, float *I, int *err,
+                           bool bf16, int *geom, float2 *A, float *I, int *err,
                            int sm_count, cudaStream_t st, float2 *tail_part);
 size_t tc_tail_part_bytes(long long n_pix, int sm_count);
 // The same kernel in store mode, the uniform-q detector's y-contraction on the
@@ -269,10 +288,11 @@ struct UqStore {
     bool bf16;                  // H's 16-bit type
 };
 cudaError_t launch_uq_y_tc_mma(const TcMaps &maps, const double *qrow, int det_ny, int nx, int ny, int nz, int Nxp,
-                               int Nyp, double voxel, bool split, bool bf16, const int *bounds, uint2 *list,
+                               int Nyp, double voxel, bool split, bool bf16, int *geom,
                                const UqStore &store, int *err, int sm_count, cudaStream_t st);
-// Real flops one contraction launch issues for the given per-slice boxes.
-double tc_issued_flops(const int *bounds_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
+// Real flops one contraction launch issues for the recorded slice geometry
+// (a host copy of the first 4 nz + 2 kGeomChunks nz ints of the buffer).
+double tc_issued_flops(const int *geom_host, int nz, int Nxp, int Nyp, long long n_pix, bool split);
 bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why);
 // A 3D tiled tensor map over 16-bit elements with a 32-, 64- or 128-byte
 // swizzle (dims innermost first; strides of dims 1 and 2 in bytes; the box's

@@ -335,7 +335,7 @@ long long scatman_footprint_bytes(const scatman_config *c) {
     }
     long long b = 0;
     b += round_2mib(npix * 24);                 // q
-    b += round_2mib(24LL * c->nz + 8);          // slice bounds and occupied-slice list
+    b += round_2mib(4LL * (long long)scm::slice_geom_ints(c->nz));   // slice geometry and the unit list
     b += round_2mib(nvox * 4);                  // occupancy
     b += round_2mib(s_bytes);                   // slices
     b += round_2mib(npix * cx);                 // field cache

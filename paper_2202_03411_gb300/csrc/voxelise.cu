@@ -243,6 +243,12 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
                 atomicMax(&out.bounds[nz + iz], ix + 1);
                 atomicMin(&out.bounds[2 * nz + iz], y0 + lo);
                 atomicMax(&out.bounds[3 * nz + iz], y0 + hi + 1);
+                if (out.chunk_y) {
+                    // y range of this slice's 8-column chunk (tensor-core grids: ix < 8 kGeomChunks)
+                    const int c = iz * kGeomChunks + (ix >> 3);
+                    atomicMin(&out.chunk_y[c], y0 + lo);
+                    atomicMax(&out.chunk_y[kGeomChunks * nz + c], y0 + hi + 1);
+                }
             }
         }
     }
@@ -280,18 +286,21 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
     }
 }
 
-__global__ void bounds_init_kernel(int *b, int nz) {
+__global__ void bounds_init_kernel(int *b, int nz, int *cy) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 4 * nz) {
         const int part = i / nz;
         b[i] = (part == 0 || part == 2) ? 0x7fffffff : 0;     // lo parts start high, hi parts low
     }
+    if (cy && i < 2 * kGeomChunks * nz) cy[i] = i < kGeomChunks * nz ? 0x7fffffff : 0;
 }
 
 cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const SliceOut &out, bool scan_fp64,
                             bool fp64_mode, cudaStream_t st) {
     if (gp.nz > 32 * kMaxRun) return cudaErrorInvalidValue;
-    if (out.bounds) bounds_init_kernel<<<(4 * gp.nz + 255) / 256, 256, 0, st>>>(out.bounds, gp.nz);
+    if (out.chunk_y && (out.bounds == nullptr || gp.nx > 8 * kGeomChunks)) return cudaErrorInvalidValue;
+    if (out.bounds)
+        bounds_init_kernel<<<(2 * kGeomChunks * gp.nz + 255) / 256, 256, 0, st>>>(out.bounds, gp.nz, out.chunk_y);
     dim3 grid(gp.nx, (gp.ny + kLinesPerCta - 1) / kLinesPerCta);
     size_t cx = fp64_mode ? sizeof(double2) : sizeof(float2);
     size_t smem = (cx + sizeof(float)) * (size_t)(gp.nz + 1) * kLinesPerCta + kVoxQueue * sizeof(int);
