@@ -10,18 +10,18 @@
 //   Sr[x, y] = Re s_j(x, y), Si[x, y] = Im s_j(x, y).
 // The slice operand is stored as three planes [-Si | Sr | Si], so both B
 // operands are windows of one staged block.  The phase operand [Pr | Pi] of a
-// pixel tile lives in tensor memory (row m in lane m), built once per tile by
-// the epilogue warps with tcgen05.st; with split phases it is held as an
-// FP16/BF16 pair P = P_hi + P_lo and both halves accumulate into the same FP32
-// result.  Reading A from tensor memory takes its 4 KB per MMA off the shared
-// memory port, which otherwise adds about 30 cycles to every MMA.
+// pixel tile is built once per tile by the epilogue warps in shared memory
+// (K-major, 128-byte swizzle); with split phases it is held as an FP16/BF16
+// pair P = P_hi + P_lo and both halves accumulate into the same FP32 result.
 //
-// Work units.  Each occupied slice is cut into units of contiguous 8-column
-// chunks of x, at most `max_chunks` per unit (the two accumulator buffers and
-// the phase operand share the 512 tensor-memory columns); a unit runs only
-// the K steps its own chunks' y range needs, and may shift its K steps by
-// 8 y when that saves one (the B box then starts 8 y later and the epilogue
-// multiplies the unit's sum by e^{-i q_y 8 dy}).  Each stage of the shared
+// Work units.  A unit is one occupied slice's run of occupied 8-column chunks
+// of x (up to the full 128): its MMAs have N = 16 nch, and it runs only the K
+// steps its y range needs, shifted by 8 y when that saves one (the B box then
+// starts 8 y later and the epilogue multiplies the unit's sum by
+// e^{-i q_y 8 dy}).  Whole slices keep each unit's MMA work long enough to
+// hide the hand-offs between the warp roles (holding a phase half in tensor
+// memory makes each MMA cheaper but forces units of at most 96 x into the
+// remaining columns, and then those hand-offs show).  Each stage of the shared
 // memory ring is one 3D TMA box (64 y x 8 nch rows x 3 planes, 128-byte
 // swizzle), as large as the unit.  Accumulators are double buffered, and
 // eight epilogue warps apply the x- and z-phases (second line) while the next
@@ -61,6 +61,7 @@ constexpr int kMaxSmem = 232448;           // 227 KB opt-in per block
 constexpr int kTcMaxTailParts = 4;         // unit ranges per tile of the last partial wave
 constexpr int kTmemCols = 512;             // the whole tensor memory of the SM
 constexpr int kUnitMaxSteps = 21;          // K steps a unit word can hold
+constexpr int kEpiBatch = 3;               // chunks whose tensor-memory loads share one wait
 
 struct TcParams {
     const double *q;
@@ -68,7 +69,7 @@ struct TcParams {
     long long n_pix;
     int nx, ny, nz;
     int Nxp, Nyp;               // padded x (multiple of 16) and y (multiple of 16)
-    int nkb_b;                  // 64-element K blocks of a slice row (Nyp)
+    int nkb_a, nkb_b;           // 64-element K blocks of the phase operand (2 Nyp) and of a slice row (Nyp)
     uint32_t ring_bytes;        // slice-stage ring (multiple of 1024)
     int split, bf16;
     int num_m_tiles;
@@ -81,7 +82,6 @@ struct TcParams {
     float2 *Apart;              // [part][(tile - whole) * 128 + m]
     uint32_t idesc;             // without the N field (set per unit)
     uint32_t acc_cols;          // tensor-memory columns of one accumulator buffer
-    uint32_t a_col;             // first tensor-memory column of the phase operand
     double voxel;
     float str_re, str_im;
     float2 *A;
@@ -101,19 +101,27 @@ __host__ __device__ inline int unit_nch(uint32_t w) { return (int)((w >> 5) & 31
 __host__ __device__ inline int unit_shift(uint32_t w) { return (int)((w >> 10) & 1u); }
 __host__ __device__ inline uint32_t unit_kmask(uint32_t w) { return w >> 11; }
 
-// Tensor-memory layout of a grid: the phase operand takes (split ? 2 : 1) Nyp
-// columns ([Pr | Pi], Nyp / 2 columns each, two 16-bit values per column);
-// the rest holds two accumulator buffers of 16 max_chunks columns (a unit of
-// nch chunks fills 16 nch of them: [Re G | Im G]).
-__host__ __device__ inline int tc_a_cols(int Nyp, bool split) { return (split ? 2 : 1) * Nyp; }
-__host__ __device__ inline int tc_max_chunks(int Nyp, bool split) {
-    const int m = (kTmemCols - tc_a_cols(Nyp, split)) / 32;
-    return m > kTcMaxChunks ? kTcMaxChunks : m;
+// Tensor memory holds two accumulator buffers of 256 columns (a unit of nch
+// chunks fills 16 nch of them: [Re G | Im G]).  Shared memory: the phase
+// operand (and its low half), the stage ring, the reduction buffer and the
+// barriers.
+constexpr int kAccCols = 16 * kTcMaxChunks;
+static int tc_nkb(int K) { return (K + kBK - 1) / kBK; }
+static size_t tc_fixed_bytes() { return 1024 /*align*/ + kBM * sizeof(float2) + 512 /*barriers*/; }
+static size_t tc_a_bytes(int Nyp) { return (size_t)tc_nkb(2 * Nyp) * kBM * 128; }
+// Bytes of the slice-stage ring beside the phase operand(s), or 0 when two
+// stages as wide as the grid do not fit.
+static size_t tc_ring_bytes(int Nxp, int Nyp, bool split) {
+    const size_t used = tc_fixed_bytes() + (split ? 2 : 1) * tc_a_bytes(Nyp);
+    if (used >= (size_t)kMaxSmem) return 0;
+    const size_t r = ((size_t)kMaxSmem - used) / 1024 * 1024;
+    const size_t widest = (size_t)kPlanes * Nxp * 128;
+    return r >= 2 * widest ? r : 0;
 }
 
 bool tc_grid_ok(int Nxp, int Nyp, bool split) {
     return Nxp >= 16 && Nxp % 16 == 0 && Nxp <= 8 * kGeomChunks && Nyp >= 16 && Nyp % 16 == 0 &&
-           Nyp / 16 <= kUnitMaxSteps && tc_max_chunks(Nyp, split) >= 4;
+           Nyp / 16 <= kUnitMaxSteps && tc_ring_bytes(Nxp, Nyp, split) > 0;
 }
 
 // The work units of slice t from the recorded y range of each of its 8-column
@@ -217,24 +225,21 @@ __device__ __forceinline__ uint32_t ring_start(uint32_t head_off, uint32_t sz, u
     return head_off + sz > ring ? 0u : head_off;
 }
 
-// Phase operand P[m, y] of one pixel tile (and its low part when split) in
-// tensor memory: [Pr_hi | Pi_hi | Pr_lo | Pi_lo] from column a_col, Nyp / 2
-// columns each, y = 2j and 2j + 1 packed in column j.  Called by the
-// kEpiThreads epilogue threads; thread `tid` serves row m = tid % 128, which
-// is its warp's lane quarter (lane_base).  Each group of 8 consecutive y takes
-// one reduced sincos and FP32 complex products with the rotations
-// e^{-i q_y k dy}, k = 1..4 (a few ulp, far below the 16-bit operands'
-// resolution).  Returns after this thread's stores have landed.
-__device__ __forceinline__ void build_phase_tmem(const TcParams &P, double qy, bool valid, uint32_t lane_base,
-                                                 int tid) {
+// Phase operand P[m, k] of one pixel tile (and its low part when split),
+// K-major with the 128-byte swizzle: [Pr | Pi] over k = y and Nyp + y.
+// Built by the kEpiThreads epilogue threads; thread `tid` always serves pixel
+// row m = tid % 128; each group of 8 consecutive y takes one reduced sincos
+// and FP32 complex products with the rotations e^{-i q_y k dy}, k = 1..4 (a
+// few ulp, far below the 16-bit operands' resolution).
+__device__ __forceinline__ void build_phase(const TcParams &P, double qy, bool valid, uint8_t *sA_hi,
+                                           uint8_t *sA_lo, int tid) {
+    const int m = tid % kBM;
     const int ny8 = P.Nyp >> 3;
-    const uint32_t hc = (uint32_t)P.Nyp >> 1;
     const float qh = (float)qy, ql = (float)(qy - (double)qh);
     const float yoff = 0.5f * (float)(P.ny - 1), vox = (float)P.voxel;
     // rotations by 1..3 and 4 voxels: each group of 8 phases is two levels deep
     const float2 s1 = expmi_fs(qh, ql, vox);
     const float2 s2 = cmul(s1, s1), s3 = cmul(s2, s1), s4 = cmul(s2, s2);
-    const uint32_t base = lane_base + P.a_col;
 #pragma unroll 2
     for (int y8 = tid / kBM; y8 < ny8; y8 += kEpiThreads / kBM) {
         const float2 p0 = expmi_fs(qh, ql, ((float)(8 * y8) - yoff) * vox);
@@ -249,22 +254,25 @@ __device__ __forceinline__ void build_phase_tmem(const TcParams &P, double qy, b
             split_pair(in0 ? phs[e].x : 0.f, in1 ? phs[e + 1].x : 0.f, P.bf16, &re_hi[e >> 1], &re_lo[e >> 1]);
             split_pair(in0 ? phs[e].y : 0.f, in1 ? phs[e + 1].y : 0.f, P.bf16, &im_hi[e >> 1], &im_lo[e >> 1]);
         }
-        const uint32_t col = base + 4u * (uint32_t)y8;
-        tmem_st4(col, re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
-        tmem_st4(col + hc, im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
+        const uint32_t o_re = a_chunk_offset(m, 8 * y8);
+        const uint32_t o_im = a_chunk_offset(m, P.Nyp + 8 * y8);
+        *reinterpret_cast<uint4 *>(sA_hi + o_re) = make_uint4(re_hi[0], re_hi[1], re_hi[2], re_hi[3]);
+        *reinterpret_cast<uint4 *>(sA_hi + o_im) = make_uint4(im_hi[0], im_hi[1], im_hi[2], im_hi[3]);
         if (P.split) {
-            tmem_st4(col + 2 * hc, re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
-            tmem_st4(col + 3 * hc, im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
+            *reinterpret_cast<uint4 *>(sA_lo + o_re) = make_uint4(re_lo[0], re_lo[1], re_lo[2], re_lo[3]);
+            *reinterpret_cast<uint4 *>(sA_lo + o_im) = make_uint4(im_lo[0], im_lo[1], im_lo[2], im_lo[3]);
         }
     }
-    tmem_st_wait();
 }
 
 template <bool kStoreH>
 __global__ void __launch_bounds__(kTcThreads, 1)
     msft_tc_kernel(const __grid_constant__ TcMaps maps, const TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *ring = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA_hi = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t a_bytes = (uint32_t)P.nkb_a * (uint32_t)(kBM * 128);
+    uint8_t *sA_lo = sA_hi + a_bytes;
+    uint8_t *ring = sA_hi + (P.split ? 2u : 1u) * a_bytes;
     const uint32_t R = P.ring_bytes;
     float2 *red = reinterpret_cast<float2 *>(ring + R);
     uint64_t *bars = reinterpret_cast<uint64_t *>(red + kBM);
@@ -363,8 +371,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t mine = (uint32_t)(warp - kMmaWarp);
         bool ok = true;
         const uint64_t ring0 = sw128_desc(smem_u32(ring));
-        const uint32_t hc = (uint32_t)P.Nyp >> 1;
-        const uint32_t a_base = tmem_base + P.a_col;
+        const uint64_t ahi0 = sw128_desc(smem_u32(sA_hi)), alo0 = sw128_desc(smem_u32(sA_lo));
         uint32_t head_off = 0;
         uint32_t tl = 0;
         const int n_list = (int)__ldg(&P.list[0].x);
@@ -416,15 +423,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         if (!((kbits >> kk) & 1u)) continue;
-                        const uint32_t ar = a_base + 8u * (uint32_t)(4 * kb + kk);   // Pr_hi of this K step
+                        const int k = 4 * kb + kk;          // the phase operand's K step (y = 16 k)
+                        const uint64_t off_r = a_k_offset(16 * k) >> 4, off_i = a_k_offset(P.Nyp + 16 * k) >> 4;
                         const uint64_t b1 = w1 + (uint64_t)(kk * 2), b2 = w2 + (uint64_t)(kk * 2);
                         const uint32_t acc0 = first ? 0u : 1u;
                         if (elect_one()) {
-                            mma_f16_ts(d, ar, b1, idesc, acc0);
-                            mma_f16_ts(d, ar + hc, b2, idesc, 1u);
+                            mma_f16(d, ahi0 + off_r, b1, idesc, acc0);
+                            mma_f16(d, ahi0 + off_i, b2, idesc, 1u);
                             if (P.split) {
-                                mma_f16_ts(d, ar + 2 * hc, b1, idesc, 1u);
-                                mma_f16_ts(d, ar + 3 * hc, b2, idesc, 1u);
+                                mma_f16(d, alo0 + off_r, b1, idesc, 1u);
+                                mma_f16(d, alo0 + off_i, b2, idesc, 1u);
                             }
                         }
                         __syncwarp();
@@ -454,7 +462,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const long long v = (long long)un.mt * kBM + m;
             const bool valid = v < P.n_pix;
             const double qy = valid ? P.q[3 * v + 1] : 0.0;
-            if (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0) build_phase_tmem(P, qy, valid, lane_base, threadIdx.x);
+            if (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0)
+                build_phase(P, qy, valid, sA_hi, sA_lo, threadIdx.x);
+            fence_async_smem();
             tc_fence_before();
             mbar_arrive(smem_u32(a_full));
             const long long g = valid ? v / P.h_Rg : 0, r = valid ? v % P.h_Rg : 0;
@@ -532,7 +542,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             // The tensor core is done with the previous tile's phase operand:
             // this thread has seen the completion of its last unit.
-            if (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0) build_phase_tmem(P, qy, valid, lane_base, threadIdx.x);
+            if (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0)
+                build_phase(P, qy, valid, sA_hi, sA_lo, threadIdx.x);
+            fence_async_smem();
             tc_fence_before();
             mbar_arrive(smem_u32(a_full));
 
@@ -546,9 +558,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             float2 W[8];                                  // e^{-i q_x k dx}, k < 8
 #pragma unroll
             for (int k = 0; k < 8; ++k) W[k] = expmi_fs(qxh, qxl, (float)k * vf);
-            float2 E[kGeomChunks];                        // e^{-i q_x x0} of each 8-column chunk
-#pragma unroll
-            for (int c = 0; c < kGeomChunks; ++c) E[c] = expmi_fs(qxh, qxl, ((float)(8 * c) - xoff) * vf);
+            const float2 X16 = expmi_fs(qxh, qxl, 16.f * vf);   // from one chunk of a half to its next
             const float2 Ysh = expmi_fs(qyh, qyl, 8.f * vf);    // a unit's K steps shifted by 8 y
             const float2 Zstep = expmi_fs(qzh, qzl, vf);
             float2 Z = make_float2(1.f, 0.f);
@@ -576,25 +586,42 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 tc_fence_after();
                 const uint32_t nr = 8u * (uint32_t)(c_hi - c_lo);
                 float2 acct = make_float2(0.f, 0.f);
+                // this half's chunks: c_first, c_first + 2, ... (nh of them), read
+                // kEpiBatch at a time with one wait; the x anchor of each is the
+                // previous one's times e^{-i q_x 16 dx}
+                const int c_first = c_lo + ((c_lo & 1) != half);
+                const int nh = c_first < c_hi ? (c_hi - c_first + 1) >> 1 : 0;
+                if (nh > 0) {
+                    float2 Ec = expmi_fs(qxh, qxl, ((float)(8 * c_first) - xoff) * vf);
+                    const uint32_t col0 = b * P.acc_cols + 8u * (uint32_t)(c_first - c_lo);
+                    for (int j0 = 0; j0 < nh; j0 += kEpiBatch) {
+                        float gr[kEpiBatch][8], gi[kEpiBatch][8];
 #pragma unroll
-                for (int c = 0; c < kGeomChunks; ++c) {
-                    // chunks alternate between the two halves
-                    if (c >= c_lo && c < c_hi && (c & 1) == half) {
-                        const uint32_t col = b * P.acc_cols + 8u * (uint32_t)(c - c_lo);
-                        float gr[8], gi[8];
-                        tmem_ld8(lane_base + col, gr);
-                        tmem_ld8(lane_base + col + nr, gi);
-                        tmem_ld_wait8(gr, gi);
-                        float hr = 0.f, hi = 0.f;
+                        for (int q = 0; q < kEpiBatch; ++q)
+                            if (j0 + q < nh) {
+                                const uint32_t col = col0 + 16u * (uint32_t)(j0 + q);
+                                tmem_ld8(lane_base + col, gr[q]);
+                                tmem_ld8(lane_base + col + nr, gi[q]);
+                            }
+                        tmem_ld_wait8(gr[0], gi[0]);
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            hr = fmaf(W[k].x, gr[k], hr);
-                            hr = fmaf(-W[k].y, gi[k], hr);
-                            hi = fmaf(W[k].x, gi[k], hi);
-                            hi = fmaf(W[k].y, gr[k], hi);
+                        for (int q = 1; q < kEpiBatch; ++q) tmem_ld_after_wait8(gr[q], gi[q]);
+#pragma unroll
+                        for (int q = 0; q < kEpiBatch; ++q) {
+                            if (j0 + q < nh) {
+                                float hr = 0.f, hi = 0.f;
+#pragma unroll
+                                for (int k = 0; k < 8; ++k) {
+                                    hr = fmaf(W[k].x, gr[q][k], hr);
+                                    hr = fmaf(-W[k].y, gi[q][k], hr);
+                                    hi = fmaf(W[k].x, gi[q][k], hi);
+                                    hi = fmaf(W[k].y, gr[q][k], hi);
+                                }
+                                acct.x = fmaf(Ec.x, hr, fmaf(-Ec.y, hi, acct.x));
+                                acct.y = fmaf(Ec.x, hi, fmaf(Ec.y, hr, acct.y));
+                                Ec = cmul(Ec, X16);
+                            }
                         }
-                        acct.x = fmaf(E[c].x, hr, fmaf(-E[c].y, hi, acct.x));
-                        acct.y = fmaf(E[c].x, hi, fmaf(E[c].y, hr, acct.y));
                     }
                 }
                 tc_fence_before();
@@ -663,22 +690,10 @@ __global__ void tc_tail_sum_kernel(const float2 *__restrict__ Apart, int parts, 
 }
 
 // ---- host side ------------------------------------------------------------------
-static size_t tc_fixed_bytes() { return 1024 /*align*/ + kBM * sizeof(float2) + 512 /*barriers*/; }
-
-static int tc_nkb(int K) { return (K + kBK - 1) / kBK; }
-
-// Bytes of the slice-stage ring: all shared memory but the reduction buffer
-// and the barriers (the phase operand is in tensor memory).  Always holds at
-// least two stages of the widest unit.
-static size_t tc_ring_bytes(int Nyp, bool split) {
-    const size_t r = ((size_t)kMaxSmem - tc_fixed_bytes()) / 1024 * 1024;
-    const size_t widest = (size_t)kPlanes * 8 * tc_max_chunks(Nyp, split) * 128;
-    return r >= 2 * widest ? r : 0;
-}
 
 double tc_issued_flops(const int *geom, int nz, int Nxp, int Nyp, long long n_pix, bool split) {
     const long long m_tiles = (n_pix + kBM - 1) / kBM;
-    const int mc = tc_max_chunks(Nyp, split);
+    const int mc = kTcMaxChunks;
     double per_tile = 0.0;
     for (int t = 0; t < nz; ++t) {
         uint32_t w[kMaxUnitsPerSlice];
@@ -715,9 +730,9 @@ static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pi
                              float2 *A, float *I, int *err, int sm_count, cudaStream_t st, const UqStore *store,
                              float2 *tail_part) {
     if (!tc_grid_ok(Nxp, Nyp, split) || nz < 1 || nz > 256 || nx > Nxp || ny > Nyp) return cudaErrorInvalidValue;
-    const size_t ring = tc_ring_bytes(Nyp, split);
+    const size_t ring = tc_ring_bytes(Nxp, Nyp, split);
     if (ring == 0) return cudaErrorInvalidValue;
-    const int max_chunks = tc_max_chunks(Nyp, split);
+    const int max_chunks = kTcMaxChunks;
     uint2 *list = geom_units(geom, nz);
     TcParams P;
     P.q = q;
@@ -728,6 +743,7 @@ static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pi
     P.nz = nz;
     P.Nxp = Nxp;
     P.Nyp = Nyp;
+    P.nkb_a = tc_nkb(2 * Nyp);
     P.nkb_b = tc_nkb(Nyp);
     P.ring_bytes = (uint32_t)ring;
     P.split = split ? 1 : 0;
@@ -758,8 +774,7 @@ static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pi
     P.num_units = P.whole + (P.num_m_tiles - P.whole) * P.parts;
     const uint32_t M = kBM;
     P.idesc = (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((M >> 4) << 24);
-    P.acc_cols = 16u * (uint32_t)max_chunks;
-    P.a_col = 2u * P.acc_cols;
+    P.acc_cols = (uint32_t)kAccCols;
     P.voxel = voxel;
     P.str_re = (float)str_re;
     P.str_im = (float)str_im;
@@ -773,7 +788,7 @@ static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pi
     P.h_Kx = store ? store->Kx : 0;
     P.h_bf16 = store && store->bf16 ? 1 : 0;
     if (store && (store->Kx < Nxp || store->Kx % 8 != 0 || store->Jp < nz)) return cudaErrorInvalidValue;
-    const size_t smem = ring + tc_fixed_bytes();
+    const size_t smem = (split ? 2 : 1) * tc_a_bytes(Nyp) + ring + tc_fixed_bytes();
     // The attribute is per function and shared by every thread of the process:
     // always raise it to the largest size any launch uses, never to this
     // launch's size, so concurrent launches from other threads stay valid.

@@ -173,6 +173,16 @@ __device__ __forceinline__ void tmem_ld_wait8(float (&a)[8], float (&b)[8]) {
                  :
                  : "memory");
 }
+// No instruction: ties two more 8-register load destinations to a preceding
+// tcgen05.wait::ld so the compiler reads them only after that wait.
+__device__ __forceinline__ void tmem_ld_after_wait8(float (&a)[8], float (&b)[8]) {
+    asm volatile(""
+                 : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(a[4]), "+f"(a[5]), "+f"(a[6]),
+                   "+f"(a[7]), "+f"(b[0]), "+f"(b[1]), "+f"(b[2]), "+f"(b[3]), "+f"(b[4]), "+f"(b[5]),
+                   "+f"(b[6]), "+f"(b[7])
+                 :
+                 : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
