@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--serving-slots", type=int, default=4)
     ap.add_argument("--fit-step", type=int, default=0,
                     help="time this many forward+gradient fit steps of the 96^3 l<=6 workload and print a JSON line")
-    ap.add_argument("--short-serving", type=int, default=240,
-                    help="requests of the short serving run folded into the default line (0: skip)")
+    ap.add_argument("--short-serving", type=int, default=2000,
+                    help="requests of the serving study folded into the default line (0: skip)")
     ap.add_argument("--fig8b-case", type=float, nargs=2, metavar=("RADIUS_LAMBDA", "DETECTOR"),
                     help="time one Fig. 8b case (uniform-q detector) in --precision and print a JSON line; "
                          "for profiler runs")
@@ -83,39 +83,97 @@ def serving_targets(reqs, precision):
     return res
 
 
-def serving_run(n_requests, slots, precision, fractions=(0.5, 0.8, 0.95), seed=0):
+def _stream_stats(lat, status, wall, n):
+    import numpy as np
+    return {"requests_per_s": n / wall, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)), "failed": int(sum(1 for x in status if x)),
+            "wall_s": wall}
+
+
+def serving_oracle_check(srv, reqs, targets, picks, n_sample=512, width=0.5):
+    """A few requests served again with their intensity returned; each is
+    compared with the FP64 oracle (soft occupancy of the server's width) on a
+    pixel sample.  Returns the relative L2 errors."""
+    import numpy as np
+
+    import oracle
+    out = []
+    for i in picks:
+        r = reqs[i]
+        t, res = srv.submit(r.geometry, r.shape, targets[i], want_gradient=True, want_I=True)
+        st, _ = srv.wait(t, timeout_s=120.0)
+        g = r.geometry
+        sample = np.sort(np.random.default_rng(i).choice(g.n_pix, size=min(n_sample, g.n_pix), replace=False))
+        chi, _ = oracle.voxelise(r.shape, g, True, width)
+        rho = oracle.slices(chi, g, r.shape.delta, r.shape.beta)
+        Iref = np.abs(oracle.msft(rho, oracle.detector_q(g)[sample], g.voxel)) ** 2
+        out.append({"request": int(i), "grid": g.nx, "detector": g.det_nx, "kind": int(r.shape.kind),
+                    "status": int(st), "rel_l2_I": oracle.relative_l2(res["I"][sample].astype(np.float64), Iref),
+                    "sample_pixels": int(len(sample))})
+    return out
+
+
+def serving_run(n_requests, slots, precision, fractions=(0.5, 0.8, 0.95), seed=0, oracle_picks=3):
     """Serving mix: forward + gradient fit requests over grids {48,64,96,128}^3 and
-    detectors {128,256,512}^2, admitted under a 120 GB budget.  First all
-    requests arrive at once (saturation throughput), then Poisson streams at
-    the given fractions of it.  Latency is submit-to-result."""
+    detectors {128,256,512}^2, admitted under a 120 GB budget.  Runs, each on
+    the same request stream:
+      cold        a fresh server, every request arriving at once (handles are
+                  created as requests need them, device allocations included);
+      saturation  a warmed server (one handle per geometry created first), all
+                  requests at once: the saturation throughput;
+      poisson     Poisson arrivals at the given fractions of that throughput;
+      one_slot    a warmed single-slot server at saturation (no overlap on the
+                  device: the baseline the slots' concurrency is measured against).
+    Latency is submit-to-result.  With oracle_picks > 0 a few requests are
+    served once more with their intensity and checked against the FP64 oracle
+    (on the CPU, after the timed runs)."""
     import numpy as np
     from paper_2202_03411_gb300.serving import Server, run_stream
     from workloads import serving_mix
     reqs = serving_mix(n_requests, rate_per_s=1.0, seed=seed)     # arrival times rescaled below
     targets = serving_targets(reqs, precision)
     budget = 120 * (1 << 30)
+    out = {"requests": len(reqs), "slots": slots, "budget_bytes": budget}
+
     srv = Server(budget, slots=slots, precision=precision)
-    # warm the slots' handles for every geometry (untimed)
-    warm = {}
-    for r, t in zip(reqs, targets):
-        warm.setdefault((r.geometry.nx, r.geometry.det_nx), (r, t))
-    run_stream(srv, [r for r, _ in warm.values()], [t for _, t in warm.values()], time_scale=0.0)
+    _, lat, status, wall = run_stream(srv, reqs, targets, time_scale=0.0)
+    out["cold"] = _stream_stats(lat, status, wall, len(reqs))
+    out["cold"]["note"] = "fresh server: handles created on demand inside the run"
+    srv.close()
+
+    def warm(server):
+        first = {}
+        for r, t in zip(reqs, targets):
+            first.setdefault((r.geometry.nx, r.geometry.det_nx), (r, t))
+        run_stream(server, [r for r, _ in first.values()], [t for _, t in first.values()], time_scale=0.0)
+
+    srv = Server(budget, slots=slots, precision=precision)
+    warm(srv)
     _, lat, status, wall = run_stream(srv, reqs, targets, time_scale=0.0)
     sat = len(reqs) / wall
-    out = {"requests": len(reqs), "slots": slots, "saturation_patterns_per_s": sat,
-           "saturation_p50_ms": 1e3 * float(np.percentile(lat, 50)),
-           "saturation_p99_ms": 1e3 * float(np.percentile(lat, 99)), "failed": int(sum(1 for x in status if x))}
+    out["saturation"] = _stream_stats(lat, status, wall, len(reqs))
+    out["saturation_patterns_per_s"] = sat
     runs = []
     mean_gap = reqs[-1].arrival_s / len(reqs)
     for f in fractions:
         scale = 1.0 / (f * sat * mean_gap)          # arrival rate = f * saturation
         _, lat, status, wall = run_stream(srv, reqs, targets, time_scale=scale)
-        runs.append({"load": f, "offered_per_s": f * sat, "patterns_per_s": len(reqs) / wall,
-                     "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                     "failed": int(sum(1 for x in status if x))})
+        row = _stream_stats(lat, status, wall, len(reqs))
+        row.update({"load": f, "offered_per_s": f * sat})
+        runs.append(row)
     out["poisson"] = runs
     out["stats"] = srv.stats()
+    if oracle_picks > 0:
+        picks = np.linspace(0, len(reqs) - 1, oracle_picks).astype(int).tolist()
+        out["served_vs_fp64_oracle"] = serving_oracle_check(srv, reqs, targets, picks)
     srv.close()
+
+    one = Server(budget, slots=1, precision=precision)
+    warm(one)
+    _, lat, status, wall = run_stream(one, reqs, targets, time_scale=0.0)
+    out["one_slot"] = _stream_stats(lat, status, wall, len(reqs))
+    one.close()
+    out["slots_over_one_slot"] = sat / out["one_slot"]["requests_per_s"]
     return out
 
 
@@ -724,7 +782,7 @@ def main():
     serving = None
     if args.short_serving > 0 and extras:
         try:
-            serving = serving_run(args.short_serving, args.serving_slots, args.precision, fractions=(0.8,))
+            serving = serving_run(args.short_serving, args.serving_slots, args.precision)
         except Exception as e:          # the main line is still printed
             serving = {"error": f"{type(e).__name__}: {e}"}
 
@@ -753,7 +811,7 @@ def main():
         "fig8b_uniform_q": fig8b,
         "map_shapes_96": maps,
         "ideal_detector": detector,
-        "serving_short": serving,
+        "serving": serving,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_pattern(args.precision, g.n_pix,

@@ -78,8 +78,9 @@ enum {
 
 /*
  * Experiment and grid (Sec. 3.1, Blocks 1-3; Listing 1 set_experiment).
- *  nx, ny, nz      voxel grid (each >= 1, nz <= 256; tensor-core modes need
- *                  nx <= 128 and, with split phases, ny <= 128)
+ *  nx, ny, nz      voxel grid (each >= 1, nx, ny <= 4096, nz <= 512; nz <= 256
+ *                  in SCATMAN_FP64; tensor-core modes need nx <= 256 and, with
+ *                  split phases, ny <= 128, unsplit ny <= 256)
  *  voxel           voxel edge and slice thickness dz, same length unit as wavelength
  *  wavelength      lambda; k0 = 2 pi / lambda
  *  theta_max_deg   scattering angle at the detector's edge midpoints, (0, 90)
@@ -100,7 +101,7 @@ enum {
  *                  nz <= 128: on the CUDA cores in SCATMAN_FP32 / SCATMAN_FP64,
  *                  on the tensor cores in the four TC modes (y-sum with FP16
  *                  operands, x/z sum in the mode's type; nx <= 128 and, with
- *                  split phases, ny <= 128 as for the flat detector)
+ *                  split phases, ny <= 128)
  */
 typedef struct {
     int nx, ny, nz;

@@ -137,7 +137,7 @@ cudaError_t launch_adjoint_field(bool fp64, const void *A, const void *dLdI, con
 int grad_param_count(const ShapeParams &sp) { return n_geom_params(sp.kind, sp.lmax); }
 
 constexpr int kGradThreads = 256;
-constexpr int kGradMaxRun = 8;
+constexpr int kGradMaxRun = 16;
 constexpr int kMaxGeom = (SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1);
 constexpr int kGradWarpSlots = (kMaxGeom + 31) / 32;
 
@@ -405,16 +405,20 @@ cudaError_t launch_grad_voxels(bool fp64, const ShapeParams &sp, const GridParam
             grad_voxel_kernel<double, 2><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
         else if (run <= 4)
             grad_voxel_kernel<double, 4><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
-        else
+        else if (run <= 8)
             grad_voxel_kernel<double, 8><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
+        else
+            grad_voxel_kernel<double, 16><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
     } else {
         const float2 *Sf = (const float2 *)S;
         if (run <= 2)
             grad_voxel_kernel<float, 2><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
         else if (run <= 4)
             grad_voxel_kernel<float, 4><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
-        else
+        else if (run <= 8)
             grad_voxel_kernel<float, 8><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
+        else
+            grad_voxel_kernel<float, 16><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
     }
     return cudaGetLastError();
 }

@@ -197,8 +197,8 @@ void scatman_destroy(scatman_handle *h) {
 // Checks shared by scatman_create and scatman_forward_noalloc: grid, lengths,
 // occupancy width, and the q set (explicit list or detector).  Sets *n_pix.
 static bool check_config(const scatman_config &c, long long *n_pix, std::string *why) {
-    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.nz > 256 || c.nx > 4096 || c.ny > 4096) {
-        *why = "grid sizes must be >= 1, nx and ny <= 4096 and nz <= 256";
+    if (c.nx < 1 || c.ny < 1 || c.nz < 1 || c.nz > 512 || c.nx > 4096 || c.ny > 4096) {
+        *why = "grid sizes must be >= 1, nx and ny <= 4096 and nz <= 512";
         return false;
     }
     if (!(c.voxel > 0) || !(c.wavelength > 0)) {
@@ -286,6 +286,8 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     }
     if (c.precision < SCATMAN_FP64 || c.precision > SCATMAN_TC_BF16)
         return fail(set_error(h, SCATMAN_ERR_ARG, "unknown precision"));
+    if (c.precision == SCATMAN_FP64 && c.nz > 256)
+        return fail(set_error(h, SCATMAN_ERR_ARG, "SCATMAN_FP64 supports nz <= 256"));
     h->uniform_q = c.detector == SCATMAN_DETECTOR_UNIFORM_Q && !cfg->q_list;
     if (h->uniform_q && c.nz > 128)
         return fail(set_error(h, SCATMAN_ERR_ARG, "the uniform-q detector supports nz <= 128"));
@@ -317,8 +319,9 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
         h->Nxp = (int)round_up(c.nx, 16);
         h->Nyp = (int)round_up(c.ny, 16);
         h->Kp = h->Nyp;                       // K extent of one slice-operand row
-        if (h->Nxp > 128)
-            return fail(set_error(h, SCATMAN_ERR_ARG, "tensor-core modes support nx <= 128"));
+        if (h->Nxp > (h->uniform_tc ? 128 : 256))
+            return fail(set_error(h, SCATMAN_ERR_ARG, h->uniform_tc ? "the uniform-q detector's tensor-core modes support nx <= 128"
+                                                                   : "tensor-core modes support nx <= 256"));
         if (!tc_grid_ok(h->Nxp, h->Nyp, h->split))
             return fail(set_error(h, SCATMAN_ERR_ARG, "ny too large for the tensor-core phase operand"));
         h->b_rows = (size_t)c.nz * 3 * h->Nxp;   // planes -Im, Re, Im of every slice

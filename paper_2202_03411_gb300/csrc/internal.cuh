@@ -129,10 +129,10 @@ struct TcMaps {
 // Per-slice geometry the voxeliser records for the contractions, in one
 // device buffer of slice_geom_ints(nz) ints:
 //   [0, 4 nz)            occupied box of every slice [x_lo | x_hi | y_lo | y_hi]
-//   [4 nz, 36 nz)        occupied y range of every 8-column chunk of every slice,
-//                        [y_lo | y_hi] x [nz][kGeomChunks] (tensor-core grids, nx <= 128)
+//   [4 nz, 68 nz)        occupied y range of every 8-column chunk of every slice,
+//                        [y_lo | y_hi] x [nz][kGeomChunks] (tensor-core grids, nx <= 256)
 //   then                 the tensor-core kernel's work-unit list (uint2, kMaxUnitsPerSlice nz + 1)
-constexpr int kGeomChunks = 16;
+constexpr int kGeomChunks = 32;
 constexpr int kMaxUnitsPerSlice = 4;
 inline size_t slice_geom_ints(int nz) {
     return 4 * (size_t)nz + 2 * (size_t)kGeomChunks * nz + 2 * ((size_t)kMaxUnitsPerSlice * nz + 1);

@@ -15,7 +15,8 @@
 // pair P = P_hi + P_lo and both halves accumulate into the same FP32 result.
 //
 // Work units.  A unit is one occupied slice's run of occupied 8-column chunks
-// of x (up to the full 128): its MMAs have N = 16 nch, and it runs only the K
+// of x, at most 16 (128 x; wider slices, up to nx = 256, are cut evenly into
+// two units): its MMAs have N = 16 nch <= 256, and it runs only the K
 // steps its y range needs, shifted by 8 y when that saves one (the B box then
 // starts 8 y later and the epilogue multiplies the unit's sum by
 // e^{-i q_y 8 dy}).  Whole slices keep each unit's MMA work long enough to
@@ -115,7 +116,7 @@ static size_t tc_ring_bytes(int Nxp, int Nyp, bool split) {
     const size_t used = tc_fixed_bytes() + (split ? 2 : 1) * tc_a_bytes(Nyp);
     if (used >= (size_t)kMaxSmem) return 0;
     const size_t r = ((size_t)kMaxSmem - used) / 1024 * 1024;
-    const size_t widest = (size_t)kPlanes * Nxp * 128;
+    const size_t widest = (size_t)kPlanes * (Nxp < 8 * kTcMaxChunks ? Nxp : 8 * kTcMaxChunks) * 128;
     return r >= 2 * widest ? r : 0;
 }
 
@@ -173,29 +174,39 @@ __host__ __device__ inline int plan_units(const int *cy, int nz, int t, int nc8,
 }
 
 // Lists the work units of every slice, in slice order: list[1 + i] =
-// {t, unit word}, list[0].x = their number.  One block of 256 threads (nz <= 256).
+// {t, unit word}, list[0].x = their number.  One block of 256 threads, 256
+// slices per pass.
 __global__ void __launch_bounds__(256) pack_units_kernel(const int *cy, int nz, int nc8, int max_chunks,
                                                          int allow_shift, uint2 *list) {
     __shared__ int s_warp[8];
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    uint32_t w[kMaxUnitsPerSlice];
-    const int n = t < nz ? plan_units(cy, nz, t, nc8, max_chunks, allow_shift != 0, w) : 0;
-    int x = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_warp[wid] = x;
+    __shared__ int s_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_base = 0;
     __syncthreads();
-    int off = x - n;
-    for (int k = 0; k < wid; ++k) off += s_warp[k];
-    for (int i = 0; i < n; ++i) list[1 + off + i] = make_uint2((uint32_t)t, w[i]);
-    if (t == 0) {
-        int tot = 0;
-        for (int k = 0; k < 8; ++k) tot += s_warp[k];
-        list[0] = make_uint2((uint32_t)tot, 0u);
+    for (int t0 = 0; t0 < nz; t0 += 256) {
+        const int t = t0 + (int)threadIdx.x;
+        uint32_t w[kMaxUnitsPerSlice];
+        const int n = t < nz ? plan_units(cy, nz, t, nc8, max_chunks, allow_shift != 0, w) : 0;
+        int x = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[wid] = x;
+        __syncthreads();
+        int off = s_base + x - n;
+        for (int k = 0; k < wid; ++k) off += s_warp[k];
+        for (int i = 0; i < n; ++i) list[1 + off + i] = make_uint2((uint32_t)t, w[i]);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = s_base;
+            for (int k = 0; k < 8; ++k) tot += s_warp[k];
+            s_base = tot;
+        }
+        __syncthreads();
     }
+    if (threadIdx.x == 0) list[0] = make_uint2((uint32_t)s_base, 0u);
 }
 
 // Tile, part (-1: whole tile) and unit range [i_lo, i_hi) of work unit u.
@@ -711,8 +722,8 @@ double tc_issued_flops(const int *geom, int nz, int Nxp, int Nyp, long long n_pi
 // three planes of one slice.
 bool encode_tmap_B(TcMaps *maps, void *base, int Kp, int Nxp, int nz, bool bf16, std::string *why) {
     std::memset(maps, 0, sizeof(TcMaps));
-    const int nch = Nxp / 8;
-    if (nch < 1 || nch > kTcMaxChunks) {
+    const int nch = Nxp / 8 < kTcMaxChunks ? Nxp / 8 : kTcMaxChunks;
+    if (nch < 1 || Nxp > 8 * kGeomChunks) {
         *why = "slice width outside the tensor-core range";
         return false;
     }
@@ -729,7 +740,7 @@ static cudaError_t launch_tc(const TcMaps &maps, const double *q, long long n_pi
                              int Nyp, double voxel, double str_re, double str_im, bool split, bool bf16, int *geom,
                              float2 *A, float *I, int *err, int sm_count, cudaStream_t st, const UqStore *store,
                              float2 *tail_part) {
-    if (!tc_grid_ok(Nxp, Nyp, split) || nz < 1 || nz > 256 || nx > Nxp || ny > Nyp) return cudaErrorInvalidValue;
+    if (!tc_grid_ok(Nxp, Nyp, split) || nz < 1 || nz > 512 || nx > Nxp || ny > Nyp) return cudaErrorInvalidValue;
     const size_t ring = tc_ring_bytes(Nxp, Nyp, split);
     if (ring == 0) return cudaErrorInvalidValue;
     const int max_chunks = kTcMaxChunks;

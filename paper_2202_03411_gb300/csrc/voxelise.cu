@@ -45,7 +45,7 @@ cudaError_t launch_detector_q(int det_nx, int det_ny, double theta_max_deg, doub
 
 constexpr int kLinesPerCta = 32;
 constexpr int kVoxThreads = 256;
-constexpr int kMaxRun = 8;          // z values per lane: nz <= 256
+constexpr int kMaxRun = 16;         // z values per lane: nz <= 512 (256 in the FP64 mode)
 constexpr int kVoxQueue = 512;      // binary voxels per CTA whose FP64 decision is batched
 
 // s_j = chi_j T_j with T_j = exp(i k0 dz (n-1) C_j) = e^{-k0 dz beta C} e^{-i k0 dz delta C}.
@@ -297,7 +297,7 @@ __global__ void bounds_init_kernel(int *b, int nz, int *cy) {
 
 cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const SliceOut &out, bool scan_fp64,
                             bool fp64_mode, cudaStream_t st) {
-    if (gp.nz > 32 * kMaxRun) return cudaErrorInvalidValue;
+    if (gp.nz > 32 * kMaxRun || (fp64_mode && gp.nz > 256)) return cudaErrorInvalidValue;
     if (out.chunk_y && (out.bounds == nullptr || gp.nx > 8 * kGeomChunks)) return cudaErrorInvalidValue;
     if (out.bounds)
         bounds_init_kernel<<<(2 * kGeomChunks * gp.nz + 255) / 256, 256, 0, st>>>(out.bounds, gp.nz, out.chunk_y);
@@ -306,7 +306,8 @@ cudaError_t launch_voxelise(const ShapeParams &sp, const GridParams &gp, const S
     size_t smem = (cx + sizeof(float)) * (size_t)(gp.nz + 1) * kLinesPerCta + kVoxQueue * sizeof(int);
     // per-function attribute shared by all threads: set it to the largest size
     // (nz = 256) so a concurrent launch from another thread is never rejected
-    const int smem_max = (int)((cx + sizeof(float)) * (32 * kMaxRun + 1) * kLinesPerCta + kVoxQueue * sizeof(int));
+    const int smem_max = (int)((cx + sizeof(float)) * ((fp64_mode ? 256 : 32 * kMaxRun) + 1) * kLinesPerCta +
+                               kVoxQueue * sizeof(int));
     const bool maps = sp.kind == SCATMAN_RADIALMAP || sp.kind == SCATMAN_VOLUMEMAP;
     auto k = fp64_mode   ? (maps ? voxelise_scan_kernel<true, double, true> : voxelise_scan_kernel<true, double, false>)
              : scan_fp64 ? (maps ? voxelise_scan_kernel<false, double, true> : voxelise_scan_kernel<false, double, false>)

@@ -46,7 +46,8 @@ def _create(lib, g, prec, **kw):
 
 @pytest.mark.parametrize("g,prec,kw,frag", [
     (Geometry(0, 8, 8, 1.0, 8.0, 30.0, 8, 8), "fp32", {}, "grid"),
-    (Geometry(8, 8, 300, 1.0, 8.0, 30.0, 8, 8), "fp32", {}, "nz"),
+    (Geometry(8, 8, 600, 1.0, 8.0, 30.0, 8, 8), "fp32", {}, "nz"),
+    (Geometry(8, 8, 300, 1.0, 8.0, 30.0, 8, 8), "fp64", {}, "nz"),
     (Geometry(8, 8, 8, 0.0, 8.0, 30.0, 8, 8), "fp32", {}, "positive"),
     (Geometry(8, 8, 8, 1.0, 8.0, 95.0, 8, 8), "fp32", {}, "theta"),
     (Geometry(8, 8, 8, 1.0, 8.0, 30.0, 0, 8), "fp32", {}, "detector"),

@@ -289,7 +289,7 @@ def test_errors_on_device():
         sm.scatman_voxelise(h, Shape(SPHHARM, R0=3.0, lmax=20, alm=np.zeros(441)))
     h.close()
     with pytest.raises(sm.ScatmanError):
-        sm.scatman_create(Geometry(200, 16, 16, 1.0, 6.0, 30.0, 8, 8), "tc_f16_split")
+        sm.scatman_create(Geometry(300, 16, 16, 1.0, 6.0, 30.0, 8, 8), "tc_f16_split")
 
 
 @pytest.mark.parametrize("prec", ["tc_f16_split", "tc_bf16_split", "tc_f16"])
