@@ -21,6 +21,18 @@
 // generators do no FP64 work.  A CTA owns two slices (two TMEM accumulators
 // sharing every R tile) and a contiguous range of pixels; the pixel ranges'
 // partial fields are summed in a fixed order afterwards.
+//
+// Order mode.  The slice factor e^{+i q_z z_j} is the only part of L_j that
+// depends on j.  With q_z = q_c + D u (u in [-1, 1] over the pixels) the
+// Jacobi-Anger expansion
+//   e^{+i q_z z_j} = e^{+i q_c z_j} sum_{n >= 0} eps_n i^n J_n(D z_j) T_n(u),
+//   T_n(u) = cos(n theta), theta = acos(u), eps_0 = 1, eps_n = 2,
+// truncated after N orders (|J_n(w)| <= (|w|/2)^n / n!, so the tail is below
+// 1e-7 of sum_q |g_q| for the N chosen on the host) turns the nz slice GEMMs into
+// N order GEMMs S~_n[x, y] = sum_q g_q cos(n theta_q) e^{+i (q_x x + q_y y)}: the
+// same kernel, with the order n in place of the slice and the real factor
+// cos(n theta_q) in place of the slice phase; adj_orders_combine_kernel then
+// forms S_j = sum_n a[j, n] S~_n with a[j, n] = e^{+i q_c z_j} eps_n i^n J_n(D z_j).
 #include "internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -34,10 +46,13 @@ constexpr int kAdjChunk = 32;                 // pixels per K block (64 real K =
 constexpr int kAdjMaxStages = 6;
 constexpr int kAdjRows = 128;                 // M: x rows
 constexpr int kAdjTileA = kAdjRows * 128;     // one A tile: 128 rows x 128 bytes
-constexpr int kAdjMaxSplits = 8;             // bounds the partial-field memory to 8 fields
+constexpr int kAdjMaxSplits = 8;             // bounds the partial-field memory to 8 fields (slice mode)
+constexpr int kAdjMaxSplitsOrders = 32;      // order mode: few order pairs, 2D partial fields
 
 struct AdjParams {
-    const float4 *tab;          // per pixel: (qxh, qxl, qyh, qyl), (qzh, qzl, e^{+i qx dv}), (e^{+i qy dv}, e^{+i qz dv})
+    const float4 *tab;          // per pixel: (qxh, qxl, qyh, qyl), (qzh, qzl, e^{+i qx dv}), (e^{+i qy dv}, e^{+i qz dv});
+                                // order mode: theta (hi, lo) in place of q_z and e^{+i theta} in place of e^{+i qz dv}
+    int orders;                 // 1: order mode (nz below is the number of orders N)
     const uint8_t *rtile;       // per 32-pixel chunk: the y-phase operand tile (2 Nyp rows x 128 bytes)
     int stages;
     int teams;                  // generator teams (1, 2 or 4; never more than stages)
@@ -66,25 +81,35 @@ __device__ __forceinline__ uint32_t pack_half2(float a, float b) {
     return *reinterpret_cast<uint32_t *>(&h);
 }
 
-// Per-pixel constants of the generators: q as FP32 pairs and e^{+i q dv}.
-__global__ void adj_pixel_table_kernel(const double *__restrict__ q, long long n, double voxel,
-                                       float4 *__restrict__ tab) {
+// Per-pixel constants of the generators: q as FP32 pairs and e^{+i q dv}; in
+// order mode (inv_d > 0) theta = acos((q_z - q_c) inv_d) replaces q_z and
+// e^{+i theta} replaces e^{+i q_z dv}.
+__global__ void adj_pixel_table_kernel(const double *__restrict__ q, long long n, double voxel, int orders,
+                                       double qc, double inv_d, float4 *__restrict__ tab) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const double qx = q[3 * p], qy = q[3 * p + 1], qz = q[3 * p + 2];
+    const double qx = q[3 * p], qy = q[3 * p + 1];
+    double qz = q[3 * p + 2];
+    const float vf = (float)voxel;
+    float zstep = vf;
+    if (orders) {
+        const double u = fmin(1.0, fmax(-1.0, (qz - qc) * inv_d));
+        qz = acos(u);
+        zstep = 1.0f;
+    }
     const float qxh = (float)qx, qxl = (float)(qx - (double)qxh);
     const float qyh = (float)qy, qyl = (float)(qy - (double)qyh);
     const float qzh = (float)qz, qzl = (float)(qz - (double)qzh);
-    const float vf = (float)voxel;
     // e^{+i t} = conj(e^{-i t}) = expmi(q, -c)
-    const float2 ex = expmi_fs(qxh, qxl, -vf), ey = expmi_fs(qyh, qyl, -vf), ez = expmi_fs(qzh, qzl, -vf);
+    const float2 ex = expmi_fs(qxh, qxl, -vf), ey = expmi_fs(qyh, qyl, -vf), ez = expmi_fs(qzh, qzl, -zstep);
     tab[3 * p] = make_float4(qxh, qxl, qyh, qyl);
     tab[3 * p + 1] = make_float4(qzh, qzl, ex.x, ex.y);
     tab[3 * p + 2] = make_float4(ey.x, ey.y, ez.x, ez.y);
 }
 
-cudaError_t launch_adj_pixel_table(const double *q, long long n, double voxel, float4 *tab, cudaStream_t st) {
-    adj_pixel_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q, n, voxel, tab);
+cudaError_t launch_adj_pixel_table(const double *q, long long n, double voxel, int orders, double qc, double inv_d,
+                                   float4 *tab, cudaStream_t st) {
+    adj_pixel_table_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(q, n, voxel, orders, qc, inv_d, tab);
     return cudaGetLastError();
 }
 
@@ -230,7 +255,9 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
         const int r0 = (warp % per_team) * ra, r1 = min(P.nx, r0 + ra);
         const float vox = (float)P.voxel;
         const float x0 = ((float)r0 - 0.5f * (float)(P.nx - 1)) * vox;
-        const float zj = ((float)j0 - 0.5f * (P.nz - 1)) * vox;
+        // slice mode: z of slice j0 (the factor e^{+i q_z z}); order mode: the order
+        // j0 (the factor e^{+i j0 theta}, stepped by e^{+i theta} to order j0 + 1)
+        const float zj = P.orders ? (float)j0 : ((float)j0 - 0.5f * (P.nz - 1)) * vox;
         // this lane's pixel data, loaded one chunk ahead so the L2 latency
         // overlaps the previous chunk's generation
         float2 a_n = make_float2(0.f, 0.f);
@@ -268,14 +295,29 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
                 const float2 ezs = make_float2(tcv.z, tcv.w);
                 const float2 ex = expmi_fs(ta.x, ta.y, -x0);
                 const float2 exs = make_float2(tb.z, tb.w);
-                float2 L0 = cmul(cmul(g, ez), ex);       // slice j0, row r0
+                if (P.orders) {
+                    // orders j0 and j0 + 1: real factors cos(j0 theta), cos((j0 + 1) theta)
+                    const float c1 = ez.x * ezs.x - ez.y * ezs.y;
+                    const float2 gx = cmul(g, ex);
+                    float2 L0 = make_float2(gx.x * ez.x, gx.y * ez.x), L1 = make_float2(gx.x * c1, gx.y * c1);
 #pragma unroll 4
-                for (int r = r0; r < r1; ++r) {
-                    const float2 L1 = cmul(L0, ezs);
-                    const uint32_t off = pair_offset(r, i);
-                    *reinterpret_cast<uint32_t *>(sA0 + off) = pack_half2(L0.x, L0.y);
-                    *reinterpret_cast<uint32_t *>(sA1 + off) = pack_half2(L1.x, L1.y);
-                    L0 = cmul(L0, exs);
+                    for (int r = r0; r < r1; ++r) {
+                        const uint32_t off = pair_offset(r, i);
+                        *reinterpret_cast<uint32_t *>(sA0 + off) = pack_half2(L0.x, L0.y);
+                        *reinterpret_cast<uint32_t *>(sA1 + off) = pack_half2(L1.x, L1.y);
+                        L0 = cmul(L0, exs);
+                        L1 = cmul(L1, exs);
+                    }
+                } else {
+                    float2 L0 = cmul(cmul(g, ez), ex);       // slice j0, row r0
+#pragma unroll 4
+                    for (int r = r0; r < r1; ++r) {
+                        const float2 L1 = cmul(L0, ezs);
+                        const uint32_t off = pair_offset(r, i);
+                        *reinterpret_cast<uint32_t *>(sA0 + off) = pack_half2(L0.x, L0.y);
+                        *reinterpret_cast<uint32_t *>(sA1 + off) = pack_half2(L1.x, L1.y);
+                        L0 = cmul(L0, exs);
+                    }
                 }
             }
             fence_async_smem();
@@ -376,13 +418,14 @@ bool adjoint_tc_supported(int nx, int ny) {
     return nx <= kAdjRows && Nyp <= 128 && adj_stages(Nyp) >= 2;
 }
 
-// Pixel ranges per slice pair: balance the grid over the SMs (1 CTA per SM).
-int adjoint_tc_splits(long long n_pix, int nz, int sm_count) {
+// Pixel ranges per slice (or order) pair: balance the grid over the SMs (1 CTA per SM).
+int adjoint_tc_splits(long long n_pix, int nz, int sm_count, bool orders) {
     const int pairs = (nz + 1) / 2;
     const long long max_split = (n_pix + kAdjChunk - 1) / kAdjChunk;
+    const int cap = orders ? kAdjMaxSplitsOrders : kAdjMaxSplits;
     int best = 1;
     double best_score = -1.0;
-    for (int ks = 1; ks <= kAdjMaxSplits && ks <= max_split; ++ks) {
+    for (int ks = 1; ks <= cap && ks <= max_split; ++ks) {
         const long long total = (long long)pairs * ks;
         const long long waves = (total + sm_count - 1) / sm_count;
         const double eff = (double)total / (double)(waves * sm_count);
@@ -396,10 +439,11 @@ int adjoint_tc_splits(long long n_pix, int nz, int sm_count) {
 }
 
 cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab, const uint8_t *rtile, long long n_pix,
-                              int nx, int ny, int nz, double voxel, int splits, float2 *partial, unsigned *gmax_bits,
-                              float2 *S, int *err, cudaStream_t st) {
+                              int nx, int ny, int nz, int orders, double voxel, int splits, float2 *partial,
+                              unsigned *gmax_bits, float2 *S, int *err, cudaStream_t st) {
     AdjParams P;
     P.tab = tab;
+    P.orders = orders ? 1 : 0;
     P.rtile = rtile;
     P.A = A;
     P.w = w;
@@ -431,6 +475,46 @@ cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab
     dim3 grid((nz + 1) / 2, splits);
     adjoint_tc_kernel<<<grid, kAdjThreads, adj_smem_bytes(P.Nyp), st>>>(P);
     adj_sum_kernel<<<(unsigned)((P.nvox + 255) / 256), 256, 0, st>>>(partial, splits, P.nvox, S);
+    return cudaGetLastError();
+}
+
+// Order mode: S[j][x][y] = sum_n coef[j][n] S~[n][x][y], summed in order n = 0, 1, ...
+// One thread per (x, y) column keeps its N order values in registers.
+template <int kMaxN>
+__global__ void adj_orders_combine_kernel(const float2 *__restrict__ Sord, const float2 *__restrict__ coef, int N,
+                                          int nz, long long nxy, float2 *__restrict__ S) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nxy) return;
+    float2 v[kMaxN];
+#pragma unroll
+    for (int n = 0; n < kMaxN; ++n) v[n] = n < N ? Sord[(size_t)n * nxy + c] : make_float2(0.f, 0.f);
+    for (int j = 0; j < nz; ++j) {
+        const float2 *a = coef + (size_t)j * N;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int n = 0; n < kMaxN; ++n) {
+            if (n < N) {
+                const float2 t = __ldg(&a[n]);
+                acc.x = fmaf(t.x, v[n].x, fmaf(-t.y, v[n].y, acc.x));
+                acc.y = fmaf(t.x, v[n].y, fmaf(t.y, v[n].x, acc.y));
+            }
+        }
+        S[(size_t)j * nxy + c] = acc;
+    }
+}
+
+cudaError_t launch_adj_orders_combine(const float2 *Sord, const float2 *coef, int N, int nz, int nx, int ny, float2 *S,
+                                      cudaStream_t st) {
+    const long long nxy = (long long)nx * ny;
+    const unsigned blocks = (unsigned)((nxy + 127) / 128);
+    if (N <= 16)
+        adj_orders_combine_kernel<16><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
+    else if (N <= 32)
+        adj_orders_combine_kernel<32><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
+    else if (N <= 64)
+        adj_orders_combine_kernel<64><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -183,6 +183,8 @@ void scatman_destroy(scatman_handle *h) {
     cudaFree(h->d_adj_part);
     cudaFree(h->d_gmax);
     cudaFree(h->d_adj_tab);
+    cudaFree(h->d_adj_coef);
+    cudaFree(h->d_adj_ord);
     cudaFree(h->d_adj_rtile);
     cudaFree(h->d_rmap);
     cudaFree(h->d_rmapf);
@@ -882,6 +884,107 @@ int scatman_photon_counts(scatman_handle *h, double photon_density, unsigned lon
                       "photon counts");
 }
 
+// Bessel functions J_0(w) .. J_{N-1}(w) of the first kind, by Miller's backward
+// recurrence J_{k-1} = (2k / x) J_k - J_{k+1} from far above N and |w|,
+// normalised with J_0 + 2 sum_{k >= 1} J_{2k} = 1; J_k(-x) = (-1)^k J_k(x).
+static void bessel_j_orders(double w, int N, double *J) {
+    for (int k = 0; k < N; ++k) J[k] = 0.0;
+    const double x = std::fabs(w);
+    if (x == 0.0) {
+        J[0] = 1.0;
+        return;
+    }
+    const double top = std::fmax((double)N, x);
+    const int m = 2 * (((int)(top + 40.0 + std::sqrt(40.0 * top))) / 2);
+    std::vector<double> t((size_t)m + 2, 0.0);
+    double jp = 0.0, j = 1e-300, norm = 0.0;
+    t[(size_t)m] = j;
+    for (int k = m; k > 0; --k) {
+        const double jm = 2.0 * k / x * j - jp;
+        jp = j;
+        j = jm;
+        t[(size_t)k - 1] = j;
+        if (std::fabs(j) > 1e250) {               // rescale everything computed so far
+            for (int q = k - 1; q <= m; ++q) t[(size_t)q] *= 1e-250;
+            j *= 1e-250;
+            jp *= 1e-250;
+        }
+    }
+    norm = t[0];
+    for (int k = 2; k <= m; k += 2) norm += 2.0 * t[(size_t)k];
+    for (int k = 0; k < N; ++k) J[k] = t[(size_t)k] / norm * ((w < 0.0 && (k & 1)) ? -1.0 : 1.0);
+}
+
+// Orders N after which the Jacobi-Anger tail 2 sum_{n >= N} |J_n(w)| is below
+// tol for every |w| <= wmax (|J_n(w)| <= (|w|/2)^n / n!, a geometric majorant
+// once n + 1 > |w| / 2).
+static int adjoint_orders_needed(double wmax, double tol) {
+    const double hw = 0.5 * std::fabs(wmax);
+    double t = 1.0;                                // (hw)^N / N!
+    for (int N = 1; N < 512; ++N) {
+        t *= hw / N;
+        if (hw < N + 1 && 2.0 * t / (1.0 - hw / (N + 1)) <= tol) return N;
+    }
+    return 512;
+}
+
+// Chooses the tensor-core adjoint's form for the handle (once): with the q_z of
+// the handle's pixels in [q_c - D, q_c + D] and |z_j| <= z_max, order mode takes
+// N orders for w = D z_max; it is used when N < nz.  Builds the pixel table in
+// the chosen form and, in order mode, the coefficients a[j][n].
+static int plan_adjoint(scatman_handle *h) {
+    const scatman_config &c = h->cfg;
+    std::vector<double> qz((size_t)h->n_pix);
+    int rc = check_cuda(h, cudaMemcpy2DAsync(qz.data(), sizeof(double), h->d_q + 2, 3 * sizeof(double), sizeof(double),
+                                             (size_t)h->n_pix, cudaMemcpyDeviceToHost, h->stream),
+                        "q_z download");
+    if (rc) return rc;
+    if ((rc = check_cuda(h, cudaStreamSynchronize(h->stream), "q_z download"))) return rc;
+    double lo = qz[0], hi = qz[0];
+    for (double v : qz) {
+        lo = std::fmin(lo, v);
+        hi = std::fmax(hi, v);
+    }
+    const double qc = 0.5 * (lo + hi), D = 0.5 * (hi - lo);
+    const double zmax = 0.5 * (c.nz - 1) * c.voxel;
+    const int N = D > 0.0 ? adjoint_orders_needed(D * zmax, 1e-7) : 1;
+    const bool orders = N < c.nz && N <= 64;
+    h->adj_orders = orders ? N : 0;
+    if ((rc = alloc_dev(h, (void **)&h->d_adj_tab, (size_t)h->n_pix * 3 * sizeof(float4), "adjoint pixel table")))
+        return rc;
+    if ((rc = check_cuda(h, launch_adj_pixel_table(h->d_q, h->n_pix, c.voxel, orders ? 1 : 0, qc,
+                                                   orders && D > 0.0 ? 1.0 / D : 0.0, h->d_adj_tab, h->stream),
+                         "adjoint pixel table")))
+        return rc;
+    if (!orders) return SCATMAN_OK;
+    // a[j][n] = e^{+i q_c z_j} eps_n i^n J_n(D z_j)
+    std::vector<float2> coef((size_t)c.nz * N);
+    std::vector<double> J((size_t)N);
+    for (int jz = 0; jz < c.nz; ++jz) {
+        const double z = (jz - 0.5 * (c.nz - 1)) * c.voxel;
+        bessel_j_orders(D * z, N, J.data());
+        const double pr = std::cos(qc * z), pi = std::sin(qc * z);
+        for (int n = 0; n < N; ++n) {
+            const double m = (n == 0 ? 1.0 : 2.0) * J[(size_t)n];
+            // i^n = (1, i, -1, -i)
+            double ar = 0.0, ai = 0.0;
+            switch (n & 3) {
+                case 0: ar = m; break;
+                case 1: ai = m; break;
+                case 2: ar = -m; break;
+                default: ai = -m; break;
+            }
+            coef[(size_t)jz * N + n] = make_float2((float)(pr * ar - pi * ai), (float)(pr * ai + pi * ar));
+        }
+    }
+    if ((rc = alloc_dev(h, (void **)&h->d_adj_coef, coef.size() * sizeof(float2), "adjoint order coefficients")))
+        return rc;
+    if ((rc = check_cuda(h, cudaMemcpy(h->d_adj_coef, coef.data(), coef.size() * sizeof(float2), cudaMemcpyHostToDevice),
+                         "adjoint order coefficients")))
+        return rc;
+    return alloc_dev(h, (void **)&h->d_adj_ord, (size_t)N * c.nx * c.ny * sizeof(float2), "adjoint order fields");
+}
+
 int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams) {
     if (!h || !dLdI_dev || !dLdparams) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
     if (!h->have_forward) return set_error(h, SCATMAN_ERR_STATE, "backward before forward");
@@ -906,9 +1009,13 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
         h->part_count = need;
     }
     if (h->tensor_core && adjoint_tc_supported(c.nx, c.ny)) {
-        // adjoint contraction on the tensor cores
-        const int splits = adjoint_tc_splits(h->n_pix, c.nz, h->sm_count);
-        const size_t cnt = (size_t)splits * nvox;
+        // adjoint contraction on the tensor cores (per slice, or per Jacobi-Anger order)
+        if (h->adj_orders < 0 && (rc = plan_adjoint(h))) return rc;
+        const int N = h->adj_orders;
+        const int nz_eff = N > 0 ? N : c.nz;
+        int splits = adjoint_tc_splits(h->n_pix, nz_eff, h->sm_count, N > 0);
+        while (N > 0 && splits > 1 && splits * N > 8 * c.nz) --splits;   // within the slice mode's partial memory
+        const size_t cnt = (size_t)splits * nz_eff * c.nx * c.ny;
         if (h->adj_part_count < cnt) {
             cudaFree(h->d_adj_part);
             h->d_adj_part = nullptr;
@@ -917,13 +1024,6 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
             h->adj_part_count = cnt;
         }
         if (!h->d_gmax && (rc = alloc_dev(h, (void **)&h->d_gmax, sizeof(unsigned), "adjoint scale"))) return rc;
-        if (!h->d_adj_tab) {
-            if ((rc = alloc_dev(h, (void **)&h->d_adj_tab, (size_t)h->n_pix * 3 * sizeof(float4), "adjoint pixel table")))
-                return rc;
-            if ((rc = check_cuda(h, launch_adj_pixel_table(h->d_q, h->n_pix, c.voxel, h->d_adj_tab, h->stream),
-                                 "adjoint pixel table")))
-                return rc;
-        }
         if (!h->d_adj_rtile) {
             if ((rc = alloc_dev(h, (void **)&h->d_adj_rtile, adj_rtile_bytes(h->n_pix, c.ny), "adjoint y-phase tiles")))
                 return rc;
@@ -931,11 +1031,16 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
                                  "adjoint y-phase tiles")))
                 return rc;
         }
-        rc = check_cuda(h, launch_adjoint_tc((const float2 *)h->d_A, (const float *)dLdI_dev, h->d_adj_tab, h->d_adj_rtile, h->n_pix, c.nx,
-                                             c.ny, c.nz, c.voxel, splits, h->d_adj_part, h->d_gmax, (float2 *)h->d_S,
-                                             h->d_err, h->stream),
+        rc = check_cuda(h, launch_adjoint_tc((const float2 *)h->d_A, (const float *)dLdI_dev, h->d_adj_tab,
+                                             h->d_adj_rtile, h->n_pix, c.nx, c.ny, nz_eff, N > 0 ? 1 : 0, c.voxel,
+                                             splits, h->d_adj_part, h->d_gmax,
+                                             N > 0 ? h->d_adj_ord : (float2 *)h->d_S, h->d_err, h->stream),
                         "adjoint field (tensor cores)");
         if (rc) return rc;
+        if (N > 0 && (rc = check_cuda(h, launch_adj_orders_combine(h->d_adj_ord, h->d_adj_coef, N, c.nz, c.nx, c.ny,
+                                                                   (float2 *)h->d_S, h->stream),
+                                      "adjoint slices from orders")))
+            return rc;
     } else {
         rc = check_cuda(h, launch_adjoint_field(f64, h->d_A, dLdI_dev, h->d_q, h->n_pix, c.nx, c.ny, c.nz, c.voxel,
                                                 h->d_S, h->stream),

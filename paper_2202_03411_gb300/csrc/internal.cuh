@@ -201,6 +201,9 @@ struct scatman_handle {
     float2 *d_adj_part = nullptr;   // tensor-core adjoint: per-pixel-range partial fields
     size_t adj_part_count = 0;
     unsigned *d_gmax = nullptr;     // tensor-core adjoint: max |w A| (float bits)
+    int adj_orders = -1;            // tensor-core adjoint: Jacobi-Anger orders N (0: one GEMM per slice; -1: not chosen yet)
+    float2 *d_adj_coef = nullptr;   // order mode: a[j][n] = e^{+i q_c z_j} eps_n i^n J_n(D z_j), [nz][N]
+    float2 *d_adj_ord = nullptr;    // order mode: the orders' fields S~ [N][nx][ny]
     float4 *d_adj_tab = nullptr;    // tensor-core adjoint: per-pixel constants (built at the first backward)
     uint8_t *d_adj_rtile = nullptr; // tensor-core adjoint: y-phase operand tiles (built at the first backward)
     // map shapes: device copies of the last voxelised map (grown as needed)
@@ -315,15 +318,22 @@ cudaError_t launch_grad_pixels(bool fp64, const void *A, const void *dLdI, long 
 int grad_pixel_blocks(long long n_pix);
 // Tensor-core adjoint field (adjoint_tc.cu).
 bool adjoint_tc_supported(int nx, int ny);
-int adjoint_tc_splits(long long n_pix, int nz, int sm_count);
+// nz: slices, or in order mode (orders != 0) the number N of Jacobi-Anger orders;
+// S receives the slices' (or orders') fields [nz][nx][ny].
+int adjoint_tc_splits(long long n_pix, int nz, int sm_count, bool orders);
 cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab, const uint8_t *rtile, long long n_pix,
-                              int nx, int ny, int nz, double voxel, int splits, float2 *partial, unsigned *gmax_bits,
-                              float2 *S, int *err, cudaStream_t st);
+                              int nx, int ny, int nz, int orders, double voxel, int splits, float2 *partial,
+                              unsigned *gmax_bits, float2 *S, int *err, cudaStream_t st);
+// Order mode: the slices' fields from the orders' (coef: [nz][N] complex).
+cudaError_t launch_adj_orders_combine(const float2 *Sord, const float2 *coef, int N, int nz, int nx, int ny, float2 *S,
+                                      cudaStream_t st);
 // The adjoint's y-phase operand tiles (once per handle).
 size_t adj_rtile_bytes(long long n_pix, int ny);
 cudaError_t launch_adj_rtile(const float4 *tab, long long n_pix, int ny, double voxel, uint8_t *rt, cudaStream_t st);
 // Per-pixel constants of the tensor-core adjoint (3 float4 per pixel), once per handle.
-cudaError_t launch_adj_pixel_table(const double *q, long long n, double voxel, float4 *tab, cudaStream_t st);
+// orders != 0: order mode with theta = acos((q_z - qc) inv_d) in place of q_z.
+cudaError_t launch_adj_pixel_table(const double *q, long long n, double voxel, int orders, double qc, double inv_d,
+                                   float4 *tab, cudaStream_t st);
 // Fit residual 2 (I - target) and partial sums of (I - target)^2 (adjoint.cu).
 int l2_residual_blocks(long long n);
 cudaError_t launch_l2_residual(bool fp64, const void *I, const float *target, long long n, void *w, double *partials,

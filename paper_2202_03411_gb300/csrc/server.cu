@@ -358,6 +358,8 @@ long long scatman_footprint_bytes(const scatman_config *c) {
         const long long Nyp16 = ((c->ny + 7) / 8 * 8 + 15) / 16 * 16;
         b += round_2mib(8 * nvox * 8) + round_2mib(4) + round_2mib(48 * npix) +
              round_2mib((npix + 31) / 32 * 2 * Nyp16 * 128);
+        // Jacobi-Anger order fields (at most 64 orders) and their coefficients
+        b += round_2mib(64LL * c->nx * c->ny * 8) + round_2mib(64LL * c->nz * 8);
     }
     b += round_2mib((608LL * ((SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1) + 2) + 256) * 8);
     return b;
