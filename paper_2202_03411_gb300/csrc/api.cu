@@ -553,6 +553,7 @@ static int upload_maps(scatman_handle *h, const scatman_shape *s, ShapeParams *s
 }
 
 int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
+    const StageRange nvtx_range("scatman_voxelise");
     if (!h || !s) return SCATMAN_ERR_ARG;
     const scatman_config &c = h->cfg;
     if (s->kind < SCATMAN_SPHERE || s->kind > SCATMAN_VOLUMEMAP)
@@ -646,6 +647,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
 }
 
 int scatman_forward(scatman_handle *h, void *I_dev, void *A_dev) {
+    const StageRange nvtx_range("scatman_forward");
     if (!h || !I_dev) return set_error(h, SCATMAN_ERR_ARG, "I_dev is NULL");
     if (!h->have_shape) return set_error(h, SCATMAN_ERR_STATE, "forward before voxelise");
     const scatman_config &c = h->cfg;
@@ -741,6 +743,7 @@ int scatman_acquire(scatman_handle *h, const scatman_shape *shape, void *I_host)
 }
 
 int scatman_acquire_batch(scatman_handle *h, const scatman_shape *shapes, int n, void *const *I_host) {
+    const StageRange nvtx_range("scatman_acquire_batch");
     if (!h || (n > 0 && (!shapes || !I_host))) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
     if (n < 0) return set_error(h, SCATMAN_ERR_ARG, "n must be >= 0");
     for (int i = 0; i < n; ++i)
@@ -986,6 +989,7 @@ static int plan_adjoint(scatman_handle *h) {
 }
 
 int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams) {
+    const StageRange nvtx_range("scatman_backward");
     if (!h || !dLdI_dev || !dLdparams) return set_error(h, SCATMAN_ERR_ARG, "NULL argument");
     if (!h->have_forward) return set_error(h, SCATMAN_ERR_STATE, "backward before forward");
     if (is_map_kind(h->sp.kind))

@@ -12,9 +12,20 @@
 
 #include "../../include/scatman.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace scm {
 
 constexpr double kPi = 3.14159265358979323846;
+
+// An NVTX range around a stage of the host API (visible in Nsight timelines;
+// a no-op unless a profiling tool is attached).
+struct StageRange {
+    explicit StageRange(const char *name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange &) = delete;
+    StageRange &operator=(const StageRange &) = delete;
+};
 
 // Device allocation used by every buffer of the library; a test hook
 // (scatman_debug_fail_allocation) can make one of them fail on the host.

@@ -158,6 +158,7 @@ static int create_cached(const scatman_server_config &scfg, Slot &s, const Req &
 
 // Runs one request on the slot's stream with handle `c`; returns the status.
 static int run_request(const scatman_server_config &scfg, Slot &s, Req &r, Cached &c) {
+    const StageRange nvtx_range("server request");
     const bool f64 = scfg.precision == SCATMAN_FP64;
     scatman_handle *h = c.h;
     // a cached handle may come from another slot: its work is finished, and

@@ -65,6 +65,27 @@ def test_gradient_vs_oracle_small(kind, prec):
     assert err < GTOL[prec], (kind, prec, err)
 
 
+@pytest.mark.parametrize("prec", ["tc_f16_split", "tc_bf16_split"])
+@pytest.mark.parametrize("nz", [5, 40])
+def test_tensor_core_adjoint_slice_and_order_forms(nz, prec):
+    """The tensor-core adjoint runs one GEMM per slice when the Jacobi-Anger
+    expansion of e^{i q_z z} would need as many orders as there are slices
+    (nz = 5 here), and N < nz order GEMMs otherwise (nz = 40: about 18 orders
+    at this q_z range); both forms against the oracle's FP64 gradient."""
+    g = Geometry(22, 20, nz, 1.0, 5.0, 45.0, 28, 24)
+    rng = np.random.default_rng(40 + nz)
+    s = Shape(SPHHARM, R0=min(6.5, 0.4 * nz), lmax=4, alm=random_alm(rng, 4, 0.08), delta=0.03, beta=0.004,
+              latitude=15, longitude=-30, rotation=80)
+    width = 0.6
+    t = perturbed(s, np.random.default_rng(200 + nz), rel=0.05)
+    target = oracle.forward(t, g, soft=True, width=width)[0]
+    I, A = oracle.forward(s, g, soft=True, width=width)
+    _, got, I_gpu = _gpu_grad(g, s, target, prec, width)
+    ref = oracle.gradient(s, g, 2 * (I_gpu - target), A, width=width)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < GTOL[prec], (nz, prec, err)
+
+
 def test_gradient_fp64_matches_central_differences_of_the_gpu_forward():
     """Directional derivative along a random direction, from the GPU's own forward."""
     g = Geometry(18, 18, 18, 1.0, 5.0, 45.0, 20, 20)
