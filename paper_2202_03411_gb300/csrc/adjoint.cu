@@ -208,7 +208,9 @@ __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridPara
         }
     }
     const R inv_w = sizeof(R) == 4 ? (R)sp.inv_w_f : (R)sp.inv_w;
-    chi = (R)1 / ((R)1 + exp(-(rs - rr) * inv_w));
+    const R t = (rs - rr) * inv_w;
+    // the forward's FP32 cut (soft_zero): chi = 0 there, and so is its derivative
+    chi = (sizeof(R) == 4 && soft_zero((float)t)) ? (R)0 : (R)1 / ((R)1 + exp(-t));
 }
 
 // kRun: voxels per lane along z (nz <= 32 kRun), a compile-time bound so the

@@ -95,6 +95,35 @@ def test_soft_occupancy(prec, tol):
         np.testing.assert_allclose(chi, ref, atol=max(tol, 1e-7))   # chi is stored as float
 
 
+
+@pytest.mark.parametrize("prec", ["fp32", "tc_f16_split", "tc_bf16_split"])
+def test_soft_occupancy_cut(prec):
+    """FP32 and tensor-core modes zero a soft voxel whose logistic is below
+    2^-24 (the exact oracle keeps it): voxels the oracle puts clearly below the
+    cut are exactly zero, the rest match it, the contraction skips the empty
+    chunks, and I still matches the uncut oracle within the mode's tolerance."""
+    import paper_2202_03411_gb300 as sm
+    g = Geometry(64, 64, 64, 1.0, 8.0, 45.0, 40, 40)
+    rng = np.random.default_rng(11)
+    cut = 2.0 ** -24
+    for s in [Shape(SPHHARM, R0=18.0, lmax=6, alm=random_alm(rng, 6), delta=0.01, beta=0.001, latitude=30,
+                    longitude=-60, rotation=40),
+              Shape(SPHERE, r=15.2, delta=0.02, beta=0.004, cx=2.3)]:
+        I, _, h = run_gpu(g, s, prec, soft=True, width=0.5, want_A=True)
+        sm.scatman_voxelise(h, s)
+        chi = sm.scatman_get_occupancy(h, (g.nz, g.nx, g.ny))
+        issued, dense = sm.scatman_contraction_flops(h)
+        h.close()
+        ref, _ = oracle.voxelise(s, g, soft=True, width=0.5)
+        below, above = ref < 0.5 * cut, ref > 2.0 * cut
+        assert below.sum() > 0 and np.all(chi[below] == 0.0)
+        np.testing.assert_allclose(chi[above], ref[above], atol=2e-6)
+        assert np.all(chi[~(below | above)] <= 2.1 * cut)
+        Ir, _ = oracle_field(g, s, soft=True, width=0.5)
+        assert rel_l2(I, Ir) < TOL[prec], (s.kind, rel_l2(I, Ir))
+        if prec != "fp32":
+            assert 0 < issued < 0.7 * dense, issued / dense
+
 # ---- a3: transmission scan ----------------------------------------------------------
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
