@@ -216,15 +216,20 @@ __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridPara
 // kRun: voxels per lane along z (nz <= 32 kRun), a compile-time bound so the
 // per-lane runs stay in registers.
 template <typename R, int kRun>
-__global__ void __launch_bounds__(kGradThreads, 2) grad_voxel_kernel(ShapeParams sp, GridParams gp,
+__global__ void __launch_bounds__(kGradThreads, sizeof(R) == 4 ? 3 : 2) grad_voxel_kernel(ShapeParams sp, GridParams gp,
                                                                   const typename Cx<R>::T *__restrict__ S,
                                                                   double *__restrict__ partials) {
     using C = typename Cx<R>::T;
     const int ng = n_geom_params(sp.kind, sp.lmax);
     // Sphere / ellipsoid parameters and the harmonics' R0 accumulate per
-    // thread (acc[0..2]); the harmonics' a_lm (index j = l^2 + l + m - 1)
-    // accumulate warp-summed, coefficient j held by lane j % 32 in slot j / 32,
-    // so no per-thread array of (lmax + 1)^2 sums is needed.
+    // thread (acc[0..2]).  The harmonics' a_lm (index j = l^2 + l + m - 1):
+    // FP32 keeps one running sum per lane and coefficient in shared memory
+    // (s_alm[warp][j][lane], consecutive lanes in consecutive banks), so a
+    // voxel adds with one read-modify-write per coefficient and the lanes are
+    // summed once, at the end; FP64 sums each term over the warp right away,
+    // coefficient j held by lane j % 32 in slot j / 32.
+    constexpr bool kSmemAlm = sizeof(R) == 4;
+    extern __shared__ float s_alm[];
     R acc[3] = {(R)0, (R)0, (R)0};
     R aw[kGradWarpSlots];
 #pragma unroll
@@ -233,6 +238,9 @@ __global__ void __launch_bounds__(kGradThreads, 2) grad_voxel_kernel(ShapeParams
     C D;
     D.x = D.y = (R)0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *my_alm = s_alm + (size_t)warp * (ng - 1) * 32;
+    if (kSmemAlm && sh)
+        for (int j = 0; j < ng - 1; ++j) my_alm[j * 32 + lane] = 0.f;
     const int nz = gp.nz, run = (nz + 31) / 32;
     // c = n^2 - 1 and n - 1 for n = 1 - delta + i beta
     const double d = gp.delta, b = gp.beta;
@@ -352,19 +360,23 @@ __global__ void __launch_bounds__(kGradThreads, 2) grad_voxel_kernel(ShapeParams
                 }
             }
             // d radius / d a_lm = R0 Y_lm: every lane evaluates its direction (w0 = 0
-            // where the voxel does not contribute) and the warp sums each term
+            // where the voxel does not contribute)
             if (sh && __any_sync(0xffffffffu, w0 != (R)0)) {
                 const ShTab<R> tb(sp);
                 real_sh_all<R>(tb, sp.lmax, ct, st, cph, sph, [&](int idx, R y) {
                     if (idx == 0) return;
-                    R v = w0 * y;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                     const int j = idx - 1;
-                    if (lane == (j & 31)) {
+                    if constexpr (kSmemAlm) {
+                        my_alm[j * 32 + lane] += w0 * y;
+                    } else {
+                        R v = w0 * y;
 #pragma unroll
-                        for (int q = 0; q < kGradWarpSlots; ++q)
-                            if (q == (j >> 5)) aw[q] += v;
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        if (lane == (j & 31)) {
+#pragma unroll
+                            for (int q = 0; q < kGradWarpSlots; ++q)
+                                if (q == (j >> 5)) aw[q] += v;
+                        }
                     }
                 });
             }
@@ -381,7 +393,17 @@ __global__ void __launch_bounds__(kGradThreads, 2) grad_voxel_kernel(ShapeParams
         const int at = k < n_thread ? (sh ? ng - 1 : k) : ng + (k - n_thread);
         if (lane == 0) red[warp][at] = v;
     }
-    if (sh) {
+    if (sh && kSmemAlm) {
+        // lane sums of coefficient j, added in the fixed order t = 0..31 over
+        // lanes (j + t) % 32 (the rotation keeps the 32 reading lanes in 32 banks)
+        __syncwarp();
+        for (int j = lane; j < ng - 1; j += 32) {
+            float v = 0.f;
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) v += my_alm[j * 32 + ((j + t) & 31)];
+            red[warp][j] = (double)v;
+        }
+    } else if (sh) {
         // a_lm sums are already warp totals
 #pragma unroll
         for (int q = 0; q < kGradWarpSlots; ++q) {
@@ -395,6 +417,24 @@ __global__ void __launch_bounds__(kGradThreads, 2) grad_voxel_kernel(ShapeParams
         for (int w = 0; w < kGradThreads / 32; ++w) s += red[w][k];
         partials[(size_t)blockIdx.x * (ng + 2) + k] = s;
     }
+}
+
+// Dynamic shared memory of the FP32 voxel gradient: the harmonics' per-lane
+// a_lm sums (8 warps x ((lmax + 1)^2 - 1) x 32 floats; 172 KB at lmax 12).
+static size_t grad_voxel_smem(const ShapeParams &sp) {
+    if (sp.kind != SCATMAN_SPHHARM) return 0;
+    return (size_t)(kGradThreads / 32) * (size_t)(n_geom_params(sp.kind, sp.lmax) - 1) * 32 * sizeof(float);
+}
+
+template <int kRun>
+static cudaError_t launch_grad_voxels_f32(const ShapeParams &sp, const GridParams &gp, const float2 *S,
+                                          double *partials, int n_blocks, cudaStream_t st) {
+    const size_t smem = grad_voxel_smem(sp);
+    cudaError_t e = cudaFuncSetAttribute(grad_voxel_kernel<float, kRun>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    grad_voxel_kernel<float, kRun><<<n_blocks, kGradThreads, smem, st>>>(sp, gp, S, partials);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_grad_voxels(bool fp64, const ShapeParams &sp, const GridParams &gp, const void *S,
@@ -411,18 +451,13 @@ cudaError_t launch_grad_voxels(bool fp64, const ShapeParams &sp, const GridParam
             grad_voxel_kernel<double, 8><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
         else
             grad_voxel_kernel<double, 16><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
-    } else {
-        const float2 *Sf = (const float2 *)S;
-        if (run <= 2)
-            grad_voxel_kernel<float, 2><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
-        else if (run <= 4)
-            grad_voxel_kernel<float, 4><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
-        else if (run <= 8)
-            grad_voxel_kernel<float, 8><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
-        else
-            grad_voxel_kernel<float, 16><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sf, partials);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    const float2 *Sf = (const float2 *)S;
+    if (run <= 2) return launch_grad_voxels_f32<2>(sp, gp, Sf, partials, n_blocks, st);
+    if (run <= 4) return launch_grad_voxels_f32<4>(sp, gp, Sf, partials, n_blocks, st);
+    if (run <= 8) return launch_grad_voxels_f32<8>(sp, gp, Sf, partials, n_blocks, st);
+    return launch_grad_voxels_f32<16>(sp, gp, Sf, partials, n_blocks, st);
 }
 
 // sum_q w_q |A_q|^2 per block.

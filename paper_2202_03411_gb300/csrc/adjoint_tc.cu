@@ -479,16 +479,21 @@ cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab
 }
 
 // Order mode: S[j][x][y] = sum_n coef[j][n] S~[n][x][y], summed in order n = 0, 1, ...
-// One thread per (x, y) column keeps its N order values in registers.
+// A thread holds one (x, y) column's N order values in registers and forms
+// kAdjCombineZ consecutive slices of it; blockIdx.y picks the slice group, so
+// a 96^2 x 96 grid runs 12 x 72 blocks instead of 72 threads' worth of work
+// per SM.
+constexpr int kAdjCombineZ = 8;
 template <int kMaxN>
 __global__ void adj_orders_combine_kernel(const float2 *__restrict__ Sord, const float2 *__restrict__ coef, int N,
                                           int nz, long long nxy, float2 *__restrict__ S) {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nxy) return;
+    const int j0 = blockIdx.y * kAdjCombineZ, j1 = min(nz, j0 + kAdjCombineZ);
     float2 v[kMaxN];
 #pragma unroll
     for (int n = 0; n < kMaxN; ++n) v[n] = n < N ? Sord[(size_t)n * nxy + c] : make_float2(0.f, 0.f);
-    for (int j = 0; j < nz; ++j) {
+    for (int j = j0; j < j1; ++j) {
         const float2 *a = coef + (size_t)j * N;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -506,7 +511,7 @@ __global__ void adj_orders_combine_kernel(const float2 *__restrict__ Sord, const
 cudaError_t launch_adj_orders_combine(const float2 *Sord, const float2 *coef, int N, int nz, int nx, int ny, float2 *S,
                                       cudaStream_t st) {
     const long long nxy = (long long)nx * ny;
-    const unsigned blocks = (unsigned)((nxy + 127) / 128);
+    const dim3 blocks((unsigned)((nxy + 127) / 128), (unsigned)((nz + kAdjCombineZ - 1) / kAdjCombineZ));
     if (N <= 16)
         adj_orders_combine_kernel<16><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
     else if (N <= 32)
