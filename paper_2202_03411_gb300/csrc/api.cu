@@ -422,9 +422,9 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
 // |sum_m a_lm Y_lm| <= |a_l| sqrt((2l+1)/(4 pi)) (Cauchy-Schwarz with the
 // addition theorem sum_m Y_lm^2 = (2l+1)/(4 pi)), then the clip; radii map:
 // the interpolation stays within the samples' range.
-static void set_radius_band(const scatman_shape *s, ShapeParams *sp) {
+static void set_radius_band(const scatman_shape *s, ShapeParams *sp, bool fp64) {
     sp->band_lo = sp->band_hi = 0.f;
-    if (sp->soft) return;
+    if (sp->soft && fp64) return;   // FP64 soft occupancy: the exact logistic at every voxel
     double lo = 0.0, hi = 0.0;
     if (s->kind == SCATMAN_SPHHARM) {
         double b = 0.0;
@@ -441,12 +441,25 @@ static void set_radius_band(const scatman_shape *s, ShapeParams *sp) {
             lo = std::fmin(lo, s->radial_map[k]);
             hi = std::fmax(hi, s->radial_map[k]);
         }
+    } else if (sp->soft && s->kind == SCATMAN_SPHERE) {
+        lo = hi = s->r;                 // binary spheres and ellipsoids decide cheaply without it
+    } else if (sp->soft && s->kind == SCATMAN_ELLIPSOID) {
+        lo = std::fmin(s->a, std::fmin(s->b, s->c));   // the radius along any direction
+        hi = std::fmax(s->a, std::fmax(s->b, s->c));
     } else {
         return;
     }
     // widen by a relative 1e-6 so the FP64 rounding of the radius stays inside
-    sp->band_lo = (float)(lo * (1.0 - 1e-6) - 1e-9);
-    sp->band_hi = (float)(hi * (1.0 + 1e-6) + 1e-9);
+    double blo = lo * (1.0 - 1e-6) - 1e-9, bhi = hi * (1.0 + 1e-6) + 1e-9;
+    if (sp->soft) {
+        // FP32 soft occupancy: chi is exactly 1.0f where t = (r_s - |p|) / w > kSoftOneT
+        // and zero (the cut) where t < -kSoftCutT; 1e-3 w covers the FP32 rounding of t
+        const double w = 1.0 / sp->inv_w;
+        blo -= (double)kSoftOneT * w;
+        bhi += ((double)kSoftCutT + 1e-3) * w;
+    }
+    sp->band_lo = (float)blo;
+    sp->band_hi = (float)bhi;
     if (!(sp->band_hi > 0.f)) sp->band_lo = sp->band_hi = 0.f;
 }
 
@@ -612,7 +625,7 @@ int scatman_voxelise(scatman_handle *h, const scatman_shape *s) {
     finish_shape_params(&sp);
     int rc = upload_maps(h, s, &sp);
     if (rc) return rc;
-    set_radius_band(s, &sp);
+    set_radius_band(s, &sp, h->precision == SCATMAN_FP64);
 
     const GridParams gp = make_grid(c.nx, c.ny, c.nz, c.voxel, h->k0, s->delta, s->beta);
     SliceOut so;
@@ -1221,7 +1234,7 @@ extern "C" int scatman_forward_noalloc(const scatman_config *cfg, const scatman_
     if (s->kind == SCATMAN_SPHHARM && s->lmax > 0)        // alm may be NULL at lmax = 0
         for (int k = 0; k < (s->lmax + 1) * (s->lmax + 1); ++k) sp.alm[k] = s->alm[k];
     finish_shape_params(&sp);
-    set_radius_band(s, &sp);
+    set_radius_band(s, &sp, false);   // CUDA-core FP32 path
     const GridParams gp = make_grid(c.nx, c.ny, c.nz, c.voxel, k0, s->delta, s->beta);
     SliceOut so;
     so.layout = kLayoutC32;

@@ -93,10 +93,17 @@ struct ShapeParams {
     const double *mdelta, *mbeta;   // per-cell index, or null
     int varn;                       // 1: voxel-resolved index (s carries (n_v^2 - 1) / nscale)
     double nscale;                  // max |n_v^2 - 1| over the map's cells
-    // binary harmonics / radii map: the surface radius lies in [band_lo, band_hi]
-    // for every direction (band_hi = 0: no band)
+    // harmonics / radii map (and soft spheres / ellipsoids): a voxel centre with
+    // |p| below band_lo is inside (soft: chi = 1), above band_hi outside
+    // (chi = 0) (band_hi = 0: no band)
     float band_lo, band_hi;
 };
+
+// Soft occupancy cut of the FP32 modes: chi = 1 / (1 + e^{-t}) with
+// t = (r_s - |p|) / w is taken as zero when chi < 2^-24, i.e. t < -kSoftCutT.
+constexpr float kSoftCutT = 16.635532f;   // ln(2^24 - 1)
+// Above this t the FP32 logistic is exactly 1.0f (e^{-t} below half an ulp of 1).
+constexpr float kSoftOneT = 17.5f;
 
 // Fills the FP32 copies and the harmonic recurrence tables of a ShapeParams
 // whose double fields are set (api.cu).

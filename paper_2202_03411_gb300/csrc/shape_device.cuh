@@ -257,15 +257,12 @@ __device__ __forceinline__ int vmap_cell(const ShapeParams &sp, const GridParams
 // kinds' instantiation carries none of their code.
 // kDefer (FP32 modes): a binary voxel the FP32 test cannot settle returns -1
 // instead of taking the FP64 path here, so the caller can batch those voxels.
-// Soft occupancy cut of the FP32 modes: chi = 1 / (1 + e^{-t}) with
-// t = (r_s - |p|) / w is taken as zero when chi < 2^-24, i.e. t < -ln(2^24 - 1).
-// Without the cut every voxel of the grid has chi > 0 (the logistic never
+// Soft occupancy cut of the FP32 modes (kSoftCutT): without the cut every voxel of the grid has chi > 0 (the logistic never
 // vanishes) and the contraction cannot skip the empty part of a slice.  The
 // dropped voxels change the field by at most |n^2 - 1| times their summed
 // occupancy (each below 2^-24; 3e-9 to 4e-9 of the total occupancy for
 // 128^3 shapes at w = 0.5 voxel), and the gradient applies the same cut, so
 // it stays the derivative of the function the forward computes.
-constexpr float kSoftCutT = 16.635532f;   // ln(2^24 - 1)
 __device__ __forceinline__ bool soft_zero(float t) { return t < -kSoftCutT; }
 
 template <bool kFp64, bool kMaps = false, bool kDefer = false,

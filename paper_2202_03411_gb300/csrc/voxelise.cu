@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
     const bool varn = kMaps && sp.varn != 0;                      // per-cell index of a volume map
     const ScanT kdz = vc_pick<ScanT>(vc.kdz, vc.kdz_f);
     const Re inv_scale = vc_pick<Re>(vc.inv_scale, vc.inv_scale_f);
-    // radius band of a binary harmonics or radii-map shape: inside below lo, outside above hi
-    const bool band = !sp.soft && sp.band_hi > 0.f;
+    // radius band (harmonics, radii maps, soft spheres and ellipsoids): inside below lo, outside above hi
+    // (the host sets none for FP64 soft occupancy)
+    const bool band = (!kFp64 || !sp.soft) && sp.band_hi > 0.f;
     const float vox = gp.voxf;
     const float xo = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
 
