@@ -141,17 +141,12 @@ constexpr int kGradMaxRun = 16;
 constexpr int kMaxGeom = (SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 1);
 constexpr int kGradWarpSlots = (kMaxGeom + 31) / 32;
 
-int grad_voxel_blocks(const GridParams &gp) {
-    long long cols = (long long)gp.nx * gp.ny;
-    long long b = (cols + (kGradThreads / 32) - 1) / (kGradThreads / 32);
-    return (int)(b < 608 ? b : 608);
-}
-
 // Soft occupancy of one voxel with its surface radius and clip state: the
 // forward voxeliser's soft branch in FP64; in FP32 with FP32 body coordinates
 // (the occupancy is smooth, so this moves chi by ~1e-7, far inside the FP32
 // gradient's tolerance, and keeps FP64 off the per-voxel path).
-template <typename R>
+// kMaxL: compile-time bound on the harmonics' degree (sp.lmax <= kMaxL).
+template <typename R, int kMaxL>
 __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz, R &chi,
                                            R &rs, int &clip, R &ux, R &uy, R &uz) {
     R px, py, pz;
@@ -197,7 +192,7 @@ __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridPara
         rs = (R)1 / sqrt(ux * ux * ia * ia + uy * uy * ib * ib + uz * uz * ic * ic);
     } else {
         const ShTab<R> tb(sp);
-        R raw = sh_radius_unclipped<R>(sp, px, py, pz, rr);
+        R raw = sh_radius_unclipped<R, kMaxL>(sp, px, py, pz, rr);
         rs = raw;
         if (raw < tb.rmin) {
             rs = tb.rmin;
@@ -214,8 +209,9 @@ __device__ __forceinline__ void soft_voxel(const ShapeParams &sp, const GridPara
 }
 
 // kRun: voxels per lane along z (nz <= 32 kRun), a compile-time bound so the
-// per-lane runs stay in registers.
-template <typename R, int kRun>
+// per-lane runs stay in registers.  kMaxL: bound on the harmonics' degree, so
+// shapes of low degree run a kernel whose unrolled harmonic code is short.
+template <typename R, int kRun, int kMaxL>
 __global__ void __launch_bounds__(kGradThreads, sizeof(R) == 4 ? 3 : 2) grad_voxel_kernel(ShapeParams sp, GridParams gp,
                                                                   const typename Cx<R>::T *__restrict__ S,
                                                                   double *__restrict__ partials) {
@@ -268,7 +264,8 @@ __global__ void __launch_bounds__(kGradThreads, sizeof(R) == 4 ? 3 : 2) grad_vox
         for (int k = 0; k < kRun; ++k) {
             const int iz = lane * run + k;
             chi[k] = (R)0;
-            if (k < run && iz < nz) soft_voxel<R>(sp, gp, ix, iy, iz, chi[k], rs[k], clip[k], ux[k], uy[k], uz[k]);
+            if (k < run && iz < nz)
+                soft_voxel<R, kMaxL>(sp, gp, ix, iy, iz, chi[k], rs[k], clip[k], ux[k], uy[k], uz[k]);
             local += chi[k];
         }
         R incl = local;
@@ -363,7 +360,7 @@ __global__ void __launch_bounds__(kGradThreads, sizeof(R) == 4 ? 3 : 2) grad_vox
             // where the voxel does not contribute)
             if (sh && __any_sync(0xffffffffu, w0 != (R)0)) {
                 const ShTab<R> tb(sp);
-                real_sh_all<R>(tb, sp.lmax, ct, st, cph, sph, [&](int idx, R y) {
+                real_sh_all<R, kMaxL>(tb, sp.lmax, ct, st, cph, sph, [&](int idx, R y) {
                     if (idx == 0) return;
                     const int j = idx - 1;
                     if constexpr (kSmemAlm) {
@@ -426,38 +423,64 @@ static size_t grad_voxel_smem(const ShapeParams &sp) {
     return (size_t)(kGradThreads / 32) * (size_t)(n_geom_params(sp.kind, sp.lmax) - 1) * 32 * sizeof(float);
 }
 
-template <int kRun>
-static cudaError_t launch_grad_voxels_f32(const ShapeParams &sp, const GridParams &gp, const float2 *S,
-                                          double *partials, int n_blocks, cudaStream_t st) {
-    const size_t smem = grad_voxel_smem(sp);
-    cudaError_t e = cudaFuncSetAttribute(grad_voxel_kernel<float, kRun>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    grad_voxel_kernel<float, kRun><<<n_blocks, kGradThreads, smem, st>>>(sp, gp, S, partials);
-    return cudaGetLastError();
+template <typename R>
+using GradVoxelFn = void (*)(ShapeParams, GridParams, const typename Cx<R>::T *, double *);
+
+// The instantiation for this shape and grid: z run per lane from nz, and the
+// short harmonic code (degree <= 6) for FP32 shapes that need no more.
+template <typename R, int kMaxL>
+static GradVoxelFn<R> grad_voxel_fn_l(int run) {
+    if (run <= 2) return grad_voxel_kernel<R, 2, kMaxL>;
+    if (run <= 4) return grad_voxel_kernel<R, 4, kMaxL>;
+    if (run <= 8) return grad_voxel_kernel<R, 8, kMaxL>;
+    return grad_voxel_kernel<R, 16, kMaxL>;
+}
+
+template <typename R>
+static GradVoxelFn<R> grad_voxel_fn(const ShapeParams &sp, const GridParams &gp) {
+    const int run = (gp.nz + 31) / 32;
+    if (sizeof(R) == 8 || (sp.kind == SCATMAN_SPHHARM && sp.lmax > 6))
+        return grad_voxel_fn_l<R, SCATMAN_MAX_LMAX>(run);
+    return grad_voxel_fn_l<R, 6>(run);
+}
+
+// Blocks of the voxel gradient: one per 8 columns, at most the resident count
+// of the instantiation that runs (whole waves), and never above 608 (the
+// serving footprint's bound on the partial sums).
+int grad_voxel_blocks(bool fp64, const ShapeParams &sp, const GridParams &gp, int sm_count) {
+    const long long cols = (long long)gp.nx * gp.ny;
+    const long long b = (cols + (kGradThreads / 32) - 1) / (kGradThreads / 32);
+    int per_sm = 0;
+    if (fp64) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grad_voxel_fn<double>(sp, gp), kGradThreads, 0) !=
+            cudaSuccess)
+            per_sm = 1;
+    } else {
+        const auto fn = grad_voxel_fn<float>(sp, gp);
+        const size_t smem = grad_voxel_smem(sp);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGradThreads, smem) != cudaSuccess)
+            per_sm = 1;
+    }
+    (void)cudaGetLastError();
+    long long cap = (long long)(sm_count > 0 ? sm_count : 1) * (per_sm > 0 ? per_sm : 1);
+    if (cap > 608) cap = 608;
+    return (int)(b < cap ? b : cap);
 }
 
 cudaError_t launch_grad_voxels(bool fp64, const ShapeParams &sp, const GridParams &gp, const void *S,
                                double *partials, int n_blocks, cudaStream_t st) {
     if (gp.nz > 32 * kGradMaxRun) return cudaErrorInvalidValue;
-    const int run = (gp.nz + 31) / 32;
     if (fp64) {
-        const double2 *Sd = (const double2 *)S;
-        if (run <= 2)
-            grad_voxel_kernel<double, 2><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
-        else if (run <= 4)
-            grad_voxel_kernel<double, 4><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
-        else if (run <= 8)
-            grad_voxel_kernel<double, 8><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
-        else
-            grad_voxel_kernel<double, 16><<<n_blocks, kGradThreads, 0, st>>>(sp, gp, Sd, partials);
+        grad_voxel_fn<double>(sp, gp)<<<n_blocks, kGradThreads, 0, st>>>(sp, gp, (const double2 *)S, partials);
         return cudaGetLastError();
     }
-    const float2 *Sf = (const float2 *)S;
-    if (run <= 2) return launch_grad_voxels_f32<2>(sp, gp, Sf, partials, n_blocks, st);
-    if (run <= 4) return launch_grad_voxels_f32<4>(sp, gp, Sf, partials, n_blocks, st);
-    if (run <= 8) return launch_grad_voxels_f32<8>(sp, gp, Sf, partials, n_blocks, st);
-    return launch_grad_voxels_f32<16>(sp, gp, Sf, partials, n_blocks, st);
+    const auto fn = grad_voxel_fn<float>(sp, gp);
+    const size_t smem = grad_voxel_smem(sp);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<n_blocks, kGradThreads, smem, st>>>(sp, gp, (const float2 *)S, partials);
+    return cudaGetLastError();
 }
 
 // sum_q w_q |A_q|^2 per block.

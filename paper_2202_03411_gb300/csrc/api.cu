@@ -1017,7 +1017,7 @@ int scatman_backward(scatman_handle *h, const void *dLdI_dev, double *dLdparams)
     }
     const GridParams gp = make_grid(c.nx, c.ny, c.nz, c.voxel, h->k0, h->shape.delta, h->shape.beta);
     const int ng = grad_param_count(h->sp);
-    const int nvb = grad_voxel_blocks(gp), npb = grad_pixel_blocks(h->n_pix);
+    const int nvb = grad_voxel_blocks(f64, h->sp, gp, h->sm_count), npb = grad_pixel_blocks(h->n_pix);
     const size_t need = (size_t)nvb * (ng + 2) + (size_t)npb;
     if (h->part_count < need) {
         cudaFree(h->d_part);

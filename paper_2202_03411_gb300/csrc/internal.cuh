@@ -330,7 +330,7 @@ cudaError_t launch_adjoint_field(bool fp64, const void *A, const void *dLdI, con
 int grad_param_count(const ShapeParams &sp);
 cudaError_t launch_grad_voxels(bool fp64, const ShapeParams &sp, const GridParams &gp, const void *S,
                                double *partials, int n_blocks, cudaStream_t st);
-int grad_voxel_blocks(const GridParams &gp);
+int grad_voxel_blocks(bool fp64, const ShapeParams &sp, const GridParams &gp, int sm_count);
 cudaError_t launch_grad_pixels(bool fp64, const void *A, const void *dLdI, long long n_pix,
                                double *partials, int n_blocks, cudaStream_t st);
 int grad_pixel_blocks(long long n_pix);

@@ -37,14 +37,16 @@ template <> struct ShTab<double> {
 // every table index and callback index is a compile-time constant (the
 // coefficients become constant-bank operands) while the arithmetic and its
 // order are those of the plain loops.
-template <typename T, typename F>
+// kMaxL: compile-time bound on L (the unrolled code covers degrees up to it).
+template <typename T, int kMaxL = SCATMAN_MAX_LMAX, typename F>
 __device__ __forceinline__ void real_sh_all(const ShTab<T> &tb, int L, T ct, T st, T cphi, T sphi, F &&f) {
+    static_assert(kMaxL >= 0 && kMaxL <= SCATMAN_MAX_LMAX, "degree bound");
     const T kInvSqrt4Pi = (T)0.28209479177387814347;
     const T kSqrt2 = (T)1.41421356237309504880;
     T pmm = kInvSqrt4Pi;
     T cm = (T)1, sm = (T)0;
 #pragma unroll
-    for (int m = 0; m <= SCATMAN_MAX_LMAX; ++m) {
+    for (int m = 0; m <= kMaxL; ++m) {
         if (m > L) break;
         if (m > 0) {
             pmm = tb.d[m] * st * pmm;
@@ -57,7 +59,7 @@ __device__ __forceinline__ void real_sh_all(const ShTab<T> &tb, int L, T ct, T s
         const T ws = kSqrt2 * sm;
         T p2 = (T)0, p1 = pmm;
 #pragma unroll
-        for (int l = m; l <= SCATMAN_MAX_LMAX; ++l) {
+        for (int l = m; l <= kMaxL; ++l) {
             if (l > L) break;
             T p;
             if (l == m) {
@@ -84,7 +86,7 @@ __device__ __forceinline__ void real_sh_all(const ShTab<T> &tb, int L, T ct, T s
 
 // Harmonics surface radius R0 (1 + sum a_lm Y_lm) along body direction p
 // (not normalised), |p| = rr, before clipping.
-template <typename T>
+template <typename T, int kMaxL = SCATMAN_MAX_LMAX>
 __device__ __forceinline__ T sh_radius_unclipped(const ShapeParams &sp, T px, T py, T pz, T rr) {
     const ShTab<T> tb(sp);
     T ct = (T)1, st = (T)0, cphi = (T)1, sphi = (T)0;
@@ -98,7 +100,7 @@ __device__ __forceinline__ T sh_radius_unclipped(const ShapeParams &sp, T px, T 
         }
     }
     T sum = (T)0;
-    real_sh_all<T>(tb, sp.lmax, ct, st, cphi, sphi, [&](int idx, T y) {
+    real_sh_all<T, kMaxL>(tb, sp.lmax, ct, st, cphi, sphi, [&](int idx, T y) {
         if (idx > 0) sum += tb.alm[idx] * y;
     });
     return tb.R0 * ((T)1 + sum);

@@ -86,6 +86,27 @@ def test_tensor_core_adjoint_slice_and_order_forms(nz, prec):
     assert err < GTOL[prec], (nz, prec, err)
 
 
+
+@pytest.mark.parametrize("prec", ["fp32", "tc_bf16_split"])
+@pytest.mark.parametrize("lmax", [6, 10, 12])
+def test_gradient_harmonic_degrees(lmax, prec):
+    """The FP32 voxel gradient runs a short kernel for degree <= 6 and the full
+    one (per-lane a_lm sums in up to 172 KB of shared memory) above; every
+    d L / d a_lm of degrees 6, 10 and 12 against the oracle's FP64 gradient."""
+    g = Geometry(24, 22, 26, 1.0, 5.0, 45.0, 30, 28)
+    rng = np.random.default_rng(60 + lmax)
+    s = Shape(SPHHARM, R0=7.0, lmax=lmax, alm=random_alm(rng, lmax, 0.03), delta=0.03, beta=0.004,
+              latitude=-20, longitude=50, rotation=10)
+    width = 0.6
+    t = perturbed(s, np.random.default_rng(300 + lmax), rel=0.05)
+    target = oracle.forward(t, g, soft=True, width=width)[0]
+    I, A = oracle.forward(s, g, soft=True, width=width)
+    _, got, I_gpu = _gpu_grad(g, s, target, prec, width)
+    ref = oracle.gradient(s, g, 2 * (I_gpu - target), A, width=width)
+    assert got.shape == ref.shape == ((lmax + 1) ** 2 + 2,)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < GTOL[prec], (lmax, prec, err)
+
 def test_gradient_fp64_matches_central_differences_of_the_gpu_forward():
     """Directional derivative along a random direction, from the GPU's own forward."""
     g = Geometry(18, 18, 18, 1.0, 5.0, 45.0, 20, 20)
