@@ -70,6 +70,28 @@ def test_binary_occupancy_bit_exact(prec):
             assert np.array_equal(chi, ref), (prec, s.kind, int((chi != ref).sum()))
 
 
+
+@pytest.mark.parametrize("prec", ["fp32", "tc_bf16_split"])
+@pytest.mark.parametrize("lmax", [8, 9, 12])
+def test_occupancy_harmonic_degrees(lmax, prec):
+    """Harmonics up to the largest degree: binary occupancy bit-exact and soft
+    occupancy to 2e-6 at degrees 8, 9 and 12."""
+    import paper_2202_03411_gb300 as sm
+    g = Geometry(30, 28, 26, 1.0, 8.0, 30.0, 8, 8)
+    rng = np.random.default_rng(70 + lmax)
+    s = Shape(SPHHARM, R0=8.5, lmax=lmax, alm=random_alm(rng, lmax, 0.04), delta=0.01, beta=0.001, latitude=35,
+              longitude=-15, rotation=120)
+    for soft in (False, True):
+        h = sm.scatman_create(g, prec, soft=soft, soft_width=0.6)
+        sm.scatman_voxelise(h, s)
+        chi = sm.scatman_get_occupancy(h, (g.nz, g.nx, g.ny))
+        h.close()
+        ref, _ = oracle.voxelise(s, g, soft=soft, width=0.6)
+        if soft:
+            np.testing.assert_allclose(chi, ref, atol=2e-6)
+        else:
+            assert np.array_equal(chi, ref), (lmax, int((chi != ref).sum()))
+
 def test_binary_occupancy_full_size_workloads():
     import paper_2202_03411_gb300 as sm
     for g, shapes in (ellipsoid_96(n_shapes=3), sh_128(n_shapes=2)):
