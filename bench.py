@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--serving", type=int, default=0,
                     help="run the serving mix with this many requests and print its own JSON line")
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-device-time", type=int, default=0,
+                    help="time this many requests of the serving mix one at a time on one stream and print a JSON line")
     ap.add_argument("--fit-step", type=int, default=0,
                     help="time this many forward+gradient fit steps of the 96^3 l<=6 workload and print a JSON line")
     ap.add_argument("--short-serving", type=int, default=2000,
@@ -176,6 +178,51 @@ def serving_run(n_requests, slots, precision, fractions=(0.5, 0.8, 0.95), seed=0
     out["slots_over_one_slot"] = sat / out["one_slot"]["requests_per_s"]
     return out
 
+
+
+def serving_device_time(n_requests, precision, seed=0):
+    """Device time of the serving mix's requests run one at a time on one
+    stream (no overlap): voxelise + forward, then residual + backward, CUDA
+    events around each part; one handle per geometry, created before timing,
+    each request timed on its second run.  The served rate over 1 / (mean of
+    these) says how much the server's slots overlap requests on the device."""
+    import numpy as np
+    import torch
+    import paper_2202_03411_gb300 as sm
+    from workloads import serving_mix
+    reqs = serving_mix(n_requests, rate_per_s=1.0, seed=seed)
+    targets = serving_targets(reqs, precision)
+    stream = torch.cuda.current_stream()
+    handles, rows = {}, {}
+    for r, t in zip(reqs, targets):
+        g = r.geometry
+        key = (g.nx, g.det_nx)
+        if key not in handles:
+            handles[key] = sm.scatman_create(g, precision, soft=True, soft_width=0.5)
+        h = handles[key]
+        I = torch.empty(g.n_pix, dtype=torch.float32, device="cuda")
+        tt = torch.as_tensor(t, device="cuda")
+        for rep in range(2):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            sm.scatman_voxelise(h, r.shape)
+            sm.scatman_forward(h, I)
+            ev[1].record(stream)
+            sm.scatman_backward(h, 2.0 * (I - tt))
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+        rows.setdefault(key, []).append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
+    for h in handles.values():
+        h.close()
+    per = {}
+    tot = []
+    for key in sorted(rows):
+        a = np.array(rows[key])
+        per["grid%d_det%d" % key] = {"requests": len(a), "forward_ms": float(a[:, 0].mean()),
+                                     "backward_ms": float(a[:, 1].mean())}
+        tot.extend(a.sum(1).tolist())
+    mean = float(np.mean(tot))
+    return {"requests": len(tot), "mean_ms": mean, "requests_per_s_if_serial": 1e3 / mean, "per_geometry": per}
 
 def fit_step_run(n_shapes, precision, warm=2):
     """Forward + gradient fit steps on the 96^3 / 256^2 l<=6 harmonics workload
@@ -604,6 +651,14 @@ def main():
                         reps=3)
         print(json.dumps({"metric": "MSFT ms per pattern (Fig. 8b case, uniform-q detector)", "unit": "ms",
                           "higher_is_better": False, "data": "synthetic", "fig8b": res}), flush=True)
+        return
+    if args.serving_device_time > 0:
+        import __graft_entry__
+        __graft_entry__.build()
+        res = serving_device_time(args.serving_device_time, args.precision)
+        print(json.dumps({"metric": "MSFT serving mix, device ms per request run alone", "value": res["mean_ms"],
+                          "unit": "ms", "n_gpus": 1, "higher_is_better": False, "data": "synthetic",
+                          "serving_device_time": res}), flush=True)
         return
     if args.serving > 0:
         import __graft_entry__
