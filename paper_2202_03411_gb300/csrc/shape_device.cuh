@@ -313,17 +313,17 @@ __device__ __forceinline__ OccT occupancy(const ShapeParams &sp, const GridParam
         if (kDefer && !kFp64) return (OccT)-1;
         return (OccT)occupancy_binary_fp64(sp, gp, ix, iy, iz);
     }
-    double px, py, pz;
-    if (sp.kind == SCATMAN_SPHERE) {
-        px = (ix - 0.5 * (gp.nx - 1)) * gp.voxel - sp.cx;
-        py = (iy - 0.5 * (gp.ny - 1)) * gp.voxel - sp.cy;
-        pz = (iz - 0.5 * (gp.nz - 1)) * gp.voxel - sp.cz;
-    } else {
-        body_coords(sp, gp, ix, iy, iz, px, py, pz);
-    }
-    double p2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
-    double rr = sqrt(p2);
-    if (kFp64) {
+    if constexpr (kFp64) {
+        double px, py, pz;
+        if (sp.kind == SCATMAN_SPHERE) {
+            px = (ix - 0.5 * (gp.nx - 1)) * gp.voxel - sp.cx;
+            py = (iy - 0.5 * (gp.ny - 1)) * gp.voxel - sp.cy;
+            pz = (iz - 0.5 * (gp.nz - 1)) * gp.voxel - sp.cz;
+        } else {
+            body_coords(sp, gp, ix, iy, iz, px, py, pz);
+        }
+        double p2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+        double rr = sqrt(p2);
         double rs;
         if (sp.kind == SCATMAN_SPHERE) {
             rs = sp.r;
@@ -337,23 +337,38 @@ __device__ __forceinline__ OccT occupancy(const ShapeParams &sp, const GridParam
             rs = sh_radius<double>(sp, px, py, pz, rr);
         }
         return (OccT)(1.0 / (1.0 + exp(-(rs - rr) * sp.inv_w)));
-    }
-    float rf = (float)rr, rs;
-    if (sp.kind == SCATMAN_SPHERE) {
-        rs = (float)sp.r;
-    } else if (sp.kind == SCATMAN_ELLIPSOID) {
-        float u0 = 0.f, u1 = 0.f, u2 = 1.f;
-        if (rf > 0.f) { u0 = (float)px / rf; u1 = (float)py / rf; u2 = (float)pz / rf; }
-        const float ia = sp.inv_af, ib = sp.inv_bf, ic = sp.inv_cf;
-        rs = rsqrtf(u0 * u0 * ia * ia + u1 * u1 * ib * ib + u2 * u2 * ic * ic);
-    } else if (kMaps && sp.kind == SCATMAN_RADIALMAP) {
-        rs = rmap_radius_f(sp, (float)px, (float)py, (float)pz);
     } else {
-        rs = sh_radius<float>(sp, (float)px, (float)py, (float)pz, rf);
+        // FP32 modes: FP32 body coordinates, as the gradient's voxel pass forms
+        // them (the logistic is smooth: their rounding moves chi by ~1e-6 at
+        // most, and no FP64 arithmetic runs per voxel)
+        const float vox = gp.voxf;
+        const float dx = ((float)ix - 0.5f * (float)(gp.nx - 1)) * vox - sp.cxf;
+        const float dy = ((float)iy - 0.5f * (float)(gp.ny - 1)) * vox - sp.cyf;
+        const float dz = ((float)iz - 0.5f * (float)(gp.nz - 1)) * vox - sp.czf;
+        float px = dx, py = dy, pz = dz;
+        if (sp.kind != SCATMAN_SPHERE) {
+            px = sp.Rf[0] * dx + sp.Rf[3] * dy + sp.Rf[6] * dz;
+            py = sp.Rf[1] * dx + sp.Rf[4] * dy + sp.Rf[7] * dz;
+            pz = sp.Rf[2] * dx + sp.Rf[5] * dy + sp.Rf[8] * dz;
+        }
+        const float rf = sqrtf(px * px + py * py + pz * pz);
+        float rs;
+        if (sp.kind == SCATMAN_SPHERE) {
+            rs = (float)sp.r;
+        } else if (sp.kind == SCATMAN_ELLIPSOID) {
+            float u0 = 0.f, u1 = 0.f, u2 = 1.f;
+            if (rf > 0.f) { u0 = px / rf; u1 = py / rf; u2 = pz / rf; }
+            const float ia = sp.inv_af, ib = sp.inv_bf, ic = sp.inv_cf;
+            rs = rsqrtf(u0 * u0 * ia * ia + u1 * u1 * ib * ib + u2 * u2 * ic * ic);
+        } else if (kMaps && sp.kind == SCATMAN_RADIALMAP) {
+            rs = rmap_radius_f(sp, px, py, pz);
+        } else {
+            rs = sh_radius<float>(sp, px, py, pz, rf);
+        }
+        const float t = (rs - rf) * sp.inv_w_f;
+        if (soft_zero(t)) return (OccT)0;
+        return (OccT)(1.0f / (1.0f + __expf(-t)));
     }
-    const float t = (rs - rf) * sp.inv_w_f;
-    if (soft_zero(t)) return (OccT)0;
-    return (OccT)(1.0f / (1.0f + __expf(-t)));
 }
 
 }  // namespace scm
