@@ -480,31 +480,34 @@ cudaError_t launch_adjoint_tc(const float2 *A, const float *w, const float4 *tab
 
 // Order mode: S[j][x][y] = sum_n coef[j][n] S~[n][x][y], summed in order n = 0, 1, ...
 // A thread holds one (x, y) column's N order values in registers and forms
-// kAdjCombineZ consecutive slices of it; blockIdx.y picks the slice group, so
-// a 96^2 x 96 grid runs 12 x 72 blocks instead of 72 threads' worth of work
-// per SM.
+// kAdjCombineZ consecutive slices of it from the block's coefficients, staged
+// in shared memory; blockIdx.y picks the slice group.
 constexpr int kAdjCombineZ = 8;
 template <int kMaxN>
-__global__ void adj_orders_combine_kernel(const float2 *__restrict__ Sord, const float2 *__restrict__ coef, int N,
-                                          int nz, long long nxy, float2 *__restrict__ S) {
+__global__ void __launch_bounds__(128) adj_orders_combine_kernel(const float2 *__restrict__ Sord,
+                                                                 const float2 *__restrict__ coef, int N, int nz,
+                                                                 long long nxy, float2 *__restrict__ S) {
+    __shared__ float2 s_coef[kAdjCombineZ * kMaxN];
+    const int j0 = blockIdx.y * kAdjCombineZ, nj = min(kAdjCombineZ, nz - j0);
+    for (int i = threadIdx.x; i < nj * N; i += blockDim.x) s_coef[i] = coef[(size_t)j0 * N + i];
+    __syncthreads();
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nxy) return;
-    const int j0 = blockIdx.y * kAdjCombineZ, j1 = min(nz, j0 + kAdjCombineZ);
     float2 v[kMaxN];
 #pragma unroll
     for (int n = 0; n < kMaxN; ++n) v[n] = n < N ? Sord[(size_t)n * nxy + c] : make_float2(0.f, 0.f);
-    for (int j = j0; j < j1; ++j) {
-        const float2 *a = coef + (size_t)j * N;
+    for (int jj = 0; jj < nj; ++jj) {
+        const float2 *a = s_coef + jj * N;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int n = 0; n < kMaxN; ++n) {
             if (n < N) {
-                const float2 t = __ldg(&a[n]);
+                const float2 t = a[n];
                 acc.x = fmaf(t.x, v[n].x, fmaf(-t.y, v[n].y, acc.x));
                 acc.y = fmaf(t.x, v[n].y, fmaf(t.y, v[n].x, acc.y));
             }
         }
-        S[(size_t)j * nxy + c] = acc;
+        S[(size_t)(j0 + jj) * nxy + c] = acc;
     }
 }
 
@@ -512,10 +515,15 @@ cudaError_t launch_adj_orders_combine(const float2 *Sord, const float2 *coef, in
                                       cudaStream_t st) {
     const long long nxy = (long long)nx * ny;
     const dim3 blocks((unsigned)((nxy + 127) / 128), (unsigned)((nz + kAdjCombineZ - 1) / kAdjCombineZ));
+    if (N <= 0) return cudaErrorInvalidValue;
     if (N <= 16)
         adj_orders_combine_kernel<16><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
+    else if (N <= 24)
+        adj_orders_combine_kernel<24><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
     else if (N <= 32)
         adj_orders_combine_kernel<32><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
+    else if (N <= 48)
+        adj_orders_combine_kernel<48><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
     else if (N <= 64)
         adj_orders_combine_kernel<64><<<blocks, 128, 0, st>>>(Sord, coef, N, nz, nxy, S);
     else
