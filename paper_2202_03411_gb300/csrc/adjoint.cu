@@ -439,9 +439,16 @@ static GradVoxelFn<R> grad_voxel_fn_l(int run) {
 template <typename R>
 static GradVoxelFn<R> grad_voxel_fn(const ShapeParams &sp, const GridParams &gp) {
     const int run = (gp.nz + 31) / 32;
-    if (sizeof(R) == 8 || (sp.kind == SCATMAN_SPHHARM && sp.lmax > 6))
-        return grad_voxel_fn_l<R, SCATMAN_MAX_LMAX>(run);
-    return grad_voxel_fn_l<R, 6>(run);
+    if constexpr (sizeof(R) == 8) {
+        // FP64 (the accuracy mode, nz <= 256): two instantiations keep the build
+        // short (the FP64 8-voxel form alone took minutes in ptxas); runs above
+        // 2 take the 16-voxel form, whose per-lane arrays live in local memory
+        (void)sp;
+        return run <= 2 ? grad_voxel_kernel<R, 2, SCATMAN_MAX_LMAX> : grad_voxel_kernel<R, 16, SCATMAN_MAX_LMAX>;
+    } else {
+        if (sp.kind == SCATMAN_SPHHARM && sp.lmax > 6) return grad_voxel_fn_l<R, SCATMAN_MAX_LMAX>(run);
+        return grad_voxel_fn_l<R, 6>(run);
+    }
 }
 
 // Blocks of the voxel gradient: one per 8 columns, at most the resident count

@@ -107,6 +107,23 @@ def test_gradient_harmonic_degrees(lmax, prec):
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err < GTOL[prec], (lmax, prec, err)
 
+
+def test_gradient_fp64_deep_grid():
+    """FP64 mode on 80 slices (three z per lane: the 16-per-lane form of the
+    voxel gradient) against the oracle's FP64 gradient."""
+    g = Geometry(20, 18, 80, 1.0, 5.0, 45.0, 22, 20)
+    rng = np.random.default_rng(81)
+    s = Shape(SPHHARM, R0=7.0, lmax=5, alm=random_alm(rng, 5, 0.05), delta=0.03, beta=0.004, latitude=10,
+              longitude=-70, rotation=25, cz=4.0)
+    width = 0.6
+    t = perturbed(s, np.random.default_rng(82), rel=0.05)
+    target = oracle.forward(t, g, soft=True, width=width)[0]
+    I, A = oracle.forward(s, g, soft=True, width=width)
+    _, got, I_gpu = _gpu_grad(g, s, target, "fp64", width)
+    ref = oracle.gradient(s, g, 2 * (I_gpu - target), A, width=width)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < GTOL["fp64"], err
+
 def test_gradient_fp64_matches_central_differences_of_the_gpu_forward():
     """Directional derivative along a random direction, from the GPU's own forward."""
     g = Geometry(18, 18, 18, 1.0, 5.0, 45.0, 20, 20)
