@@ -296,18 +296,30 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_tc_kernel(const AdjPar
                 const float2 ex = expmi_fs(ta.x, ta.y, -x0);
                 const float2 exs = make_float2(tb.z, tb.w);
                 if (P.orders) {
-                    // orders j0 and j0 + 1: real factors cos(j0 theta), cos((j0 + 1) theta)
-                    const float c1 = ez.x * ezs.x - ez.y * ezs.y;
-                    const float2 gx = cmul(g, ex);
-                    float2 L0 = make_float2(gx.x * ez.x, gx.y * ez.x), L1 = make_float2(gx.x * c1, gx.y * c1);
-#pragma unroll 4
-                    for (int r = r0; r < r1; ++r) {
-                        const uint32_t off = pair_offset(r, i);
-                        *reinterpret_cast<uint32_t *>(sA0 + off) = pack_half2(L0.x, L0.y);
-                        *reinterpret_cast<uint32_t *>(sA1 + off) = pack_half2(L1.x, L1.y);
-                        L0 = cmul(L0, exs);
-                        L1 = cmul(L1, exs);
+                    // orders j0 and j0 + 1: real factors c0 = cos(j0 theta), c1 = cos((j0 + 1) theta)
+                    // of one complex row value G_r = g e^{+i q_x x_r}, rotated row by row
+                    const float c0 = ez.x, c1 = ez.x * ezs.x - ez.y * ezs.y;
+                    float2 G = cmul(g, ex);
+                    auto put = [&](uint8_t *d0, uint8_t *d1) {
+                        *reinterpret_cast<uint32_t *>(d0) = pack_half2(c0 * G.x, c0 * G.y);
+                        *reinterpret_cast<uint32_t *>(d1) = pack_half2(c1 * G.x, c1 * G.y);
+                        G = cmul(G, exs);
+                    };
+                    int r = r0;
+                    for (; r < r1 && (r & 7) != 0; ++r) put(sA0 + pair_offset(r, i), sA1 + pair_offset(r, i));
+                    if (r + 8 <= r1) {
+                        // whole groups of 8 rows (one swizzle period): this lane's offsets
+                        // within a group, the group base advancing by 1 KB
+                        uint32_t o[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) o[k] = pair_offset(k, i);
+                        uint8_t *g0 = sA0 + (size_t)r * 128, *g1 = sA1 + (size_t)r * 128;
+                        for (; r + 8 <= r1; r += 8, g0 += 1024, g1 += 1024) {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) put(g0 + o[k], g1 + o[k]);
+                        }
                     }
+                    for (; r < r1; ++r) put(sA0 + pair_offset(r, i), sA1 + pair_offset(r, i));
                 } else {
                     float2 L0 = cmul(cmul(g, ez), ex);       // slice j0, row r0
 #pragma unroll 4
