@@ -194,15 +194,18 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
                 carry_d += __shfl_sync(0xffffffffu, id, 31);
                 carry_b += __shfl_sync(0xffffffffu, ib, 31);
                 if (iz < nz) {
-                    const ScanT mag = exp(-kdz * Cb);
-                    ScanT sn, cs;
-                    sincos(kdz * Cd, &sn, &cs);
-                    const Re sr = (Re)((-2.0 * dl + dl * dl - bt * bt)) * inv_scale;
-                    const Re si = (Re)((2.0 * bt - 2.0 * dl * bt)) * inv_scale;
-                    const Re tr = (Re)(mag * cs), ti = -(Re)(mag * sn);
                     Cx v;
-                    v.x = chi * (sr * tr - si * ti);
-                    v.y = chi * (sr * ti + si * tr);
+                    v.x = v.y = (Re)0;
+                    if (chi != (Re)0) {
+                        const ScanT mag = exp(-kdz * Cb);
+                        ScanT sn, cs;
+                        sincos(kdz * Cd, &sn, &cs);
+                        const Re sr = (Re)((-2.0 * dl + dl * dl - bt * bt)) * inv_scale;
+                        const Re si = (Re)((2.0 * bt - 2.0 * dl * bt)) * inv_scale;
+                        const Re tr = (Re)(mag * cs), ti = -(Re)(mag * sn);
+                        v.x = chi * (sr * tr - si * ti);
+                        v.y = chi * (sr * ti + si * tr);
+                    }
                     srow[iz] = v;
                 }
                 continue;
@@ -216,12 +219,15 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
             const ScanT C = carry + incl - (ScanT)chi;
             carry += __shfl_sync(0xffffffffu, incl, 31);
             if (iz < nz) {
-                const ScanT mag = exp(-a_att * C);
-                ScanT sn, cs;
-                sincos(a_ph * C, &sn, &cs);
                 Cx v;
-                v.x = chi * (Re)(mag * cs);
-                v.y = -chi * (Re)(mag * sn);
+                v.x = v.y = (Re)0;                 // s = chi T vanishes with chi: no T needed
+                if (chi != (Re)0) {
+                    const ScanT mag = exp(-a_att * C);
+                    ScanT sn, cs;
+                    sincos(a_ph * C, &sn, &cs);
+                    v.x = chi * (Re)(mag * cs);
+                    v.y = -chi * (Re)(mag * sn);
+                }
                 srow[iz] = v;
             }
         }
