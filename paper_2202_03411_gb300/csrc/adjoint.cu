@@ -458,18 +458,21 @@ int grad_voxel_blocks(bool fp64, const ShapeParams &sp, const GridParams &gp, in
     const long long cols = (long long)gp.nx * gp.ny;
     const long long b = (cols + (kGradThreads / 32) - 1) / (kGradThreads / 32);
     int per_sm = 0;
+    bool ok;
     if (fp64) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grad_voxel_fn<double>(sp, gp), kGradThreads, 0) !=
-            cudaSuccess)
-            per_sm = 1;
+        ok = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, grad_voxel_fn<double>(sp, gp), kGradThreads, 0) ==
+             cudaSuccess;
     } else {
         const auto fn = grad_voxel_fn<float>(sp, gp);
         const size_t smem = grad_voxel_smem(sp);
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGradThreads, smem) != cudaSuccess)
-            per_sm = 1;
+        ok = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGradThreads, smem) == cudaSuccess;
     }
-    (void)cudaGetLastError();
+    if (!ok) {
+        // a failed query only costs the whole-wave sizing; the launch reports real errors
+        (void)cudaGetLastError();
+        per_sm = 1;
+    }
     long long cap = (long long)(sm_count > 0 ? sm_count : 1) * (per_sm > 0 ? per_sm : 1);
     if (cap > 608) cap = 608;
     return (int)(b < cap ? b : cap);

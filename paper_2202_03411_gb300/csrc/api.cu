@@ -416,12 +416,15 @@ int scatman_create(const scatman_config *cfg, void *cuda_stream, scatman_handle 
     return SCATMAN_OK;
 }
 
-// Radius band of a binary harmonics or radii-map shape: every direction's
-// surface radius lies in [band_lo, band_hi], so voxels clearly inside or
-// outside skip the radius evaluation.  Harmonics: per degree l,
+// Radius band of a harmonics or radii-map shape (and, with soft occupancy in
+// the FP32 modes, of a sphere or ellipsoid): every direction's surface radius
+// lies in [band_lo, band_hi], so voxels clearly inside or outside skip the
+// radius evaluation.  Harmonics: per degree l,
 // |sum_m a_lm Y_lm| <= |a_l| sqrt((2l+1)/(4 pi)) (Cauchy-Schwarz with the
 // addition theorem sum_m Y_lm^2 = (2l+1)/(4 pi)), then the clip; radii map:
-// the interpolation stays within the samples' range.
+// the interpolation stays within the samples' range; sphere: r; ellipsoid:
+// between its smallest and largest semi-axis.  Soft occupancy widens the band
+// by the logistic's reach on both sides.
 static void set_radius_band(const scatman_shape *s, ShapeParams *sp, bool fp64) {
     sp->band_lo = sp->band_hi = 0.f;
     if (sp->soft && fp64) return;   // FP64 soft occupancy: the exact logistic at every voxel
