@@ -90,7 +90,10 @@ enum {
  *                  NULL/0 selects the detector
  *  precision       scatman_precision
  *  soft            0: binary occupancy (voxel centre inside, ties inside);
- *                  1: logistic occupancy sigmoid((r_s - |p|)/soft_width)
+ *                  1: logistic occupancy sigmoid((r_s - |p|)/soft_width);
+ *                  outside SCATMAN_FP64 a voxel whose logistic is below
+ *                  2^-24 counts as empty (forward and gradient alike), so
+ *                  the contraction can skip the empty part of each slice
  *  soft_width      logistic width in length units (> 0 when soft)
  *  scan_fp64       1 forces the transmission scan into FP64 (always on in
  *                  SCATMAN_FP64; switched on automatically when
