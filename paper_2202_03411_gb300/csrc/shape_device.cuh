@@ -216,6 +216,92 @@ static __device__ __noinline__ double occupancy_binary_fp64(const ShapeParams &s
     return rr <= rs ? 1.0 : 0.0;
 }
 
+// Coefficient tables of the harmonics, staged in shared memory for
+// sh_binary_fp64_warp: a and b (kShTri each), d and e (kShDiag each), then alm.
+constexpr int kShTri = (SCATMAN_MAX_LMAX + 1) * (SCATMAN_MAX_LMAX + 2) / 2;
+constexpr int kShDiag = SCATMAN_MAX_LMAX + 1;
+constexpr int kShTabDoubles = 2 * kShTri + 2 * kShDiag + kShDiag * kShDiag;
+
+__device__ __forceinline__ void sh_stage_tables(const ShapeParams &sp, double *tab) {
+    for (int k = threadIdx.x; k < kShTabDoubles; k += blockDim.x) {
+        double v;
+        if (k < kShTri) v = sp.sh_a[k];
+        else if (k < 2 * kShTri) v = sp.sh_b[k - kShTri];
+        else if (k < 2 * kShTri + kShDiag) v = sp.sh_d[k - 2 * kShTri];
+        else if (k < 2 * kShTri + 2 * kShDiag) v = sp.sh_e[k - 2 * kShTri - kShDiag];
+        else v = sp.alm[k - 2 * kShTri - 2 * kShDiag];
+        tab[k] = v;
+    }
+}
+
+// The FP64 binary decision of one harmonics voxel by a whole warp (call with
+// all 32 lanes; every lane gets the result): the body coordinates and |p| as in
+// occupancy_binary_fp64, then lane m (m <= lmax) sums the terms of orders +m
+// and -m over l = m..lmax with the recurrences of real_sh_all, and the warp
+// adds the lanes' sums.  GB300 runs FP64 at a small fraction of its FP32 rate,
+// so the warp's instruction count, not its lane count, sets the cost of the
+// near-surface decisions: splitting the orders over lanes cuts it about three-fold.
+// Only the summation order differs from occupancy_binary_fp64 (both decide in
+// FP64; the oracle evaluates the radius by yet another route).
+static __device__ __noinline__ double sh_binary_fp64_warp(const ShapeParams &sp, const GridParams &gp, int ix, int iy,
+                                                         int iz, const double *tab) {
+    const double *ta = tab, *tb = tab + kShTri, *td = tab + 2 * kShTri, *te = td + kShDiag, *talm = te + kShDiag;
+    double px, py, pz;
+    body_coords(sp, gp, ix, iy, iz, px, py, pz);
+    const double p2 = __dadd_rn(__dadd_rn(__dmul_rn(px, px), __dmul_rn(py, py)), __dmul_rn(pz, pz));
+    const double rr = sqrt(p2);
+    double ct = 1.0, st = 0.0, cphi = 1.0, sphi = 0.0;
+    if (rr > 0.0) {
+        ct = pz / rr;
+        const double rho = sqrt(px * px + py * py);
+        st = rho / rr;
+        if (rho > 0.0) {
+            cphi = px / rho;
+            sphi = py / rho;
+        }
+    }
+    const int L = sp.lmax, m = threadIdx.x & 31;
+    double part = 0.0;
+    if (m <= L) {
+        double pmm = 0.28209479177387814347, cm = 1.0, sm = 0.0;
+        for (int k = 1; k <= m; ++k) {
+            pmm = td[k] * st * pmm;
+            const double c2 = cm * cphi - sm * sphi, s2 = sm * cphi + cm * sphi;
+            cm = c2;
+            sm = s2;
+        }
+        const double kSqrt2 = 1.41421356237309504880;
+        const double wc = m == 0 ? 1.0 : kSqrt2 * cm, ws = kSqrt2 * sm;
+        double q2 = 0.0, q1 = pmm;
+        for (int l = m; l <= L; ++l) {
+            double p;
+            if (l == m) {
+                p = pmm;
+            } else if (l == m + 1) {
+                p = te[m] * ct * pmm;
+            } else {
+                const int i = l * (l + 1) / 2 + m;
+                p = ta[i] * (ct * q1 - tb[i] * q2);
+            }
+            if (l > m) {
+                q2 = q1;
+                q1 = p;
+            }
+            if (l == 0) continue;                     // a_00 is not a coefficient
+            if (m == 0)
+                part += talm[l * l + l] * p;
+            else
+                part += talm[l * l + l + m] * (p * wc) + talm[l * l + l - m] * (p * ws);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    double rs = sp.R0 * (1.0 + part);
+    rs = rs < sp.rmin ? sp.rmin : rs;
+    rs = rs > sp.rmax ? sp.rmax : rs;
+    return rr <= rs ? 1.0 : 0.0;
+}
+
 // Volume-map cell of voxel (ix, iy, iz) in either precision (see vmap_cell_fp64).
 template <bool kFp64>
 __device__ __forceinline__ int vmap_cell(const ShapeParams &sp, const GridParams &gp, int ix, int iy, int iz) {

@@ -149,12 +149,29 @@ __global__ void __launch_bounds__(kVoxThreads, 3) voxelise_scan_kernel(ShapePara
     }
     __syncthreads();
     if (!kFp64) {
-        // the queued voxels' FP64 decisions, one voxel per thread
+        // the queued voxels' FP64 decisions: harmonics one voxel per warp (its
+        // lanes split the orders; coefficient tables staged in the slice tile,
+        // which the FP32 modes leave unused until pass 2, when it is large
+        // enough), other kinds one voxel per thread
         const int qn = min(s_qn, kVoxQueue);
-        for (int k = threadIdx.x; k < qn; k += kVoxThreads) {
-            const int e = queue[k];
-            const int yl = e >> 16, iz = e & 0xffff;
-            chi_tile[(size_t)yl * zs + iz] = (float)occupancy_binary_fp64(sp, gp, ix, y0 + yl, iz);
+        const bool warp_sh = !kMaps && sp.kind == SCATMAN_SPHHARM &&
+                             sizeof(Cx) * (size_t)zs * kLinesPerCta >= kShTabDoubles * sizeof(double);
+        if (warp_sh && qn > 0) {
+            double *tab = reinterpret_cast<double *>(s_tile);
+            sh_stage_tables(sp, tab);
+            __syncthreads();
+            for (int k = warp; k < qn; k += kVoxThreads / 32) {
+                const int e = queue[k];
+                const int yl = e >> 16, iz = e & 0xffff;
+                const double in = sh_binary_fp64_warp(sp, gp, ix, y0 + yl, iz, tab);
+                if (lane == 0) chi_tile[(size_t)yl * zs + iz] = (float)in;
+            }
+        } else {
+            for (int k = threadIdx.x; k < qn; k += kVoxThreads) {
+                const int e = queue[k];
+                const int yl = e >> 16, iz = e & 0xffff;
+                chi_tile[(size_t)yl * zs + iz] = (float)occupancy_binary_fp64(sp, gp, ix, y0 + yl, iz);
+            }
         }
         __syncthreads();
     }
